@@ -1,0 +1,400 @@
+#!/usr/bin/env python3
+"""Benchmark of the SLASH hot path on B300: inserts/s and queries/s.
+
+One step = reset the index, insert the workload's rows (Algorithm 1), run its
+query batch (Algorithm 2), all through the C ABI with inputs resident in HBM.
+`value` is inserts/s over all ranks; queries/s is reported beside it.  `e2e`
+repeats the step through the same public calls from pinned HOST buffers, with
+the host->device copies of the inputs and the device->host read of the
+results inside the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload criteo|tiny|uneven]
+    python bench.py --impl reference ...   # the CPU oracle on a bounded sample
+
+Multi-GPU (torchrun, one rank per GPU): every rank indexes its own disjoint row
+range (the paper's data partitions D_i, Sec. 3) and answers its own queries;
+nothing is exchanged on the data path, so scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import datagen  # noqa: E402
+from datagen import workloads  # noqa: E402
+
+METRIC = "inserts/s and queries/s on 1 B300 (bit-exact), batched vs plain; serving p50/p99 ms"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6400.0, "source": "fallback"}
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        try:
+            for ln in open(self.path):
+                f = [x.strip() for x in ln.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())}
+
+
+# ----------------------------------------------------------------------------- inputs
+def make_inputs(w: workloads.Workload, row0: int, n_rows: int, n_queries: int, qseed_off: int = 0):
+    g = datagen.Generator(dim_bits=w.dim_bits)
+    t = time.time()
+    offs, cols = g.rows(w.seed, row0, n_rows, lo=w.nnz_lo, hi=w.nnz_hi)
+    qo, qc, src = g.queries(w.seed, w.qseed + qseed_off, n_queries, n_rows, q0=0, **w.query_kwargs())
+    if row0:
+        src = np.where(src >= 0, src + row0, src)  # planted sources refer to this rank's rows
+    log(f"[bench] generated {n_rows} rows ({len(cols)} nnz) and {n_queries} queries in {time.time() - t:.1f}s")
+    return offs, cols, qo, qc, src
+
+
+def as_i64(a):
+    return a.view(np.int64)
+
+
+def as_i32(a):
+    return a.view(np.int32)
+
+
+# ----------------------------------------------------------------------------- CPU baseline (oracle)
+def cpu_baseline(w: workloads.Workload, offs, cols, qo, qc, budget_s: float = 20.0) -> dict:
+    import oracle
+    n_s = min(len(offs) - 1, 200_000 if w.L >= 32 else 1_000_000)
+    ix = oracle.Index(K=w.K, L=w.L, log2_buckets=w.log2_buckets, reservoir=w.reservoir, cm_rows=w.cm_rows,
+                      cm_width=w.cm_width, shards=w.shards, seed=w.seed, capacity=w.n_rows)
+    o = offs[:n_s + 1]
+    t = time.perf_counter()
+    ix.insert(o, cols[:int(o[-1])])
+    ti = time.perf_counter() - t
+    nq = min(len(qo) - 1, 2000)
+    t = time.perf_counter()
+    ix.query(qo[:nq + 1], qc[:int(qo[nq])], w.topk)
+    tq = time.perf_counter() - t
+    return {"value": n_s / ti, "unit": "rows/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n_s} rows of the {w.name} workload inserted into the oracle's dense index "
+                      f"(single thread, {ti:.1f}s); queries/s {nq / tq:.1f} on {nq} of its queries against "
+                      f"that {n_s}-row index (smaller buckets than the full-size index)",
+            "queries_per_s": nq / tq}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, w: workloads.Workload) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    per_step = 30_000 if w.L >= 32 else 150_000
+    total = per_step * (args.steps + args.warmup)
+    g = datagen.Generator(dim_bits=w.dim_bits)
+    offs, cols = g.rows(w.seed, 0, total, lo=w.nnz_lo, hi=w.nnz_hi)
+    times = []
+    for i in range(args.warmup + args.steps):
+        a, b = i * per_step, (i + 1) * per_step
+        o = offs[a:b + 1]
+        c = cols[int(o[0]):int(o[-1])]
+        ix = oracle.Index(K=w.K, L=w.L, log2_buckets=w.log2_buckets, reservoir=w.reservoir,
+                          cm_rows=w.cm_rows, cm_width=w.cm_width, shards=w.shards, seed=w.seed,
+                          capacity=w.n_rows)
+        t = time.perf_counter()
+        ix.insert(o, c)
+        dt = time.perf_counter() - t
+        del ix
+        if i >= args.warmup:
+            times.append(dt)
+    v = per_step / statistics.mean(times)
+    out = {"metric": METRIC, "value": v, "unit": "rows/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "impl": "reference",
+           "config": config_of(w, args),
+           "cpu_baseline": {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{per_step} rows of the {w.name} workload per step, each step into "
+                                      f"a fresh dense oracle index (single thread)"},
+           "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def config_of(w, args) -> dict:
+    return {"workload": w.name, "rows_per_gpu": w.n_rows, "queries_per_gpu": w.n_queries, "K": w.K, "L": w.L,
+            "log2_buckets": w.log2_buckets, "reservoir": w.reservoir, "cm": f"{w.cm_rows}x{w.cm_width}",
+            "topk": w.topk, "shards": w.shards, "parallelism": f"rows{args.gpus}",
+            "l2": "inputs larger than L2 (CSR and bucket arrays are GBs), no flush"}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+ALGO_BYTES_DOC = {
+    "k_hash_insert": "8 + 4*nnz (CSR read) + 4*L (addresses written) per row",
+    "k_scatter": "4 (address read) + 4 (id written) per (row, table)",
+    "k_merge_small": "4 (staged id read) per (row, table) + 4*R written per touched bucket",
+    "k_merge_big": "4 (staged id read) per (row, table) + 4*R written per touched bucket",
+    "k_hash": "8 + 4*nnz + 4*L per query",
+    "k_query": "4*L (addresses) + 4*S*L (fills) + 4*sum(fill) (ids) + 8*k (outputs) per query",
+}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="criteo", choices=sorted(workloads.ALL))
+    ap.add_argument("--impl", default="slash", choices=["slash", "reference"])
+    ap.add_argument("--rows", type=int, default=0, help="override rows per GPU (small profiling runs)")
+    ap.add_argument("--queries", type=int, default=0, help="override queries per GPU")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    w = workloads.ALL[args.workload]
+    if args.rows or args.queries:
+        from dataclasses import replace
+        w = replace(w, n_rows=args.rows or w.n_rows, n_queries=args.queries or w.n_queries)
+    if args.warmup < 3:
+        log("[bench] warning: fewer than 3 warm-up steps")
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    import paper_2008_03260_b300 as slash
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    offs, cols, qo, qc, _ = make_inputs(w, rank * w.n_rows, w.n_rows, w.n_queries, qseed_off=rank)
+    h2d_bytes = offs.nbytes + cols.nbytes + qo.nbytes + qc.nbytes
+    d2h_bytes = 2 * 4 * w.n_queries * w.topk
+    t = time.time()
+    h_offs = torch.from_numpy(as_i64(offs)).pin_memory()
+    h_cols = torch.from_numpy(as_i32(cols)).pin_memory()
+    h_qo = torch.from_numpy(as_i64(qo)).pin_memory()
+    h_qc = torch.from_numpy(as_i32(qc)).pin_memory()
+    h_ids = torch.empty((w.n_queries, w.topk), dtype=torch.int32).pin_memory()
+    h_sc = torch.empty((w.n_queries, w.topk), dtype=torch.int32).pin_memory()
+    d_offs, d_cols = h_offs.cuda(), h_cols.cuda()
+    d_qo, d_qc = h_qo.cuda(), h_qc.cuda()
+    d_ids = torch.empty((w.n_queries, w.topk), dtype=torch.int32, device="cuda")
+    d_sc = torch.empty_like(d_ids)
+    torch.cuda.synchronize()
+    log(f"[bench] pinned + uploaded {h2d_bytes / 1e9:.2f} GB in {time.time() - t:.1f}s")
+
+    p = slash.Params(**w.params(capacity=w.n_rows))
+    ix = slash.Index(p)
+    st = torch.cuda.current_stream()
+
+    def step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(st)
+        ix.reset(st)
+        ev[1].record(st)
+        ix.insert(d_offs, d_cols, st)
+        ev[2].record(st)
+        ix.query(d_qo, d_qc, w.topk, st, d_ids_out=d_ids, d_scores_out=d_sc)
+        ev[3].record(st)
+        return ev
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ix.sync(st)
+    # per-query candidate volume (for the query's algorithmic bytes), from the warm index
+    _, qbk = ix.debug_hash(d_qo, d_qc, want_codes=False)
+    _, fill = ix.export()
+    qb = qbk.cpu().numpy().view(np.uint32)                       # [L][nq]
+    sum_fill = int(sum(fill[s][t][qb[t]].astype(np.int64).sum() for s in range(w.shards) for t in range(w.L)))
+    torch.cuda.synchronize()
+
+    ix.profile(True)
+    _, launches0 = ix.profile_read()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t0 = time.perf_counter()
+        evs = [step() for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    prof, launches1 = ix.profile_read()
+    ix.profile(False)
+    rc = slash.slash_sync(ix.h)
+    if rc != slash.SLASH_OK:
+        raise SystemExit(f"device reported {slash.slash_strerror(rc)}")
+    ins = [e[1].elapsed_time(e[2]) / 1e3 for e in evs]
+    qry = [e[2].elapsed_time(e[3]) / 1e3 for e in evs]
+    tot = [e[0].elapsed_time(e[3]) / 1e3 for e in evs]
+    t_ins, t_q, t_step = statistics.mean(ins), statistics.mean(qry), statistics.mean(tot)
+    if dist:
+        v = torch.tensor([t_ins, t_q, t_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        t_ins, t_q, t_step = v.tolist()
+
+    # e2e: the same calls from pinned host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        e_ins, e_q = [], []
+        for i in range(args.warmup + args.steps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ix.reset(st)
+            ev[0].record(st)
+            d_offs.copy_(h_offs, non_blocking=True)
+            d_cols.copy_(h_cols, non_blocking=True)
+            ix.insert(d_offs, d_cols, st)
+            ev[1].record(st)
+            d_qo.copy_(h_qo, non_blocking=True)
+            d_qc.copy_(h_qc, non_blocking=True)
+            ix.query(d_qo, d_qc, w.topk, st, d_ids_out=d_ids, d_scores_out=d_sc)
+            h_ids.copy_(d_ids, non_blocking=True)
+            h_sc.copy_(d_sc, non_blocking=True)
+            ev[2].record(st)
+            ev[2].synchronize()
+            if i >= args.warmup:
+                e_ins.append(ev[0].elapsed_time(ev[1]) / 1e3)
+                e_q.append(ev[1].elapsed_time(ev[2]) / 1e3)
+        ei, eq = statistics.mean(e_ins), statistics.mean(e_q)
+        if dist:
+            v = torch.tensor([ei, eq], device="cuda", dtype=torch.float64)
+            dist.all_reduce(v, op=dist.ReduceOp.MAX)
+            ei, eq = v.tolist()
+        e2e = {"value": world * w.n_rows / ei, "unit": "rows/s", "h2d_bytes_per_step": h2d_bytes,
+               "d2h_bytes_per_step": d2h_bytes, "queries_per_s": world * w.n_queries / eq,
+               "insert_ms": 1e3 * ei, "query_ms": 1e3 * eq}
+
+    # per-kernel shares and the dominant kernel's roofline
+    pk = peaks()
+    nnz = int(len(cols))
+    kern = {}
+    tot_ms = sum(v[0] for v in prof.values()) or 1.0
+    for name, (ms, n) in sorted(prof.items(), key=lambda x: -x[1][0]):
+        kern[name] = {"launches": n, "ms_per_launch": ms / n, "share": ms / tot_ms}
+    rows, L, R, k = w.n_rows, w.L, w.reservoir, w.topk
+    algo = {
+        "k_hash_insert": 8 * rows + 4 * nnz + 4 * L * rows,
+        "k_scatter": 8 * L * rows,
+        "k_hash": 8 * w.n_queries + 4 * int(len(qc)) + 4 * L * w.n_queries,
+        "k_query": 4 * L * w.n_queries + 4 * w.shards * L * w.n_queries + 4 * sum_fill + 8 * k * w.n_queries,
+    }
+    dom = max(kern, key=lambda n: kern[n]["ms_per_launch"] * kern[n]["launches"])
+    roof = None
+    if dom in algo:
+        launches_per_step = kern[dom]["launches"] / args.steps
+        bytes_per_launch = algo[dom] / launches_per_step
+        ach = bytes_per_launch / (kern[dom]["ms_per_launch"] / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"],
+                "algorithmic_bytes_per_launch": bytes_per_launch, "bytes_def": ALGO_BYTES_DOC.get(dom)}
+    path_ins_bytes = 8 * rows + 4 * nnz + 12 * L * rows   # per-row figure of the insert path
+    path_q_bytes = algo["k_hash"] + algo["k_query"]
+    out = {
+        "metric": METRIC,
+        "value": world * w.n_rows / t_ins,
+        "unit": "rows/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32", "data": "synthetic (seeded Criteo-shaped generator)",
+        "config": config_of(w, args),
+        "queries_per_s": world * w.n_queries / t_q,
+        "insert_ms": 1e3 * t_ins, "query_ms": 1e3 * t_q,
+        "path_roofline": {"insert_frac": path_ins_bytes / t_ins / 1e9 / pk["hbm_gbs"],
+                          "query_frac": path_q_bytes / t_q / 1e9 / pk["hbm_gbs"],
+                          "insert_bytes": path_ins_bytes, "query_bytes": path_q_bytes,
+                          "mean_candidates_per_query": sum_fill / max(1, w.n_queries)},
+        "roofline": roof,
+        "kernels": kern,
+        "gpu_launches": int(launches1 - launches0),
+        "clocks": clk.summary(),
+        "wall_s": wall,
+    }
+    if e2e:
+        out["e2e"] = e2e
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, offs, cols, qo, qc)
+    ix.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

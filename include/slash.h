@@ -1,0 +1,163 @@
+/*
+ * slash.h -- C ABI of the SLASH similarity-search hot path on one B300 GPU.
+ *
+ * Method: Meisburger & Shrivastava, "Distributed Tera-Scale Similarity Search
+ * with MPI" (arXiv 2008.03260).  The library indexes very sparse binary
+ * vectors with densified one-permutation MinHash (DOPH, Sec. 2.2) in a
+ * (K, L)-parameterised LSH structure (Sec. 2.3), stores ids in fixed-size
+ * sub-sampled buckets (Sec. 3, "Avoid Skewed buckets"), and answers a query by
+ * counting the ids of its L buckets in a count-min sketch and ranking them by
+ * estimated frequency (Sec. 2.3 "Cheap Frequency based Filtering and K-NN";
+ * Algorithm 2) -- no distance is ever computed.  The paper's m machine
+ * partitions D_i (Sec. 3, Design) become `shards` on-device partitions whose
+ * sketches are summed in device memory (Algorithm 2, merge across machines).
+ *
+ * Conventions for every entry point:
+ *   - Return value: SLASH_OK (0) or a negative SLASH_E* code; slash_strerror()
+ *     names it.  A call that fails validation changes nothing.
+ *   - Pointers named d_* are caller-owned DEVICE memory on the index's device;
+ *     the library never frees or retains them past the call's stream work.
+ *     Pointers named h_* are caller-owned host memory.
+ *   - `cuda_stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued on it and the call returns without waiting, except where a call
+ *     says it synchronises.  Caller buffers must stay valid until that stream
+ *     work completes.
+ *   - Errors the device finds in the data (a column id >= dim, decreasing
+ *     offsets) do not fault: the offending feature (or row) is skipped, a
+ *     sticky error word is set, and the next slash_sync() returns SLASH_EDATA
+ *     and clears it.
+ *   - An index is not thread-safe: serialise calls on one index and issue them
+ *     on one stream at a time (the library's per-index workspace is reused by
+ *     every call).
+ *   - CSR input: row i's feature ids are d_cols[d_offs[i] .. d_offs[i+1]), ids
+ *     in [0, dim); d_offs holds n+1 entries (d_offs[0] need not be 0).  Order
+ *     and duplicates within a row do not matter (MinHash is a set function);
+ *     a row with no features is valid (all its codes are empty, it still
+ *     occupies one bucket per table).
+ */
+#ifndef SLASH_H
+#define SLASH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SLASH_OK        0
+#define SLASH_EINVAL   (-1)  /* bad argument or parameter                          */
+#define SLASH_ENOMEM   (-2)  /* device allocation failed (index left unchanged)    */
+#define SLASH_ECUDA    (-3)  /* a CUDA runtime call failed                         */
+#define SLASH_EFULL    (-4)  /* insert would exceed `capacity`                     */
+#define SLASH_EBUSY    (-5)  /* admission refused (serving layer)                  */
+#define SLASH_ETIMEOUT (-6)  /* a bounded device wait gave up                      */
+#define SLASH_EDATA    (-7)  /* the device found invalid input data (see above)    */
+
+#define SLASH_EMPTY 0xFFFFFFFFu /* an unused bucket slot */
+
+/* Limits of this implementation (checked by slash_build_index). */
+#define SLASH_MAX_L     128u   /* tables                                  */
+#define SLASH_MAX_NB    1024u  /* K * L DOPH bins                         */
+#define SLASH_MAX_R     512u   /* reservoir slots per bucket              */
+#define SLASH_MAX_CMROWS 8u    /* count-min rows d                        */
+#define SLASH_MAX_TOPK  256u   /* k of a query                            */
+
+typedef struct slash_index slash_index; /* opaque; owned by the library */
+
+/* Index parameters.  Sec. 4 "Initialization": L x K hash functions from one
+ * shared seed; every shard (the paper's machine partition) uses the same
+ * functions, so the shards form one logical index. */
+typedef struct {
+  uint32_t dim;           /* D: feature ids must be < dim                          */
+  uint32_t K;             /* codes concatenated per table address (>= 1)           */
+  uint32_t L;             /* tables (1..SLASH_MAX_L); K*L <= SLASH_MAX_NB          */
+  uint32_t log2_buckets;  /* B: 2^B buckets per table (1..30)                      */
+  uint32_t reservoir;     /* R: ids kept per bucket (1..SLASH_MAX_R)               */
+  uint32_t cm_rows;       /* d: count-min rows (1..SLASH_MAX_CMROWS)               */
+  uint32_t cm_width;      /* w: counters per row, a power of two (>= 32)           */
+  uint32_t shards;        /* S: on-device partitions (1 = single index)            */
+  uint64_t seed;          /* the shared random seed                                */
+  uint64_t capacity;      /* max ids ever inserted (1..2^31-1; ids are int32)      */
+} slash_params;
+
+/* Allocate and clear an index on the current CUDA device: buckets
+ * uint32 [S][L][2^B][R] (SLASH_EMPTY) and fill counts uint32 [S][L][2^B] (0).
+ * Sec. 4 "Initialization".  Synchronises `cuda_stream`.
+ * Errors: SLASH_EINVAL (limits above), SLASH_ENOMEM, SLASH_ECUDA. */
+int slash_build_index(const slash_params *p, void *cuda_stream, slash_index **out);
+
+/* Pre-processing (Algorithm 1): rows get ids [*first_id_out, +n_rows) in
+ * order; each id enters one bucket per table of shard floor(id*S/capacity).
+ * A bucket keeps the R ids of smallest seeded priority among all ids ever
+ * inserted into it, in ascending priority -- independent of insertion order
+ * and of how rows are split into calls.  n_rows = 0 is a no-op.
+ * Errors: SLASH_EINVAL (NULL pointers with n_rows > 0), SLASH_EFULL,
+ * SLASH_ENOMEM (workspace growth), SLASH_ECUDA. */
+int slash_insert(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n_rows,
+                 uint64_t *first_id_out, void *cuda_stream);
+
+/* Querying (Algorithm 2): for each query, hash it into its L buckets, gather
+ * the ids they hold in every shard, count them in a d x w count-min sketch
+ * (shard sketches summed), estimate each distinct candidate's frequency as the
+ * minimum over rows, and write the top-k candidates by (estimate descending,
+ * id ascending).  Outputs, row-major [n_queries][topk]: d_ids_out int32 (-1
+ * padding when fewer than topk candidates exist) and d_scores_out uint32 (the
+ * estimates, 0 padding).  1 <= topk <= SLASH_MAX_TOPK; n_queries = 0 is a no-op.
+ * Errors: SLASH_EINVAL, SLASH_ENOMEM, SLASH_ECUDA. */
+int slash_query(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n_queries,
+                uint32_t topk, int32_t *d_ids_out, uint32_t *d_scores_out, void *cuda_stream);
+
+/* Release the index and its workspace (synchronises the device first).
+ * NULL is accepted.  Always SLASH_OK unless a CUDA call fails. */
+int slash_free(slash_index *ix);
+
+/* Human-readable name of a return code (static storage). */
+const char *slash_strerror(int code);
+
+/* Wait for `cuda_stream`, then report and clear the sticky device error word:
+ * SLASH_EDATA if invalid input data was seen since the last call, SLASH_ECUDA
+ * on an asynchronous CUDA error, else SLASH_OK. */
+int slash_sync(slash_index *ix, void *cuda_stream);
+
+/* Empty every bucket and restart ids at 0 (same state as a fresh build). */
+int slash_reset(slash_index *ix, void *cuda_stream);
+
+/* Number of ids inserted so far. */
+uint64_t slash_size(const slash_index *ix);
+
+/* Profiling support -- when enabled (enable != 0), every kernel the index
+ * launches is bracketed by CUDA events recorded on its launch stream.  Each
+ * call synchronises the device and discards the previous record. */
+int slash_profile(slash_index *ix, int enable);
+
+/* Profiling support -- per kernel name (at most max_kernels of them, in first
+ * launch order): h_names char [max_kernels][32] (NUL-terminated), h_ms summed
+ * event time in milliseconds, h_launches launch count; *n_kernels_out = the
+ * number of distinct kernels recorded; *total_launches_out (may be NULL) =
+ * kernel launches issued by this index since it was built, profiled or not.
+ * Synchronises.  Any output array may be NULL.  Errors: SLASH_EINVAL, SLASH_ECUDA. */
+int slash_profile_read(slash_index *ix, uint32_t max_kernels, char *h_names, float *h_ms,
+                       uint32_t *h_launches, uint32_t *n_kernels_out, uint64_t *total_launches_out);
+
+/* Test support -- the DOPH codes (Sec. 2.2, after densification) d_codes
+ * uint32 [n][K*L] (may be NULL) and table addresses d_buckets uint32 [L][n]
+ * (table-major) of n CSR rows, computed by the same kernel that insert and
+ * query use.  Errors: SLASH_EINVAL, SLASH_ECUDA. */
+int slash_debug_hash(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n,
+                     uint32_t *d_codes, uint32_t *d_buckets, void *cuda_stream);
+
+/* Test support -- copy the whole index to host memory: h_slots uint32
+ * [S][L][2^B][R], h_fill uint32 [S][L][2^B].  Synchronises.  Either pointer
+ * may be NULL.  Errors: SLASH_ECUDA. */
+int slash_debug_export(slash_index *ix, uint32_t *h_slots, uint32_t *h_fill);
+
+/* Test support -- copy selected buckets to host memory: for i < n,
+ * bucket (h_shard[i], h_table[i], h_bucket[i]) -> h_slots[i][R], h_fill[i].
+ * Synchronises.  Errors: SLASH_EINVAL (index out of range), SLASH_ECUDA. */
+int slash_debug_buckets(slash_index *ix, const uint32_t *h_shard, const uint32_t *h_table,
+                        const uint32_t *h_bucket, uint32_t n, uint32_t *h_slots, uint32_t *h_fill);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLASH_H */

@@ -1,0 +1,305 @@
+"""Python binding of ``libslash.so`` -- the SLASH hot path on one B300.
+
+Argument marshalling only: every step of hashing, insertion and querying runs
+in the library's CUDA kernels (see ``include/slash.h``).  PyTorch supplies
+device memory and streams.  There is no CPU fallback: if the library is
+missing or fails to load, importing this package raises.
+
+The functions carry the C ABI's names::
+
+    ix = slash_build_index(params)                       # -> handle
+    first = slash_insert(ix, d_offs, d_cols)             # Algorithm 1
+    ids, scores = slash_query(ix, d_offs, d_cols, topk)  # Algorithm 2
+    slash_free(ix)
+
+``d_offs`` is an 8-byte integer CUDA tensor of n+1 CSR offsets, ``d_cols`` a
+4-byte integer CUDA tensor of feature ids; both are passed by pointer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libslash.so")
+
+SLASH_OK = 0
+SLASH_EINVAL = -1
+SLASH_ENOMEM = -2
+SLASH_ECUDA = -3
+SLASH_EFULL = -4
+SLASH_EBUSY = -5
+SLASH_ETIMEOUT = -6
+SLASH_EDATA = -7
+SLASH_EMPTY = 0xFFFFFFFF
+SLASH_MAX_TOPK = 256
+
+
+class SlashError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {slash_strerror(code)} ({code})")
+
+
+class slash_params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_uint32), ("K", ctypes.c_uint32), ("L", ctypes.c_uint32),
+                ("log2_buckets", ctypes.c_uint32), ("reservoir", ctypes.c_uint32),
+                ("cm_rows", ctypes.c_uint32), ("cm_width", ctypes.c_uint32),
+                ("shards", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("capacity", ctypes.c_uint64)]
+
+
+def _load() -> ctypes.CDLL:
+    from . import build as _build
+    if _build.needs_build():  # compile the CUDA library in place (nvcc); no fallback if that fails
+        _build.build()
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libslash.so not built ({_LIB_PATH}); run python -m paper_2008_03260_b300.build")
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    P = ctypes.POINTER
+    sig = {
+        "slash_build_index": (i32, [P(slash_params), vp, P(vp)]),
+        "slash_insert": (i32, [vp, vp, vp, u32, P(u64), vp]),
+        "slash_query": (i32, [vp, vp, vp, u32, u32, vp, vp, vp]),
+        "slash_free": (i32, [vp]),
+        "slash_strerror": (ctypes.c_char_p, [i32]),
+        "slash_sync": (i32, [vp, vp]),
+        "slash_reset": (i32, [vp, vp]),
+        "slash_size": (u64, [vp]),
+        "slash_debug_hash": (i32, [vp, vp, vp, u32, vp, vp, vp]),
+        "slash_debug_export": (i32, [vp, vp, vp]),
+        "slash_debug_buckets": (i32, [vp, vp, vp, vp, u32, vp, vp]),
+        "slash_profile": (i32, [vp, i32]),
+        "slash_profile_read": (i32, [vp, u32, vp, vp, vp, P(u32), P(u64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    return lib
+
+
+_lib = _load()
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != SLASH_OK:
+        raise SlashError(rc, where)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream or None
+    return int(stream) or None
+
+
+def _dev_ptr(t: torch.Tensor, itemsize: int, name: str) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.element_size() != itemsize or not t.is_contiguous():
+        raise TypeError(f"{name} must be contiguous with {itemsize}-byte elements")
+    return t.data_ptr()
+
+
+@dataclass(frozen=True)
+class Params:
+    """Index parameters (see ``slash_params`` in include/slash.h)."""
+    dim: int = 1 << 20
+    K: int = 4
+    L: int = 16
+    log2_buckets: int = 16
+    reservoir: int = 32
+    cm_rows: int = 4
+    cm_width: int = 4096
+    shards: int = 1
+    seed: int = 0
+    capacity: int = 100_000
+
+    def c(self) -> slash_params:
+        return slash_params(self.dim, self.K, self.L, self.log2_buckets, self.reservoir,
+                            self.cm_rows, self.cm_width, self.shards, self.seed, self.capacity)
+
+    @property
+    def index_bytes(self) -> int:
+        nk = self.shards * self.L << self.log2_buckets
+        return nk * (self.reservoir + 1) * 4
+
+
+# --------------------------------------------------------------------------- C-ABI names
+def slash_strerror(code: int) -> str:
+    return _lib.slash_strerror(code).decode()
+
+
+def slash_build_index(p: Params, stream=None) -> int:
+    h = ctypes.c_void_p()
+    cp = p.c()
+    _check(_lib.slash_build_index(ctypes.byref(cp), _stream(stream), ctypes.byref(h)),
+           "slash_build_index")
+    return h.value
+
+
+def slash_insert(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, stream=None) -> int:
+    n = d_offs.numel() - 1
+    if n < 0:
+        raise ValueError("d_offs needs n+1 entries")
+    first = ctypes.c_uint64()
+    _check(_lib.slash_insert(ix, _dev_ptr(d_offs, 8, "d_offs"), _dev_ptr(d_cols, 4, "d_cols"), n,
+                             ctypes.byref(first), _stream(stream)), "slash_insert")
+    return int(first.value)
+
+
+def slash_query(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, topk: int,
+                d_ids_out: torch.Tensor | None = None, d_scores_out: torch.Tensor | None = None,
+                stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+    nq = d_offs.numel() - 1
+    if nq < 0:
+        raise ValueError("d_offs needs n+1 entries")
+    dev = d_offs.device
+    if d_ids_out is None:
+        d_ids_out = torch.empty((nq, topk), dtype=torch.int32, device=dev)
+    if d_scores_out is None:
+        d_scores_out = torch.empty((nq, topk), dtype=torch.int32, device=dev)
+    if d_ids_out.numel() < nq * topk or d_scores_out.numel() < nq * topk:
+        raise ValueError("output tensors too small")
+    _check(_lib.slash_query(ix, _dev_ptr(d_offs, 8, "d_offs"), _dev_ptr(d_cols, 4, "d_cols"), nq, topk,
+                            _dev_ptr(d_ids_out, 4, "d_ids_out"), _dev_ptr(d_scores_out, 4, "d_scores_out"),
+                            _stream(stream)), "slash_query")
+    return d_ids_out, d_scores_out
+
+
+def slash_free(ix: int) -> None:
+    if ix:
+        _check(_lib.slash_free(ix), "slash_free")
+
+
+def slash_sync(ix: int, stream=None) -> int:
+    return int(_lib.slash_sync(ix, _stream(stream)))
+
+
+def slash_reset(ix: int, stream=None) -> None:
+    _check(_lib.slash_reset(ix, _stream(stream)), "slash_reset")
+
+
+def slash_size(ix: int) -> int:
+    return int(_lib.slash_size(ix))
+
+
+def slash_debug_hash(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, nb: int, L: int,
+                     want_codes: bool = True, stream=None):
+    n = d_offs.numel() - 1
+    dev = d_offs.device
+    codes = torch.empty((n, nb), dtype=torch.int32, device=dev) if want_codes else None
+    bk = torch.empty((L, n), dtype=torch.int32, device=dev)
+    _check(_lib.slash_debug_hash(ix, _dev_ptr(d_offs, 8, "d_offs"), _dev_ptr(d_cols, 4, "d_cols"), n,
+                                 codes.data_ptr() if codes is not None else None, bk.data_ptr(),
+                                 _stream(stream)), "slash_debug_hash")
+    return codes, bk
+
+
+def slash_debug_export(ix: int, p: Params):
+    import numpy as np
+    nk = p.shards * p.L << p.log2_buckets
+    slots = np.empty(nk * p.reservoir, dtype=np.uint32)
+    fill = np.empty(nk, dtype=np.uint32)
+    _check(_lib.slash_debug_export(ix, slots.ctypes.data, fill.ctypes.data), "slash_debug_export")
+    return (slots.reshape(p.shards, p.L, 1 << p.log2_buckets, p.reservoir),
+            fill.reshape(p.shards, p.L, 1 << p.log2_buckets))
+
+
+def slash_debug_buckets(ix: int, p: Params, shard, table, bucket):
+    import numpy as np
+    s = np.ascontiguousarray(shard, dtype=np.uint32)
+    t = np.ascontiguousarray(table, dtype=np.uint32)
+    b = np.ascontiguousarray(bucket, dtype=np.uint32)
+    n = s.size
+    slots = np.empty((n, p.reservoir), dtype=np.uint32)
+    fill = np.empty(n, dtype=np.uint32)
+    _check(_lib.slash_debug_buckets(ix, s.ctypes.data, t.ctypes.data, b.ctypes.data, n,
+                                    slots.ctypes.data, fill.ctypes.data), "slash_debug_buckets")
+    return slots, fill
+
+
+def slash_profile(ix: int, enable: bool) -> None:
+    _check(_lib.slash_profile(ix, 1 if enable else 0), "slash_profile")
+
+
+def slash_profile_read(ix: int, max_kernels: int = 32) -> tuple[dict, int]:
+    """{kernel name: (total ms, launches)} since profiling was enabled, and the
+    index's total kernel launches since it was built."""
+    names = ctypes.create_string_buffer(32 * max_kernels)
+    ms = (ctypes.c_float * max_kernels)()
+    cnt = (ctypes.c_uint32 * max_kernels)()
+    n = ctypes.c_uint32()
+    tot = ctypes.c_uint64()
+    _check(_lib.slash_profile_read(ix, max_kernels, names, ms, cnt, ctypes.byref(n), ctypes.byref(tot)),
+           "slash_profile_read")
+    out = {}
+    for i in range(min(n.value, max_kernels)):
+        nm = names.raw[32 * i:32 * i + 32].split(b"\0", 1)[0].decode()
+        out[nm] = (float(ms[i]), int(cnt[i]))
+    return out, int(tot.value)
+
+
+class Index:
+    """Owning wrapper: ``Index(Params(...))``, ``.insert``, ``.query``, ``.close``."""
+
+    def __init__(self, p: Params, stream=None):
+        self.p = p
+        self.h = slash_build_index(p, stream)
+
+    def insert(self, d_offs, d_cols, stream=None) -> int:
+        return slash_insert(self.h, d_offs, d_cols, stream)
+
+    def query(self, d_offs, d_cols, topk: int, stream=None, **kw):
+        return slash_query(self.h, d_offs, d_cols, topk, stream=stream, **kw)
+
+    def sync(self, stream=None) -> None:
+        _check(slash_sync(self.h, stream), "slash_sync")
+
+    def reset(self, stream=None) -> None:
+        slash_reset(self.h, stream)
+
+    @property
+    def size(self) -> int:
+        return slash_size(self.h)
+
+    def export(self):
+        return slash_debug_export(self.h, self.p)
+
+    def buckets(self, shard, table, bucket):
+        return slash_debug_buckets(self.h, self.p, shard, table, bucket)
+
+    def debug_hash(self, d_offs, d_cols, want_codes: bool = True, stream=None):
+        return slash_debug_hash(self.h, d_offs, d_cols, self.p.K * self.p.L, self.p.L, want_codes, stream)
+
+    def profile(self, enable: bool = True) -> None:
+        slash_profile(self.h, enable)
+
+    def profile_read(self) -> tuple[dict, int]:
+        return slash_profile_read(self.h)
+
+    def close(self) -> None:
+        h, self.h = self.h, None
+        if h:
+            slash_free(h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
