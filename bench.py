@@ -203,6 +203,7 @@ ALGO_BYTES_DOC = {
     "k_merge_big": "4 (staged id read) per (row, table) + 4*R written per touched bucket",
     "k_hash": "8 + 4*nnz + 4*L per query",
     "k_query": "4*L (addresses) + 4*S*L (fills) + 4*sum(fill) (ids) + 8*k (outputs) per query",
+    "k_query_fused": "8 + 4*nnz (CSR) + 4*S*L (fills) + 4*sum(fill) (ids) + 8*k (outputs) per query",
 }
 
 
@@ -215,13 +216,16 @@ def main():
     ap.add_argument("--impl", default="slash", choices=["slash", "reference"])
     ap.add_argument("--rows", type=int, default=0, help="override rows per GPU (small profiling runs)")
     ap.add_argument("--queries", type=int, default=0, help="override queries per GPU")
+    ap.add_argument("--log2-buckets", type=int, default=0, help="override (small profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     w = workloads.ALL[args.workload]
-    if args.rows or args.queries:
+    if args.rows or args.queries or args.log2_buckets:
         from dataclasses import replace
-        w = replace(w, n_rows=args.rows or w.n_rows, n_queries=args.queries or w.n_queries)
+        w = replace(w, n_rows=args.rows or w.n_rows, n_queries=args.queries or w.n_queries,
+                    log2_buckets=args.log2_buckets or w.log2_buckets)
     if args.warmup < 3:
         log("[bench] warning: fewer than 3 warm-up steps")
     if args.impl == "reference":
@@ -276,9 +280,16 @@ def main():
         step()
     torch.cuda.synchronize()
     ix.sync(st)
+    tuned = None
+    if not args.no_autotune:
+        best, best_ms = ix.autotune(d_qo, d_qc, w.topk, st)
+        tuned = {"schedule": repr(best), "ms": best_ms}
+        log(f"[bench] autotuned query schedule: {best} ({best_ms:.3f} ms)")
+        step()
+        torch.cuda.synchronize()
     # per-query candidate volume (for the query's algorithmic bytes), from the warm index
     _, qbk = ix.debug_hash(d_qo, d_qc, want_codes=False)
-    _, fill = ix.export()
+    _, fill = ix.export(fill_only=True)
     qb = qbk.cpu().numpy().view(np.uint32)                       # [L][nq]
     sum_fill = int(sum(fill[s][t][qb[t]].astype(np.int64).sum() for s in range(w.shards) for t in range(w.L)))
     torch.cuda.synchronize()
@@ -298,6 +309,17 @@ def main():
     rc = slash.slash_sync(ix.h)
     if rc != slash.SLASH_OK:
         raise SystemExit(f"device reported {slash.slash_strerror(rc)}")
+    # the plain one-launch-per-stage query path on the same batch, for comparison
+    plain = []
+    for i in range(args.warmup + args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        ix.query(d_qo, d_qc, w.topk, st, d_ids_out=d_ids, d_scores_out=d_sc, mode="plain", threads=512)
+        b.record(st)
+        b.synchronize()
+        if i >= args.warmup:
+            plain.append(a.elapsed_time(b) / 1e3)
+    t_plain = statistics.mean(plain)
     ins = [e[1].elapsed_time(e[2]) / 1e3 for e in evs]
     qry = [e[2].elapsed_time(e[3]) / 1e3 for e in evs]
     tot = [e[0].elapsed_time(e[3]) / 1e3 for e in evs]
@@ -350,6 +372,8 @@ def main():
         "k_hash_insert": 8 * rows + 4 * nnz + 4 * L * rows,
         "k_scatter": 8 * L * rows,
         "k_hash": 8 * w.n_queries + 4 * int(len(qc)) + 4 * L * w.n_queries,
+        "k_query_fused": 8 * w.n_queries + 4 * int(len(qc)) + 4 * w.shards * L * w.n_queries
+                         + 4 * sum_fill + 8 * k * w.n_queries,
         "k_query": 4 * L * w.n_queries + 4 * w.shards * L * w.n_queries + 4 * sum_fill + 8 * k * w.n_queries,
     }
     dom = max(kern, key=lambda n: kern[n]["ms_per_launch"] * kern[n]["launches"])
@@ -362,7 +386,7 @@ def main():
                 "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"],
                 "algorithmic_bytes_per_launch": bytes_per_launch, "bytes_def": ALGO_BYTES_DOC.get(dom)}
     path_ins_bytes = 8 * rows + 4 * nnz + 12 * L * rows   # per-row figure of the insert path
-    path_q_bytes = algo["k_hash"] + algo["k_query"]
+    path_q_bytes = algo["k_query_fused"]
     out = {
         "metric": METRIC,
         "value": world * w.n_rows / t_ins,
@@ -373,6 +397,8 @@ def main():
         "dtype": "u32", "data": "synthetic (seeded Criteo-shaped generator)",
         "config": config_of(w, args),
         "queries_per_s": world * w.n_queries / t_q,
+        "plain_queries_per_s": world * w.n_queries / t_plain,
+        "query_schedule": tuned,
         "insert_ms": 1e3 * t_ins, "query_ms": 1e3 * t_q,
         "path_roofline": {"insert_frac": path_ins_bytes / t_ins / 1e9 / pk["hbm_gbs"],
                           "query_frac": path_q_bytes / t_q / 1e9 / pk["hbm_gbs"],

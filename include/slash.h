@@ -107,6 +107,31 @@ int slash_insert(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols
 int slash_query(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n_queries,
                 uint32_t topk, int32_t *d_ids_out, uint32_t *d_scores_out, void *cuda_stream);
 
+/* Query schedules.  Both give bit-identical results. */
+#define SLASH_QUERY_FUSED 0u  /* one persistent launch: hash -> gather -> count -> top-k per CTA */
+#define SLASH_QUERY_PLAIN 1u  /* one launch per stage: hash kernel, then gather/count/top-k kernel */
+
+typedef struct {
+  uint32_t mode;         /* SLASH_QUERY_FUSED or SLASH_QUERY_PLAIN                     */
+  uint32_t threads;      /* threads per CTA: 256, 512 or 1024 (0 = 512)                  */
+  uint32_t ctas_per_sm;  /* cap on resident CTAs per SM (0 = as many as smem allows)     */
+} slash_query_opts;
+
+/* slash_query with an explicit schedule (opts == NULL: the index's default,
+ * initially {FUSED, 512, 0}, replaced by slash_autotune).  Same outputs and
+ * errors as slash_query; SLASH_EINVAL also when the schedule does not fit. */
+int slash_query_ex(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n_queries,
+                   uint32_t topk, int32_t *d_ids_out, uint32_t *d_scores_out, const slash_query_opts *opts,
+                   void *cuda_stream);
+
+/* Autotuner: time every query schedule (mode x threads x CTAs/SM) on the given
+ * sample batch (each twice after a warm-up, CUDA events on `cuda_stream`), make
+ * the fastest the index's default, and report it (*best_out, *best_ms_out may be
+ * NULL).  The outputs buffers receive the sample's results.  Synchronises. */
+int slash_autotune(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n_queries,
+                   uint32_t topk, int32_t *d_ids_out, uint32_t *d_scores_out, void *cuda_stream,
+                   slash_query_opts *best_out, float *best_ms_out);
+
 /* Release the index and its workspace (synchronises the device first).
  * NULL is accepted.  Always SLASH_OK unless a CUDA call fails. */
 int slash_free(slash_index *ix);

@@ -44,6 +44,18 @@ class SlashError(RuntimeError):
         super().__init__(f"{where}: {slash_strerror(code)} ({code})")
 
 
+SLASH_QUERY_FUSED = 0
+SLASH_QUERY_PLAIN = 1
+
+
+class slash_query_opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
+
+    def __repr__(self):
+        m = "fused" if self.mode == SLASH_QUERY_FUSED else "plain"
+        return f"slash_query_opts({m}, threads={self.threads}, ctas_per_sm={self.ctas_per_sm})"
+
+
 class slash_params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_uint32), ("K", ctypes.c_uint32), ("L", ctypes.c_uint32),
                 ("log2_buckets", ctypes.c_uint32), ("reservoir", ctypes.c_uint32),
@@ -73,6 +85,8 @@ def _load() -> ctypes.CDLL:
         "slash_debug_hash": (i32, [vp, vp, vp, u32, vp, vp, vp]),
         "slash_debug_export": (i32, [vp, vp, vp]),
         "slash_debug_buckets": (i32, [vp, vp, vp, vp, u32, vp, vp]),
+        "slash_query_ex": (i32, [vp, vp, vp, u32, u32, vp, vp, P(slash_query_opts), vp]),
+        "slash_autotune": (i32, [vp, vp, vp, u32, u32, vp, vp, vp, P(slash_query_opts), P(ctypes.c_float)]),
         "slash_profile": (i32, [vp, i32]),
         "slash_profile_read": (i32, [vp, u32, vp, vp, vp, P(u32), P(u64)]),
     }
@@ -157,9 +171,19 @@ def slash_insert(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, stream=Non
     return int(first.value)
 
 
+def _opts(mode, threads, ctas_per_sm):
+    if mode is None:
+        return None
+    m = {"fused": SLASH_QUERY_FUSED, "plain": SLASH_QUERY_PLAIN}.get(mode, mode)
+    return slash_query_opts(int(m), int(threads or 0), int(ctas_per_sm or 0))
+
+
 def slash_query(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, topk: int,
                 d_ids_out: torch.Tensor | None = None, d_scores_out: torch.Tensor | None = None,
-                stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+                stream=None, mode=None, threads: int = 0, ctas_per_sm: int = 0
+                ) -> tuple[torch.Tensor, torch.Tensor]:
+    """Algorithm 2 for a batch.  ``mode`` None = the index's default schedule,
+    else "fused" / "plain" (with optional ``threads`` and ``ctas_per_sm``)."""
     nq = d_offs.numel() - 1
     if nq < 0:
         raise ValueError("d_offs needs n+1 entries")
@@ -170,10 +194,28 @@ def slash_query(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, topk: int,
         d_scores_out = torch.empty((nq, topk), dtype=torch.int32, device=dev)
     if d_ids_out.numel() < nq * topk or d_scores_out.numel() < nq * topk:
         raise ValueError("output tensors too small")
-    _check(_lib.slash_query(ix, _dev_ptr(d_offs, 8, "d_offs"), _dev_ptr(d_cols, 4, "d_cols"), nq, topk,
-                            _dev_ptr(d_ids_out, 4, "d_ids_out"), _dev_ptr(d_scores_out, 4, "d_scores_out"),
-                            _stream(stream)), "slash_query")
+    o = _opts(mode, threads, ctas_per_sm)
+    args = (ix, _dev_ptr(d_offs, 8, "d_offs"), _dev_ptr(d_cols, 4, "d_cols"), nq, topk,
+            _dev_ptr(d_ids_out, 4, "d_ids_out"), _dev_ptr(d_scores_out, 4, "d_scores_out"))
+    if o is None:
+        _check(_lib.slash_query(*args, _stream(stream)), "slash_query")
+    else:
+        _check(_lib.slash_query_ex(*args, ctypes.byref(o), _stream(stream)), "slash_query_ex")
     return d_ids_out, d_scores_out
+
+
+def slash_autotune(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, topk: int, stream=None):
+    """Time every query schedule on this sample batch; the fastest becomes the
+    index default.  Returns (opts, best ms)."""
+    nq = d_offs.numel() - 1
+    ids = torch.empty((nq, topk), dtype=torch.int32, device=d_offs.device)
+    sc = torch.empty_like(ids)
+    best = slash_query_opts()
+    ms = ctypes.c_float()
+    _check(_lib.slash_autotune(ix, _dev_ptr(d_offs, 8, "d_offs"), _dev_ptr(d_cols, 4, "d_cols"), nq, topk,
+                               ids.data_ptr(), sc.data_ptr(), _stream(stream), ctypes.byref(best),
+                               ctypes.byref(ms)), "slash_autotune")
+    return best, float(ms.value)
 
 
 def slash_free(ix: int) -> None:
@@ -205,13 +247,14 @@ def slash_debug_hash(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, nb: in
     return codes, bk
 
 
-def slash_debug_export(ix: int, p: Params):
+def slash_debug_export(ix: int, p: Params, fill_only: bool = False):
     import numpy as np
     nk = p.shards * p.L << p.log2_buckets
-    slots = np.empty(nk * p.reservoir, dtype=np.uint32)
+    slots = None if fill_only else np.empty(nk * p.reservoir, dtype=np.uint32)
     fill = np.empty(nk, dtype=np.uint32)
-    _check(_lib.slash_debug_export(ix, slots.ctypes.data, fill.ctypes.data), "slash_debug_export")
-    return (slots.reshape(p.shards, p.L, 1 << p.log2_buckets, p.reservoir),
+    _check(_lib.slash_debug_export(ix, None if slots is None else slots.ctypes.data, fill.ctypes.data),
+           "slash_debug_export")
+    return (None if slots is None else slots.reshape(p.shards, p.L, 1 << p.log2_buckets, p.reservoir),
             fill.reshape(p.shards, p.L, 1 << p.log2_buckets))
 
 
@@ -262,6 +305,9 @@ class Index:
     def query(self, d_offs, d_cols, topk: int, stream=None, **kw):
         return slash_query(self.h, d_offs, d_cols, topk, stream=stream, **kw)
 
+    def autotune(self, d_offs, d_cols, topk: int, stream=None):
+        return slash_autotune(self.h, d_offs, d_cols, topk, stream)
+
     def sync(self, stream=None) -> None:
         _check(slash_sync(self.h, stream), "slash_sync")
 
@@ -272,8 +318,8 @@ class Index:
     def size(self) -> int:
         return slash_size(self.h)
 
-    def export(self):
-        return slash_debug_export(self.h, self.p)
+    def export(self, fill_only: bool = False):
+        return slash_debug_export(self.h, self.p, fill_only)
 
     def buckets(self, shard, table, bucket):
         return slash_debug_buckets(self.h, self.p, shard, table, bucket)

@@ -477,24 +477,31 @@ k_merge_big(const __grid_constant__ Geo g, const uint32_t* __restrict__ off,
 }
 
 // ----------------------------------------------------------------------------- query
-constexpr int kQueryThreads = 512;
 constexpr uint32_t kHistBins = 256;  // estimate histogram; the last bin holds est >= 255
+constexpr int kGatherUnroll = 4;     // 32-id chunks a warp loads before counting them
 
-enum { C_NDIST = 0, C_NTOP, C_ESTAR, C_M, C_TIE, C_CAP, C_PREFIX_LO, C_PREFIX_HI, C_NEED, C_N };
+enum { C_NDIST = 0, C_NTOP, C_ESTAR, C_M, C_TIE, C_CAP, C_PREFIX_LO, C_PREFIX_HI, C_NEED, C_NCHUNK, C_ANY,
+       C_Q, C_N };
 
+// Shared-memory carve-up of one query (byte offsets), fixed per index and k.
 struct QueryLayout {
-  uint32_t H, hbits;      // hash-set slots (power of two) and log2
-  uint32_t topn;          // top buffer entries (power of two >= k)
-  uint32_t off_cm, off_set, off_hist, off_ctrl, off_est, bytes;
+  uint32_t H, hbits;   // hash-set slots (power of two >= 2 * max candidates) and log2
+  uint32_t maxm;       // max candidate occurrences S*L*R (= max distinct ids)
+  uint32_t nbk;        // buckets per query, S*L
+  uint32_t topn;       // top buffer entries (power of two >= k)
+  uint32_t off_top, off_cm, off_set, off_ulist, off_bkey, off_bfill, off_cpre, off_m, off_mask, off_hist,
+      off_ctrl, off_est, bytes;
 };
 
-__device__ __forceinline__ void set_insert(uint32_t* set, uint32_t H, uint32_t hbits, uint32_t id) {
+__device__ __forceinline__ bool set_insert(uint32_t* set, uint32_t H, uint32_t hbits, uint32_t id) {
   uint32_t i = (id * kGold32) >> (32u - hbits);
   for (uint32_t probe = 0; probe < H; ++probe) {
     const uint32_t old = atomicCAS(&set[i], kEmpty, id);
-    if (old == kEmpty || old == id) return;
+    if (old == kEmpty) return true;
+    if (old == id) return false;
     i = (i + 1u) & (H - 1u);
   }
+  return false;
 }
 
 // 16-bit counters packed two per 32-bit word (exact: no cell exceeds S*L*R <= 65535)
@@ -510,9 +517,39 @@ __device__ __forceinline__ uint64_t rank_key(uint32_t est, uint32_t id) {
   return ((uint64_t)(0xFFFFu - est) << 32) | id;
 }
 
-// Block-wide: among set entries with bin(est) == estar, the m-th smallest key
-// (key = id, or rank_key when the bin is the capped one).  Uses hist[0..256).
-__device__ uint64_t tie_select(const uint32_t* set, const uint16_t* est, uint32_t H, uint32_t estar,
+// warp 0 helper: digit holding the need-th smallest count of hist[0..256)
+// (lane l holds bins 8l..8l+7); writes the new prefix/need into ctrl
+__device__ __forceinline__ void pick_digit(const uint32_t* hist, uint32_t need, uint64_t prefix, int sh,
+                                           uint32_t* ctrl, uint32_t lane) {
+  uint32_t v[8], sum = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) { v[i] = hist[lane * 8 + i]; sum += v[i]; }
+  uint32_t inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= (uint32_t)o) inc += u;
+  }
+  const uint32_t ex = inc - sum;
+  if (ex < need && need <= inc) {
+    uint32_t cum = ex;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if (cum + v[i] >= need) {
+        const uint64_t np = prefix | ((uint64_t)(lane * 8u + i) << sh);
+        ctrl[C_PREFIX_LO] = (uint32_t)np;
+        ctrl[C_PREFIX_HI] = (uint32_t)(np >> 32);
+        ctrl[C_NEED] = need - cum;
+        break;
+      }
+      cum += v[i];
+    }
+  }
+}
+
+// Block-wide: among distinct candidates whose estimate bin is estar, the m-th
+// smallest key (key = id, or rank_key when estar is the capped bin).
+__device__ uint64_t tie_select(const uint32_t* ulist, const uint16_t* est, uint32_t nd, uint32_t estar,
                                bool capped, uint32_t m, uint32_t* hist, uint32_t* ctrl) {
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   uint64_t prefix = 0;
@@ -521,41 +558,14 @@ __device__ uint64_t tie_select(const uint32_t* set, const uint16_t* est, uint32_
   for (int sh = top - 8; sh >= 0; sh -= 8) {
     for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
-      const uint32_t id = set[i];
-      if (id == kEmpty) continue;
+    for (uint32_t i = threadIdx.x; i < nd; i += blockDim.x) {
       const uint32_t e = est[i];
       if (min(e, kHistBins - 1u) != estar) continue;
-      const uint64_t k = capped ? rank_key(e, id) : (uint64_t)id;
-      if ((k >> (sh + 8)) == (prefix >> (sh + 8))) atomicAdd(&hist[(k >> sh) & 255u], 1u);
+      const uint64_t kk = capped ? rank_key(e, ulist[i]) : (uint64_t)ulist[i];
+      if ((kk >> (sh + 8)) == (prefix >> (sh + 8))) atomicAdd(&hist[(kk >> sh) & 255u], 1u);
     }
     __syncthreads();
-    if (warp == 0) {
-      uint32_t v[8], sum = 0;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) { v[i] = hist[lane * 8 + i]; sum += v[i]; }
-      uint32_t inc = sum;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-        if (lane >= (uint32_t)o) inc += u;
-      }
-      const uint32_t ex = inc - sum;
-      if (ex < need && need <= inc) {
-        uint32_t cum = ex;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          if (cum + v[i] >= need) {
-            const uint64_t np = prefix | ((uint64_t)(lane * 8u + i) << sh);
-            ctrl[C_PREFIX_LO] = (uint32_t)np;
-            ctrl[C_PREFIX_HI] = (uint32_t)(np >> 32);
-            ctrl[C_NEED] = need - cum;
-            break;
-          }
-          cum += v[i];
-        }
-      }
-    }
+    if (warp == 0) pick_digit(hist, need, prefix, sh, ctrl, lane);
     __syncthreads();
     prefix = ((uint64_t)ctrl[C_PREFIX_HI] << 32) | ctrl[C_PREFIX_LO];
     need = ctrl[C_NEED];
@@ -563,137 +573,244 @@ __device__ uint64_t tie_select(const uint32_t* set, const uint16_t* est, uint32_
   return prefix;
 }
 
-// One CTA per query (grid-stride).  qbkt[t*ldq + q]: the query's table addresses.
-__global__ void __launch_bounds__(kQueryThreads)
-k_query(const __grid_constant__ Geo g, const QueryLayout lay, const uint32_t* __restrict__ qbkt,
-        uint64_t ldq, uint32_t nq, uint32_t k, const uint32_t* __restrict__ slots,
-        const uint32_t* __restrict__ fill, int32_t* __restrict__ ids_out,
-        uint32_t* __restrict__ scores_out) {
-  extern __shared__ __align__(16) unsigned char qsm[];
-  uint64_t* top = reinterpret_cast<uint64_t*>(qsm);
+// exclusive scan of a[0..n) into out[0..n] (out[n] = total), whole CTA, n small
+__device__ __forceinline__ void block_scan_small(const uint32_t* a, uint32_t* out, uint32_t n, uint32_t* tmp) {
+  // each warp scans 32-element segments sequentially; segment totals chained by thread 0
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const uint32_t nseg = (n + 31u) / 32u;
+  for (uint32_t sg = warp; sg < nseg; sg += nwarp) {
+    const uint32_t i = sg * 32u + lane;
+    const uint32_t v = i < n ? a[i] : 0u;
+    uint32_t inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= (uint32_t)o) inc += u;
+    }
+    if (i < n) out[i] = inc - v;
+    if (lane == 31) tmp[sg] = inc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (uint32_t sg = 0; sg < nseg; ++sg) { const uint32_t t = tmp[sg]; tmp[sg] = run; run += t; }
+    out[n] = run;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) out[i] += tmp[i >> 5];
+  __syncthreads();
+}
+
+// Algorithm 2 for one query whose S*L bucket keys are in bkey[] (smem, synced):
+// gather every shard's L buckets into one count-min sketch (= the sum of the
+// shards' sketches), estimate each distinct candidate, write the top-k by
+// (estimate desc, id asc).
+__device__ void query_core(const Geo& g, const QueryLayout& lay, unsigned char* qsm,
+                           const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill,
+                           uint32_t k, int32_t* __restrict__ ids_out, uint32_t* __restrict__ scores_out) {
+  uint64_t* top = reinterpret_cast<uint64_t*>(qsm + lay.off_top);
   uint32_t* cmw = reinterpret_cast<uint32_t*>(qsm + lay.off_cm);
   uint32_t* set = reinterpret_cast<uint32_t*>(qsm + lay.off_set);
+  uint32_t* ulist = reinterpret_cast<uint32_t*>(qsm + lay.off_ulist);
+  const uint32_t* bkey = reinterpret_cast<const uint32_t*>(qsm + lay.off_bkey);
+  uint32_t* bfill = reinterpret_cast<uint32_t*>(qsm + lay.off_bfill);
+  uint32_t* cpre = reinterpret_cast<uint32_t*>(qsm + lay.off_cpre);
   uint32_t* hist = reinterpret_cast<uint32_t*>(qsm + lay.off_hist);
   uint32_t* ctrl = reinterpret_cast<uint32_t*>(qsm + lay.off_ctrl);
   uint16_t* est = reinterpret_cast<uint16_t*>(qsm + lay.off_est);
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const uint32_t H = lay.H, wmask = g.w - 1u, cmwords = (g.d * g.w) >> 1;
-  const uint32_t nbk = g.S * g.L;
-  for (uint32_t q = blockIdx.x; q < nq; q += gridDim.x) {
-    // -- clear the sketch, the set, the histogram
-    uint4* cm4 = reinterpret_cast<uint4*>(cmw);
-    for (uint32_t i = threadIdx.x; i < cmwords / 4; i += blockDim.x) cm4[i] = make_uint4(0, 0, 0, 0);
-    uint4* set4 = reinterpret_cast<uint4*>(set);
-    for (uint32_t i = threadIdx.x; i < H / 4; i += blockDim.x)
-      set4[i] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
-    for (uint32_t i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
-    if (threadIdx.x < C_N) ctrl[threadIdx.x] = 0u;
-    __syncthreads();
-    // -- Algorithm 2 merge: every shard's L buckets into one sketch
-    for (uint32_t it = warp; it < nbk; it += nwarp) {
-      const uint32_t s = it / g.L, t = it - s * g.L;
-      const uint32_t b = qbkt[t * ldq + q];
-      const uint64_t key = (((uint64_t)s * g.L + t) << g.B) | b;
-      const uint32_t f = fill[key];
-      const uint32_t* bs = slots + key * g.R;
-      for (uint32_t j = lane; j < f; j += 32) {
-        const uint32_t id = __ldg(bs + j);
-        for (uint32_t r = 0; r < g.d; ++r) cm_add(cmw, r * g.w + cm_cell(id, g.sc[r], wmask));
-        set_insert(set, H, lay.hbits, id);
+  const uint32_t H = lay.H, wmask = g.w - 1u, cmwords = (g.d * g.w) >> 1, nbk = lay.nbk;
+  // -- clear the sketch and the set; fetch the fill of every bucket (chunks of 32 ids)
+  uint4* cm4 = reinterpret_cast<uint4*>(cmw);
+  for (uint32_t i = threadIdx.x; i < cmwords / 4; i += blockDim.x) cm4[i] = make_uint4(0, 0, 0, 0);
+  uint4* set4 = reinterpret_cast<uint4*>(set);
+  for (uint32_t i = threadIdx.x; i < H / 4; i += blockDim.x) set4[i] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+  for (uint32_t i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
+  if (threadIdx.x < C_Q) ctrl[threadIdx.x] = 0u;
+  for (uint32_t i = threadIdx.x; i < nbk; i += blockDim.x) bfill[i] = (fill[bkey[i]] + 31u) >> 5;
+  __syncthreads();
+  block_scan_small(bfill, cpre, nbk, hist);   // chunk prefix; hist used as scratch
+  for (uint32_t i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
+  const uint32_t nchunk = cpre[nbk];
+  // -- merge: warps take 32-id chunks, kGatherUnroll loads in flight per lane
+  for (uint32_t c0 = warp * kGatherUnroll; c0 < nchunk; c0 += nwarp * kGatherUnroll) {
+    uint32_t idv[kGatherUnroll];
+#pragma unroll
+    for (int u = 0; u < kGatherUnroll; ++u) {
+      idv[u] = kEmpty;
+      const uint32_t c = c0 + u;
+      if (c < nchunk) {
+        uint32_t lo = 0, hi = nbk;  // bucket with cpre[b] <= c < cpre[b+1]
+        while (hi - lo > 1) { const uint32_t mid = (lo + hi) >> 1; if (cpre[mid] <= c) lo = mid; else hi = mid; }
+        const uint32_t key = bkey[lo];
+        const uint32_t j = (c - cpre[lo]) * 32u + lane;
+        if (j < fill[key]) idv[u] = __ldg(slots + (uint64_t)key * g.R + j);
       }
     }
-    __syncthreads();
-    // -- estimate of every distinct candidate, histogram of estimates
-    for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
-      const uint32_t id = set[i];
+#pragma unroll
+    for (int u = 0; u < kGatherUnroll; ++u) {
+      const uint32_t id = idv[u];
       if (id == kEmpty) continue;
-      uint32_t e = 0xFFFFu;
-      for (uint32_t r = 0; r < g.d; ++r) e = min(e, cm_get(cmw, r * g.w + cm_cell(id, g.sc[r], wmask)));
-      est[i] = (uint16_t)e;
-      atomicAdd(&hist[min(e, kHistBins - 1u)], 1u);
-      atomicAdd(&ctrl[C_NDIST], 1u);
+      for (uint32_t r = 0; r < g.d; ++r) cm_add(cmw, r * g.w + cm_cell(id, g.sc[r], wmask));
+      if (set_insert(set, H, lay.hbits, id)) ulist[atomicAdd(&ctrl[C_NDIST], 1u)] = id;
     }
-    __syncthreads();
-    // -- threshold bin: fewer than k candidates above it, at least k at or above it
-    if (warp == 0) {
-      const uint32_t total = ctrl[C_NDIST];
-      if (total <= k) {
-        if (lane == 0) { ctrl[C_ESTAR] = 0u; ctrl[C_M] = 0u; ctrl[C_TIE] = 0u; ctrl[C_CAP] = 0u; }
-      } else {
-        // lane l holds bins [255-8l-7, 255-8l], walked from the top
-        uint32_t v[8], sum = 0;
+  }
+  __syncthreads();
+  const uint32_t nd = ctrl[C_NDIST];
+  // -- estimate of every distinct candidate; histogram of estimates
+  for (uint32_t i = threadIdx.x; i < nd; i += blockDim.x) {
+    const uint32_t id = ulist[i];
+    uint32_t e = 0xFFFFu;
+    for (uint32_t r = 0; r < g.d; ++r) e = min(e, cm_get(cmw, r * g.w + cm_cell(id, g.sc[r], wmask)));
+    est[i] = (uint16_t)e;
+    atomicAdd(&hist[min(e, kHistBins - 1u)], 1u);
+  }
+  __syncthreads();
+  // -- threshold bin: fewer than k candidates above it, at least k at or above it
+  if (warp == 0) {
+    if (nd <= k) {
+      if (lane == 0) { ctrl[C_ESTAR] = 0u; ctrl[C_M] = 0u; ctrl[C_TIE] = 0u; ctrl[C_CAP] = 0u; }
+    } else {
+      uint32_t v[8], sum = 0;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) { v[i] = hist[kHistBins - 1u - (lane * 8u + i)]; sum += v[i]; }
-        uint32_t inc = sum;
+      for (int i = 0; i < 8; ++i) { v[i] = hist[kHistBins - 1u - (lane * 8u + i)]; sum += v[i]; }
+      uint32_t inc = sum;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-          if (lane >= (uint32_t)o) inc += u;
-        }
-        const uint32_t ex = inc - sum;
-        if (ex < k && k <= inc) {
-          uint32_t cum = ex;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= (uint32_t)o) inc += u;
+      }
+      const uint32_t ex = inc - sum;
+      if (ex < k && k <= inc) {
+        uint32_t cum = ex;
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            if (cum + v[i] >= k) {
-              const uint32_t bin = kHistBins - 1u - (lane * 8u + i);
-              ctrl[C_ESTAR] = bin;
-              ctrl[C_M] = k - cum;
-              ctrl[C_TIE] = v[i];
-              ctrl[C_CAP] = bin == kHistBins - 1u;
-              break;
-            }
-            cum += v[i];
+        for (int i = 0; i < 8; ++i) {
+          if (cum + v[i] >= k) {
+            const uint32_t bin = kHistBins - 1u - (lane * 8u + i);
+            ctrl[C_ESTAR] = bin;
+            ctrl[C_M] = k - cum;
+            ctrl[C_TIE] = v[i];
+            ctrl[C_CAP] = bin == kHistBins - 1u;
+            break;
           }
+          cum += v[i];
         }
       }
     }
-    __syncthreads();
-    const uint32_t estar = ctrl[C_ESTAR], m = ctrl[C_M], tie = ctrl[C_TIE];
-    const bool capped = ctrl[C_CAP] != 0u;
-    // -- candidates strictly above the threshold bin (fewer than k; all when total <= k)
-    for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
-      const uint32_t id = set[i];
-      if (id == kEmpty) continue;
+  }
+  __syncthreads();
+  const uint32_t estar = ctrl[C_ESTAR], m = ctrl[C_M], tie = ctrl[C_TIE];
+  const bool capped = ctrl[C_CAP] != 0u;
+  // -- candidates strictly above the threshold bin (fewer than k; all of them when nd <= k)
+  for (uint32_t i = threadIdx.x; i < nd; i += blockDim.x) {
+    const uint32_t e = est[i];
+    if (min(e, kHistBins - 1u) > estar) {
+      const uint32_t pos = atomicAdd(&ctrl[C_NTOP], 1u);
+      if (pos < lay.topn) top[pos] = rank_key(e, ulist[i]);
+    }
+  }
+  // -- the m best of the threshold bin
+  if (m > 0) {
+    uint64_t thr = ~0ull;
+    if (tie > m) thr = tie_select(ulist, est, nd, estar, capped, m, hist, ctrl);
+    for (uint32_t i = threadIdx.x; i < nd; i += blockDim.x) {
       const uint32_t e = est[i];
-      if (min(e, kHistBins - 1u) > estar) {
+      if (min(e, kHistBins - 1u) != estar) continue;
+      const uint64_t kk = capped ? rank_key(e, ulist[i]) : (uint64_t)ulist[i];
+      if (kk <= thr) {
         const uint32_t pos = atomicAdd(&ctrl[C_NTOP], 1u);
-        if (pos < lay.topn) top[pos] = rank_key(e, id);
+        if (pos < lay.topn) top[pos] = rank_key(e, ulist[i]);
       }
     }
-    // -- the m best of the threshold bin
-    if (m > 0) {
-      uint64_t thr = ~0ull;
-      if (tie > m) thr = tie_select(set, est, H, estar, capped, m, hist, ctrl);
-      for (uint32_t i = threadIdx.x; i < H; i += blockDim.x) {
-        const uint32_t id = set[i];
-        if (id == kEmpty) continue;
-        const uint32_t e = est[i];
-        if (min(e, kHistBins - 1u) != estar) continue;
-        const uint64_t kk = capped ? rank_key(e, id) : (uint64_t)id;
-        if (kk <= thr) {
-          const uint32_t pos = atomicAdd(&ctrl[C_NTOP], 1u);
-          if (pos < lay.topn) top[pos] = rank_key(e, id);
+  }
+  __syncthreads();
+  const uint32_t ntop = min(ctrl[C_NTOP], k);
+  const uint32_t n2 = max(2u, next_pow2(ntop));
+  for (uint32_t i = ntop + threadIdx.x; i < n2; i += blockDim.x) top[i] = ~0ull;
+  __syncthreads();
+  block_bitonic(top, n2);
+  for (uint32_t j = threadIdx.x; j < k; j += blockDim.x) {
+    if (j < ntop) {
+      ids_out[j] = (int32_t)(uint32_t)top[j];
+      scores_out[j] = 0xFFFFu - (uint32_t)(top[j] >> 32);
+    } else {
+      ids_out[j] = -1;
+      scores_out[j] = 0u;
+    }
+  }
+  __syncthreads();
+}
+
+// Plain path: one CTA per query (grid-stride); addresses from k_hash, qbkt[t*ldq + q].
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads)
+k_query(const __grid_constant__ Geo g, const QueryLayout lay, const uint32_t* __restrict__ qbkt, uint64_t ldq,
+        uint32_t nq, uint32_t k, const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill,
+        int32_t* __restrict__ ids_out, uint32_t* __restrict__ scores_out) {
+  extern __shared__ __align__(16) unsigned char qsm[];
+  uint32_t* bkey = reinterpret_cast<uint32_t*>(qsm + lay.off_bkey);
+  for (uint32_t q = blockIdx.x; q < nq; q += gridDim.x) {
+    for (uint32_t it = threadIdx.x; it < lay.nbk; it += blockDim.x) {
+      const uint32_t s = it / g.L, t = it - s * g.L;
+      bkey[it] = ((s * g.L + t) << g.B) | qbkt[t * ldq + q];
+    }
+    __syncthreads();
+    query_core(g, lay, qsm, slots, fill, k, ids_out + (uint64_t)q * k, scores_out + (uint64_t)q * k);
+  }
+}
+
+// Fused path: persistent CTAs pull queries from a work counter; each query is
+// hashed (DOPH, densification, L addresses) by the whole CTA in smem and then
+// answered by query_core -- no intermediate HBM traffic, one launch per batch.
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads)
+k_query_fused(const __grid_constant__ Geo g, const QueryLayout lay, const uint64_t* __restrict__ offs,
+              const uint32_t* __restrict__ cols, uint32_t nq, uint32_t k, const uint32_t* __restrict__ slots,
+              const uint32_t* __restrict__ fill, int32_t* __restrict__ ids_out,
+              uint32_t* __restrict__ scores_out, uint32_t* __restrict__ work, uint32_t* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char qsm[];
+  uint32_t* bkey = reinterpret_cast<uint32_t*>(qsm + lay.off_bkey);
+  uint32_t* m = reinterpret_cast<uint32_t*>(qsm + lay.off_m);
+  uint32_t* mask = reinterpret_cast<uint32_t*>(qsm + lay.off_mask);
+  uint32_t* ctrl = reinterpret_cast<uint32_t*>(qsm + lay.off_ctrl);
+  for (;;) {
+    if (threadIdx.x == 0) ctrl[C_Q] = atomicAdd(work, 1u);
+    for (uint32_t j = threadIdx.x; j < g.nb; j += blockDim.x) m[j] = kEmpty;
+    if (threadIdx.x < g.nw) mask[threadIdx.x] = 0u;
+    __syncthreads();
+    const uint32_t q = ctrl[C_Q];
+    if (q >= nq) break;
+    uint64_t b0 = offs[q], b1 = offs[q + 1];
+    if (b1 < b0) {
+      if (threadIdx.x == 0) atomicOr(err, kErrOffs);
+      b1 = b0;
+    }
+    bool bad = false;
+    for (uint64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+      const uint32_t f = __ldg(cols + i);
+      if (f >= g.dim) { bad = true; continue; }
+      const uint32_t h = mix32(f ^ g.a);
+      const uint32_t bin = __umulhi(h, g.nb);
+      atomicMin(&m[bin], h);
+      atomicOr(&mask[bin >> 5], 1u << (bin & 31u));
+    }
+    if (bad) atomicOr(err, kErrCol);
+    const int any = __syncthreads_or(threadIdx.x < g.nw && mask[threadIdx.x] != 0u);
+    if (any) {
+      for (uint32_t j = threadIdx.x; j < g.nb; j += blockDim.x) {
+        if (!((mask[j >> 5] >> (j & 31u)) & 1u)) {
+          const bool right = (g.dirbits[j >> 5] >> (j & 31u)) & 1u;
+          m[j] = m[nearest_bin(mask, g.nw, j, right)];
         }
       }
     }
     __syncthreads();
-    const uint32_t ntop = min(ctrl[C_NTOP], k);
-    const uint32_t n2 = max(2u, next_pow2(ntop));
-    for (uint32_t i = ntop + threadIdx.x; i < n2; i += blockDim.x) top[i] = ~0ull;
-    __syncthreads();
-    block_bitonic(top, n2);
-    for (uint32_t j = threadIdx.x; j < k; j += blockDim.x) {
-      const uint64_t o = (uint64_t)q * k + j;
-      if (j < ntop) {
-        ids_out[o] = (int32_t)(uint32_t)top[j];
-        scores_out[o] = 0xFFFFu - (uint32_t)(top[j] >> 32);
-      } else {
-        ids_out[o] = -1;
-        scores_out[o] = 0u;
-      }
+    for (uint32_t it = threadIdx.x; it < lay.nbk; it += blockDim.x) {
+      const uint32_t s = it / g.L, t = it - s * g.L;
+      bkey[it] = ((s * g.L + t) << g.B) | table_address(g, m, t);
     }
     __syncthreads();
+    query_core(g, lay, qsm, slots, fill, k, ids_out + (uint64_t)q * k, scores_out + (uint64_t)q * k);
   }
 }
 
@@ -732,8 +849,8 @@ struct slash_index {
   // query workspace (grow-only)
   uint64_t qws = 0;
   uint32_t* qbkt = nullptr;
-  QueryLayout qlay{};
-  int query_blocks_per_sm = 0;
+  slash_query_opts qdef{SLASH_QUERY_FUSED, 512, 0};  // default query schedule (autotuned)
+  uint32_t* work = nullptr;                          // fused-kernel work counter
   // per-launch event profile (off unless slash_profile enables it)
   struct ProfRec { const char* name; cudaEvent_t a, b; };
   bool prof_on = false;
@@ -839,34 +956,36 @@ ShardMap shard_map(const slash_index* ix) {
   return m;
 }
 
-QueryLayout make_query_layout(const slash_params& p) {
+QueryLayout make_query_layout(const slash_params& p, uint32_t k) {
   QueryLayout l{};
-  const uint64_t maxm = (uint64_t)p.shards * p.L * p.reservoir;
+  const uint32_t maxm = p.shards * p.L * p.reservoir;  // <= 65535 (checked at build)
   uint32_t H = 64;
-  while (H < 2 * maxm) H <<= 1;
+  while (H < 2u * maxm) H <<= 1;
   l.H = H;
   l.hbits = 0;
   while ((1u << l.hbits) < H) ++l.hbits;
-  l.topn = 0;  // set per call (k)
-  return l;
-}
-
-void finish_layout(QueryLayout* l, const slash_params& p, uint32_t k) {
+  l.maxm = maxm;
+  l.nbk = p.shards * p.L;
   uint32_t topn = 2;
   while (topn < k) topn <<= 1;
-  l->topn = topn;
-  uint32_t o = topn * 8u;
-  l->off_cm = o;
-  o += (p.cm_rows * p.cm_width / 2u) * 4u;
-  l->off_set = o;
-  o += l->H * 4u;
-  l->off_hist = o;
-  o += kHistBins * 4u;
-  l->off_ctrl = o;
-  o += 16u * 4u;
-  l->off_est = o;
-  o += l->H * 2u;
-  l->bytes = (o + 15u) & ~15u;
+  l.topn = topn;
+  const uint32_t nb = p.K * p.L, nw = (nb + 31) / 32;
+  auto al = [](uint32_t x) { return (x + 15u) & ~15u; };
+  uint32_t o = 0;
+  l.off_top = o;   o = al(o + topn * 8u);
+  l.off_cm = o;    o = al(o + (p.cm_rows * p.cm_width / 2u) * 4u);
+  l.off_set = o;   o = al(o + H * 4u);
+  l.off_ulist = o; o = al(o + maxm * 4u);
+  l.off_bkey = o;  o = al(o + l.nbk * 4u);
+  l.off_bfill = o; o = al(o + l.nbk * 4u);
+  l.off_cpre = o;  o = al(o + (l.nbk + 1u) * 4u);
+  l.off_m = o;     o = al(o + nb * 4u);
+  l.off_mask = o;  o = al(o + nw * 4u);
+  l.off_hist = o;  o = al(o + kHistBins * 4u);
+  l.off_ctrl = o;  o = al(o + 16u * 4u);
+  l.off_est = o;   o = al(o + maxm * 2u);
+  l.bytes = o;
+  return l;
 }
 
 int run_hash(slash_index* ix, const uint64_t* offs, const uint32_t* cols, uint32_t n, uint64_t id0,
@@ -991,10 +1110,8 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
   for (uint32_t j = 0; j < g.nb; ++j)
     if (mix32(j ^ g.dirseed) & 1u) g.dirbits[j >> 5] |= 1u << (j & 31u);
   ix->nk = ((uint64_t)p->shards * p->L) << p->log2_buckets;
-  ix->qlay = make_query_layout(*p);
   {
-    QueryLayout l = ix->qlay;
-    finish_layout(&l, *p, SLASH_MAX_TOPK);
+    const QueryLayout l = make_query_layout(*p, SLASH_MAX_TOPK);
     if (l.bytes > ix->smem_optin || hash_smem(ix) > ix->smem_optin) { delete ix; return SLASH_EINVAL; }
   }
   const uint64_t nblk = (ix->nk + kScanTile - 1) / kScanTile;
@@ -1006,6 +1123,7 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
   if (e == cudaSuccess) e = cudaMalloc(&ix->blocksum, sizeof(uint64_t) * nblk);
   if (e == cudaSuccess) e = cudaMalloc(&ix->err, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&ix->big_count, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&ix->work, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemsetAsync(ix->slots, 0xFF, sizeof(uint32_t) * ix->nk * p->reservoir, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ix->fill, 0, sizeof(uint32_t) * ix->nk, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ix->cnt, 0, sizeof(uint32_t) * ix->nk, st);
@@ -1017,7 +1135,13 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
     slash_free(ix);
     return rc;
   }
-  cudaFuncSetAttribute(k_query, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ix->smem_optin);
+  const int so = (int)ix->smem_optin;
+  cudaFuncSetAttribute(k_query<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_query<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_query<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_query_fused<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_query_fused<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_query_fused<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_hash<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ix->smem_optin);
   cudaFuncSetAttribute(k_hash<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ix->smem_optin);
   *out = ix;
@@ -1048,30 +1172,105 @@ int slash_insert(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_cols
   return SLASH_OK;
 }
 
-int slash_query(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_cols, uint32_t n_queries,
-                uint32_t topk, int32_t* d_ids_out, uint32_t* d_scores_out, void* cuda_stream) {
+int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_cols, uint32_t n_queries,
+                   uint32_t topk, int32_t* d_ids_out, uint32_t* d_scores_out, const slash_query_opts* opts,
+                   void* cuda_stream) {
   if (!ix || topk == 0 || topk > SLASH_MAX_TOPK) return SLASH_EINVAL;
+  const slash_query_opts o = opts ? *opts : ix->qdef;
+  if (o.mode != SLASH_QUERY_PLAIN && o.mode != SLASH_QUERY_FUSED) return SLASH_EINVAL;
+  const uint32_t thr = o.threads ? o.threads : 512u;
+  if (thr != 256u && thr != 512u && thr != 1024u) return SLASH_EINVAL;
   if (n_queries == 0) return SLASH_OK;
   if (!d_offs || !d_cols || !d_ids_out || !d_scores_out) return SLASH_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  const QueryLayout lay = make_query_layout(ix->p, topk);
+  const void* fn = nullptr;
+  if (o.mode == SLASH_QUERY_PLAIN)
+    fn = thr == 256 ? (const void*)k_query<256> : thr == 512 ? (const void*)k_query<512> : (const void*)k_query<1024>;
+  else
+    fn = thr == 256 ? (const void*)k_query_fused<256>
+                    : thr == 512 ? (const void*)k_query_fused<512> : (const void*)k_query_fused<1024>;
+  int bps = 0;
+  SLASH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, (int)thr, lay.bytes));
+  if (bps < 1) return SLASH_EINVAL;
+  if (o.ctas_per_sm) bps = std::min<int>(bps, (int)o.ctas_per_sm);
+  const uint64_t slots_per_gpu = (uint64_t)ix->num_sms * bps;
+  if (o.mode == SLASH_QUERY_FUSED) {
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(n_queries, slots_per_gpu);
+    SLASH_CK(cudaMemsetAsync(ix->work, 0, sizeof(uint32_t), st));
+    Launch lq(ix, "k_query_fused", st);
+#define SLASH_FUSED(T)                                                                                \
+  k_query_fused<T><<<grid, T, lay.bytes, st>>>(ix->geo, lay, d_offs, d_cols, n_queries, topk, ix->slots, \
+                                               ix->fill, d_ids_out, d_scores_out, ix->work, ix->err)
+    if (thr == 256) SLASH_FUSED(256); else if (thr == 512) SLASH_FUSED(512); else SLASH_FUSED(1024);
+#undef SLASH_FUSED
+    SLASH_CK(cudaGetLastError());
+    return SLASH_OK;
+  }
   const uint64_t chunk = std::min<uint64_t>(n_queries, 1ull << 22);
   int rc = grow_query_ws(ix, chunk);
   if (rc) return rc;
-  QueryLayout lay = ix->qlay;
-  finish_layout(&lay, ix->p, topk);
-  int bps = 0;
-  SLASH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_query, kQueryThreads, lay.bytes));
-  if (bps < 1) return SLASH_EINVAL;
   for (uint64_t q0 = 0; q0 < n_queries; q0 += chunk) {
     const uint32_t n = (uint32_t)std::min<uint64_t>(chunk, n_queries - q0);
     rc = run_hash(ix, d_offs + q0, d_cols, n, 0, ix->qbkt, n, nullptr, false, st);
     if (rc) return rc;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>(n, (uint64_t)ix->num_sms * bps);
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(n, slots_per_gpu);
     Launch lq(ix, "k_query", st);
-    k_query<<<grid, kQueryThreads, lay.bytes, st>>>(ix->geo, lay, ix->qbkt, n, n, topk, ix->slots, ix->fill,
-                                                    d_ids_out + q0 * topk, d_scores_out + q0 * topk);
+#define SLASH_PLAIN(T)                                                                                 \
+  k_query<T><<<grid, T, lay.bytes, st>>>(ix->geo, lay, ix->qbkt, n, n, topk, ix->slots, ix->fill,     \
+                                         d_ids_out + q0 * topk, d_scores_out + q0 * topk)
+    if (thr == 256) SLASH_PLAIN(256); else if (thr == 512) SLASH_PLAIN(512); else SLASH_PLAIN(1024);
+#undef SLASH_PLAIN
     SLASH_CK(cudaGetLastError());
   }
+  return SLASH_OK;
+}
+
+int slash_query(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_cols, uint32_t n_queries,
+                uint32_t topk, int32_t* d_ids_out, uint32_t* d_scores_out, void* cuda_stream) {
+  return slash_query_ex(ix, d_offs, d_cols, n_queries, topk, d_ids_out, d_scores_out, nullptr, cuda_stream);
+}
+
+int slash_autotune(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_cols, uint32_t n_queries,
+                   uint32_t topk, int32_t* d_ids_out, uint32_t* d_scores_out, void* cuda_stream,
+                   slash_query_opts* best_out, float* best_ms_out) {
+  if (!ix || n_queries == 0) return SLASH_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const uint32_t modes[2] = {SLASH_QUERY_FUSED, SLASH_QUERY_PLAIN};
+  const uint32_t threads[3] = {256, 512, 1024};
+  cudaEvent_t a, b;
+  SLASH_CK(cudaEventCreate(&a));
+  SLASH_CK(cudaEventCreate(&b));
+  slash_query_opts best{SLASH_QUERY_FUSED, 512, 0};
+  float best_ms = 3.4e38f;
+  int rc = SLASH_OK;
+  for (uint32_t m : modes) {
+    for (uint32_t t : threads) {
+      for (uint32_t cps = 0; cps <= 1; ++cps) {  // 0 = as many CTAs per SM as fit, 1 = one
+        slash_query_opts o{m, t, cps};
+        float ms = 3.4e38f;
+        for (int rep = 0; rep < 3 && rc == SLASH_OK; ++rep) {
+          cudaEventRecord(a, st);
+          rc = slash_query_ex(ix, d_offs, d_cols, n_queries, topk, d_ids_out, d_scores_out, &o, st);
+          cudaEventRecord(b, st);
+          if (rc == SLASH_EINVAL) break;  // this schedule does not fit (e.g. shared memory)
+          if (cudaEventSynchronize(b) != cudaSuccess) { rc = SLASH_ECUDA; break; }
+          float t_ms = 0.f;
+          cudaEventElapsedTime(&t_ms, a, b);
+          if (rep > 0) ms = std::min(ms, t_ms);
+        }
+        if (rc == SLASH_EINVAL) { rc = SLASH_OK; continue; }
+        if (rc != SLASH_OK) break;
+        if (ms < best_ms) { best_ms = ms; best = o; }
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc != SLASH_OK) return rc;
+  ix->qdef = best;
+  if (best_out) *best_out = best;
+  if (best_ms_out) *best_ms_out = best_ms;
   return SLASH_OK;
 }
 
@@ -1081,6 +1280,7 @@ int slash_free(slash_index* ix) {
   cudaFree(ix->slots); cudaFree(ix->fill); cudaFree(ix->err);
   cudaFree(ix->bkt); cudaFree(ix->stage); cudaFree(ix->cnt); cudaFree(ix->off);
   cudaFree(ix->blocksum); cudaFree(ix->big_keys); cudaFree(ix->big_count); cudaFree(ix->qbkt);
+  cudaFree(ix->work);
   for (auto& r : ix->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ix->prof_pool) cudaEventDestroy(e);
   delete ix;

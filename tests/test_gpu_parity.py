@@ -238,3 +238,52 @@ def test_argument_errors():
         assert ix.size == 0
         slots, fill = ix.export()
         assert fill.max() == 0 and np.all(slots == EMPTY)
+
+
+@pytest.mark.parametrize("shards,R,B,w", [(1, 32, 16, 4096), (8, 16, 8, 8192), (2, 128, 12, 1024)])
+def test_every_query_schedule_is_bit_exact(shards, R, B, w):
+    """Fused persistent and plain per-stage kernels, every CTA size and CTAs/SM
+    cap: the same ids and scores as the oracle (integer work, tolerance zero)."""
+    s = _slash()
+    g = datagen.Generator()
+    n = 25_000
+    offs, cols = g.rows(12, 0, n)
+    qo, qc = _queries(g, n, 700, seed=13, planted_frac=0.3, p_perturb=0.2)
+    p = s.Params(K=4, L=16, log2_buckets=B, reservoir=R, cm_rows=4, cm_width=w, shards=shards,
+                 capacity=n, seed=12)
+    want_ids, want_sc = _oracle_index(p, offs, cols).query(qo, qc, 20)
+    with s.Index(p) as ix:
+        ix.insert(_dev(offs), _dev(cols))
+        dq, dc = _dev(qo), _dev(qc)
+        for mode in ("fused", "plain"):
+            for threads in (256, 512, 1024):
+                for cps in (0, 1):
+                    ids, sc = ix.query(dq, dc, 20, mode=mode, threads=threads, ctas_per_sm=cps)
+                    ix.sync()
+                    assert np.array_equal(ids.cpu().numpy(), want_ids), (mode, threads, cps)
+                    assert np.array_equal(_host_u32(sc), want_sc), (mode, threads, cps)
+        best, ms = ix.autotune(dq, dc, 20)
+        assert ms > 0 and best.threads in (256, 512, 1024)
+        ids, sc = ix.query(dq, dc, 20)   # the tuned default
+        ix.sync()
+        assert np.array_equal(ids.cpu().numpy(), want_ids)
+        assert np.array_equal(_host_u32(sc), want_sc)
+
+
+def test_uneven_queries_bit_exact():
+    """The `uneven` mix: 30% planted, 70% random lognormal-nnz rows up to 2000."""
+    from datagen.workloads import UNEVEN as w
+    s = _slash()
+    g = datagen.Generator()
+    offs, cols = g.rows(w.seed, 0, w.n_rows)
+    qo, qc, _ = g.queries(w.seed, w.qseed, 20_000, w.n_rows, **w.query_kwargs())
+    assert np.diff(qo).max() > 1000
+    p = s.Params(**w.params())
+    want_ids, want_sc = _oracle_index(p, offs, cols).query(qo, qc, w.topk)
+    with s.Index(p) as ix:
+        ix.insert(_dev(offs), _dev(cols))
+        for mode in ("fused", "plain"):
+            ids, sc = ix.query(_dev(qo), _dev(qc), w.topk, mode=mode)
+            ix.sync()
+            assert np.array_equal(ids.cpu().numpy(), want_ids), mode
+            assert np.array_equal(_host_u32(sc), want_sc), mode
