@@ -56,6 +56,10 @@ def _load():
             lib.sg_pois_cdf.argtypes = [vp, ctypes.POINTER(u32)]
             lib.sg_lnorm_cdf.restype = ctypes.POINTER(ctypes.c_uint64)
             lib.sg_lnorm_cdf.argtypes = [vp, ctypes.POINTER(u32)]
+            lib.sg_zipf_guide.restype = ctypes.POINTER(u32)
+            lib.sg_zipf_guide.argtypes = [vp]
+            lib.sg_pois_guide.restype = ctypes.POINTER(u32)
+            lib.sg_pois_guide.argtypes = [vp]
             lib.sg_feature.restype = u32
             lib.sg_feature.argtypes = [vp, u64, u64]
             lib.sg_u64_public.restype = u64
@@ -108,6 +112,12 @@ class Generator:
         p = self._lib.sg_lnorm_cdf(self._h, ctypes.byref(n))
         return np.ctypeslib.as_array(p, shape=(n.value,)).copy()
 
+    def zipf_guide(self) -> np.ndarray:
+        return np.ctypeslib.as_array(self._lib.sg_zipf_guide(self._h), shape=(65537,)).copy()
+
+    def poisson_guide(self) -> np.ndarray:
+        return np.ctypeslib.as_array(self._lib.sg_pois_guide(self._h), shape=(65537,)).copy()
+
     def feature(self, seed: int, u: int) -> int:
         return int(self._lib.sg_feature(self._h, seed, u))
 
@@ -158,3 +168,72 @@ class Generator:
 def u64(seed: int, stream: int, row: int, j: int) -> int:
     """The generator's counter-based uniform word (exposed for tests)."""
     return int(_load().sg_u64_public(seed, stream, row, j))
+
+
+# ---------------------------------------------------------------------- device twin
+_DEV_SRC = os.path.join(_HERE, "slashgen_dev.cu")
+_DEV_LIB = os.path.join(_HERE, "libslashgen_dev.so")
+_dev_lib = None
+
+
+def build_device(force: bool = False) -> str:
+    """Compile the CUDA twin (sm_103a) next to its source."""
+    if force or not os.path.exists(_DEV_LIB) or os.path.getmtime(_DEV_LIB) < os.path.getmtime(_DEV_SRC):
+        tmp = _DEV_LIB + f".tmp{os.getpid()}"
+        nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+        subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3",
+                               "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, _DEV_SRC])
+        os.replace(tmp, _DEV_LIB)
+    return _DEV_LIB
+
+
+def _load_dev():
+    global _dev_lib
+    with _lock:
+        if _dev_lib is None:
+            lib = ctypes.CDLL(build_device())
+            vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+            lib.sgd_rows_nnz.restype = ctypes.c_int
+            lib.sgd_rows_nnz.argtypes = [vp, vp, u32, u64, u64, u32, u32, u32, u32, vp, vp]
+            lib.sgd_rows_cols.restype = ctypes.c_int
+            lib.sgd_rows_cols.argtypes = [vp, vp, u32, u64, u64, u32, vp, vp, vp]
+            _dev_lib = lib
+    return _dev_lib
+
+
+class DeviceRows:
+    """Dataset rows generated on the GPU, byte-identical to ``Generator.rows``."""
+
+    def __init__(self, gen: Generator, device: str = "cuda"):
+        import torch
+        self.torch = torch
+        self._lib = _load_dev()
+        self.dim_bits, self.dim = gen.dim_bits, gen.dim
+        t = lambda a, dt: torch.from_numpy(a.view(dt)).to(device)
+        self.zc = t(gen.zipf_cdf(), np.int64)
+        self.zg = t(gen.zipf_guide(), np.int32)
+        pc = gen.poisson_cdf()
+        self.pn = len(pc)
+        self.pc = t(pc, np.int64)
+        self.pg = t(gen.poisson_guide(), np.int32)
+        self.device = device
+
+    def rows(self, seed: int, row0: int, n: int, lo: int = 5, hi: int = 200, stream=None):
+        """(offs int64 [n+1] from 0, cols int32) CUDA tensors for rows [row0, row0+n)."""
+        torch = self.torch
+        st = stream or torch.cuda.current_stream()
+        with torch.cuda.stream(st):
+            nnz = torch.empty(n, dtype=torch.int32, device=self.device)
+            rc = self._lib.sgd_rows_nnz(self.pc.data_ptr(), self.pg.data_ptr(), self.pn, seed, row0, n, lo, hi,
+                                        self.dim, nnz.data_ptr(), st.cuda_stream)
+            if rc:
+                raise RuntimeError("device generator launch failed")
+            offs = torch.zeros(n + 1, dtype=torch.int64, device=self.device)
+            torch.cumsum(nnz, 0, out=offs[1:])
+            total = int(offs[-1].item())
+            cols = torch.empty(total, dtype=torch.int32, device=self.device)
+            rc = self._lib.sgd_rows_cols(self.zc.data_ptr(), self.zg.data_ptr(), self.dim_bits, seed, row0, n,
+                                         offs.data_ptr(), cols.data_ptr(), st.cuda_stream)
+            if rc:
+                raise RuntimeError("device generator launch failed")
+        return offs, cols

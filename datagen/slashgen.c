@@ -147,6 +147,9 @@ void sg_free(void *p) {
 const uint64_t *sg_zipf_cdf(const void *p) { return ((const sg_gen *)p)->zipf.cdf; }
 const uint64_t *sg_pois_cdf(const void *p, uint32_t *n) { *n = ((const sg_gen *)p)->pois.n; return ((const sg_gen *)p)->pois.cdf; }
 const uint64_t *sg_lnorm_cdf(const void *p, uint32_t *n) { *n = ((const sg_gen *)p)->lnorm.n; return ((const sg_gen *)p)->lnorm.cdf; }
+const uint32_t *sg_zipf_guide(const void *p) { return ((const sg_gen *)p)->zipf.guide; }
+const uint32_t *sg_pois_guide(const void *p) { return ((const sg_gen *)p)->pois.guide; }
+uint32_t sg_dim_bits(const void *p) { return ((const sg_gen *)p)->dim_bits; }
 
 /* 4-round Feistel bijection on [0, 2^dim_bits) keyed by the dataset seed */
 static inline uint32_t sg_perm(const sg_gen *g, uint64_t seed, uint32_t x) {

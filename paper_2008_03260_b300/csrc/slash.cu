@@ -46,6 +46,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -850,7 +851,8 @@ struct slash_index {
   uint64_t qws = 0;
   uint32_t* qbkt = nullptr;
   slash_query_opts qdef{SLASH_QUERY_FUSED, 512, 0};  // default query schedule (autotuned)
-  uint32_t* work = nullptr;                          // fused-kernel work counter
+  uint32_t* work = nullptr;                          // ring of fused-kernel work counters
+  std::atomic<uint32_t> work_next{0};                // next ring slot (one per fused launch)
   // per-launch event profile (off unless slash_profile enables it)
   struct ProfRec { const char* name; cudaEvent_t a, b; };
   bool prof_on = false;
@@ -860,6 +862,8 @@ struct slash_index {
 };
 
 namespace {
+
+constexpr uint32_t kWorkRing = 4096;  // fused launches that may be in flight at once per index
 
 #define SLASH_CK(call)                                                                 \
   do {                                                                                 \
@@ -1123,7 +1127,7 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
   if (e == cudaSuccess) e = cudaMalloc(&ix->blocksum, sizeof(uint64_t) * nblk);
   if (e == cudaSuccess) e = cudaMalloc(&ix->err, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&ix->big_count, sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&ix->work, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&ix->work, sizeof(uint32_t) * kWorkRing);
   if (e == cudaSuccess) e = cudaMemsetAsync(ix->slots, 0xFF, sizeof(uint32_t) * ix->nk * p->reservoir, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ix->fill, 0, sizeof(uint32_t) * ix->nk, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ix->cnt, 0, sizeof(uint32_t) * ix->nk, st);
@@ -1197,11 +1201,13 @@ int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
   const uint64_t slots_per_gpu = (uint64_t)ix->num_sms * bps;
   if (o.mode == SLASH_QUERY_FUSED) {
     const uint32_t grid = (uint32_t)std::min<uint64_t>(n_queries, slots_per_gpu);
-    SLASH_CK(cudaMemsetAsync(ix->work, 0, sizeof(uint32_t), st));
+    // a private counter per launch: fused launches on different streams may overlap
+    uint32_t* work = ix->work + (ix->work_next.fetch_add(1u) % kWorkRing);
+    SLASH_CK(cudaMemsetAsync(work, 0, sizeof(uint32_t), st));
     Launch lq(ix, "k_query_fused", st);
 #define SLASH_FUSED(T)                                                                                \
   k_query_fused<T><<<grid, T, lay.bytes, st>>>(ix->geo, lay, d_offs, d_cols, n_queries, topk, ix->slots, \
-                                               ix->fill, d_ids_out, d_scores_out, ix->work, ix->err)
+                                               ix->fill, d_ids_out, d_scores_out, work, ix->err)
     if (thr == 256) SLASH_FUSED(256); else if (thr == 512) SLASH_FUSED(512); else SLASH_FUSED(1024);
 #undef SLASH_FUSED
     SLASH_CK(cudaGetLastError());

@@ -63,3 +63,20 @@ def test_uneven_queries_mix():
     # lognormal(ln 40, 1): median 40
     assert abs(np.median(nnz) - 40) < 3
     assert abs(np.mean(np.log(nnz)) - math.log(40)) < 0.05
+
+
+import pytest  # noqa: E402
+
+
+@pytest.mark.gpu
+def test_device_rows_match_host_rows():
+    """The CUDA twin writes the host generator's bytes (streamed workloads)."""
+    import torch
+    g = datagen.Generator()
+    dg = datagen.DeviceRows(g)
+    for row0, n, lo, hi in [(0, 50_000, 5, 200), (123_456_789, 20_000, 5, 200), (7, 3000, 1, 2000)]:
+        offs, cols = g.rows(11, row0, n, lo=lo, hi=hi)
+        doffs, dcols = dg.rows(11, row0, n, lo=lo, hi=hi)
+        torch.cuda.synchronize()
+        assert np.array_equal(doffs.cpu().numpy().view(np.uint64), offs)
+        assert np.array_equal(dcols.cpu().numpy().view(np.uint32), cols)

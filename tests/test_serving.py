@@ -1,0 +1,129 @@
+"""Serving loop: admission/batching host logic on CPU (fake executor), and the
+GPU loop's results equal to each request answered alone (tolerance zero)."""
+import time
+
+import numpy as np
+import pytest
+
+import datagen
+
+
+class FakeExecutor:
+    """Answers query i of a batch with (nnz, first col, ...) after a fixed delay."""
+
+    def __init__(self, topk, delay=0.002):
+        self.topk, self.delay = topk, delay
+        self.launched = []
+        self.peak_inflight = 0
+        self.live = 0
+
+    def launch(self, slot, offs, cols):
+        nq = len(offs) - 1
+        ids = np.full((nq, self.topk), -1, np.int32)
+        for q in range(nq):
+            row = cols[int(offs[q]):int(offs[q + 1])]
+            ids[q, 0] = len(row)
+            if len(row):
+                ids[q, 1] = row[0]
+        self.launched.append(nq)
+        self.live += 1
+        self.peak_inflight = max(self.peak_inflight, self.live)
+        return [time.perf_counter() + self.delay, ids, False]
+
+    def done(self, h):
+        return time.perf_counter() >= h[0]
+
+    def collect(self, h):
+        self.live -= 1
+        return h[1], np.zeros_like(h[1], dtype=np.uint32), h[0]
+
+
+def _pool(n=3000):
+    g = datagen.Generator()
+    qo, qc, _ = g.queries(0, 2, n, 1000, planted_frac=0.3, p_perturb=0.2)
+    return qo, qc
+
+
+def test_batcher_admission_respects_budget_and_order():
+    from paper_2008_03260_b300.serve import Batcher, Request, request_bytes
+    qo, qc = _pool(200)
+    reqs = []
+    for i in range(20):
+        o = qo[i * 10:i * 10 + 11]
+        reqs.append(Request(i, (o - o[0]).astype(np.uint64), qc[int(o[0]):int(o[-1])], 0.0))
+    budget = sum(request_bytes(r, 10) for r in reqs[:5])
+    b = Batcher(slots=3, topk=10, mem_budget=budget, max_batch_queries=30)
+    for r in reqs:
+        b.arrive(r)
+    first = b.next_batch(0)
+    assert [r.rid for r in first.reqs] == [0, 1, 2]          # capped at 30 queries
+    second = b.next_batch(1)
+    assert [r.rid for r in second.reqs] == [3, 4]             # capped by the memory budget
+    assert b.next_batch(2) is None and b.mem_in_use <= budget
+    b.finish(0)
+    third = b.next_batch(0)
+    got = [r.rid for r in third.reqs]
+    assert got == list(range(5, 5 + len(got))) and got         # arrival order kept
+    nxt = reqs[5 + len(got)]                                   # the next one did not fit
+    assert b.mem_in_use + request_bytes(nxt, 10) > budget or sum(r.nq for r in third.reqs) + nxt.nq > 30
+    assert b.mem_in_use <= budget
+    huge = Request(99, np.array([0, 1], np.uint64), np.zeros(1, np.uint32), 0.0)
+    tiny = Batcher(slots=1, topk=10, mem_budget=8, max_batch_queries=30)
+    tiny.arrive(huge)
+    assert tiny.refused == [huge] and not tiny.queue
+
+
+def test_serve_loop_slices_results_per_request():
+    from paper_2008_03260_b300.serve import poisson_requests, serve
+    qo, qc = _pool()
+    reqs = poisson_requests(20_000.0, 300, qo, qc, seed=1, max_size=64)
+    ex = FakeExecutor(topk=5)
+    res, summ = serve(reqs, ex, topk=5, slots=3, mem_budget=1 << 20, max_batch_queries=256)
+    assert summ["requests"] == 300 and summ["refused"] == 0
+    assert ex.peak_inflight <= 3 and max(ex.launched) <= 256
+    assert summ["batches"] < 300   # requests that queued up were batched together
+    by = {r.rid: r for r in res}
+    for q in reqs:
+        r = by[q.rid]
+        assert r.ids.shape == (q.nq, 5) and r.latency >= 0
+        for i in range(q.nq):
+            row = q.cols[int(q.offs[i]):int(q.offs[i + 1])]
+            assert r.ids[i, 0] == len(row)
+            if len(row):
+                assert r.ids[i, 1] == row[0]
+
+
+@pytest.mark.gpu
+def test_gpu_serving_results_equal_alone():
+    """Requests mixed into overlapping batches on several streams get exactly the
+    answer they get when queried alone (and the oracle's, for a sample)."""
+    import torch
+
+    import oracle
+    import paper_2008_03260_b300 as s
+    from paper_2008_03260_b300.serve import GpuExecutor, poisson_requests, serve
+    g = datagen.Generator()
+    n = 30_000
+    offs, cols = g.rows(0, 0, n)
+    qo, qc, _ = g.queries(0, 3, 20_000, n, planted_frac=0.3, p_perturb=0.2)
+    p = s.Params(K=4, L=16, log2_buckets=12, reservoir=32, cm_rows=4, cm_width=8192, shards=8, capacity=n)
+    dev = lambda a: torch.from_numpy(a.view(np.int64 if a.dtype == np.uint64 else np.int32)).cuda()
+    with s.Index(p) as ix:
+        ix.insert(dev(offs), dev(cols))
+        ix.sync()
+        reqs = poisson_requests(50_000.0, 400, qo, qc, seed=5, max_size=512)
+        ex = GpuExecutor(ix, topk=10, slots=4)
+        res, summ = serve(reqs, ex, topk=10, slots=4, mem_budget=64 << 20, max_batch_queries=2048)
+        assert summ["requests"] == 400 and summ["batches"] < 400
+        by = {r.rid: r for r in res}
+        for q in reqs:
+            ids, sc = ix.query(dev(q.offs), dev(q.cols), 10, mode="fused")
+            assert np.array_equal(by[q.rid].ids, ids.cpu().numpy()), q.rid
+            assert np.array_equal(by[q.rid].scores, sc.cpu().numpy().view(np.uint32)), q.rid
+        ix.sync()
+    oix = oracle.Index(K=4, L=16, log2_buckets=12, reservoir=32, cm_rows=4, cm_width=8192, shards=8,
+                       capacity=n)
+    oix.insert(offs, cols)
+    for q in reqs[:40]:
+        want_ids, want_sc = oix.query(q.offs, q.cols, 10)
+        assert np.array_equal(by[q.rid].ids, want_ids) and np.array_equal(by[q.rid].scores, want_sc)
