@@ -87,6 +87,7 @@ def _load() -> ctypes.CDLL:
         "slash_debug_buckets": (i32, [vp, vp, vp, vp, u32, vp, vp]),
         "slash_query_ex": (i32, [vp, vp, vp, u32, u32, vp, vp, P(slash_query_opts), vp]),
         "slash_autotune": (i32, [vp, vp, vp, u32, u32, vp, vp, vp, P(slash_query_opts), P(ctypes.c_float)]),
+        "slash_query_static": (i32, [vp, vp, vp, u32, u32, vp, vp, vp]),
         "slash_profile": (i32, [vp, i32]),
         "slash_profile_read": (i32, [vp, u32, vp, vp, vp, P(u32), P(u64)]),
     }

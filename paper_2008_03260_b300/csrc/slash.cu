@@ -1389,3 +1389,67 @@ int slash_debug_buckets(slash_index* ix, const uint32_t* h_shard, const uint32_t
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------- allocation-free query
+// slash_query_static: the plain query path (k_hash, then k_query) with its one
+// piece of scratch -- the queries' table addresses -- in a fixed array that is
+// part of this library's device image, so the call never allocates.  For
+// callers that cannot call cudaMalloc: code running while a CUDA graph is being
+// captured (allocation is not a capturable operation), and hosts whose device
+// memory is handed out once at start-up by their own pool, where a later
+// allocation would fail or stall the process.
+namespace {
+
+constexpr uint64_t kStaticQbktWords = 1ull << 22;  // 16 MiB: n_queries * L per call, at most
+static __device__ __align__(256) uint32_t g_static_qbkt[kStaticQbktWords];
+std::mutex g_static_mu;
+uint32_t* g_static_ptr[256] = {};  // device address of g_static_qbkt, per device ordinal
+
+// The host-side name g_static_qbkt is only a stand-in for the array; kernels
+// must be given its device address, looked up once per device (that device
+// current) and cached.
+int static_scratch(int device, uint32_t** out) {
+  if (device < 0 || device >= 256) return SLASH_EINVAL;
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[device]) {
+    uint32_t* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void**)&p, g_static_qbkt);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return SLASH_ECUDA;
+    }
+    g_static_ptr[device] = p;
+  }
+  *out = g_static_ptr[device];
+  return SLASH_OK;
+}
+
+}  // namespace
+
+extern "C" int slash_query_static(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_cols,
+                                  uint32_t n_queries, uint32_t topk, int32_t* d_ids_out,
+                                  uint32_t* d_scores_out, void* cuda_stream) {
+  if (!ix || topk == 0 || topk > SLASH_MAX_TOPK) return SLASH_EINVAL;
+  if ((uint64_t)n_queries * ix->p.L > kStaticQbktWords) return SLASH_EINVAL;
+  if (n_queries == 0) return SLASH_OK;
+  if (!d_offs || !d_cols || !d_ids_out || !d_scores_out) return SLASH_EINVAL;
+  int cur = -1;
+  SLASH_CK(cudaGetDevice(&cur));
+  if (cur != ix->device) return SLASH_EINVAL;  // the index's device must be current
+  uint32_t* qbkt = nullptr;
+  int rc = static_scratch(cur, &qbkt);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const QueryLayout lay = make_query_layout(ix->p, topk);
+  int bps = 0;
+  SLASH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_query<512>, 512, lay.bytes));
+  if (bps < 1) return SLASH_EINVAL;
+  rc = run_hash(ix, d_offs, d_cols, n_queries, 0, qbkt, n_queries, nullptr, false, st);
+  if (rc) return rc;
+  const uint32_t grid = (uint32_t)std::min<uint64_t>(n_queries, (uint64_t)ix->num_sms * bps);
+  Launch lq(ix, "k_query", st);
+  k_query<512><<<grid, 512, lay.bytes, st>>>(ix->geo, lay, qbkt, n_queries, n_queries, topk, ix->slots,
+                                             ix->fill, d_ids_out, d_scores_out);
+  SLASH_CK(cudaGetLastError());
+  return SLASH_OK;
+}
