@@ -219,6 +219,8 @@ def main():
     ap.add_argument("--log2-buckets", type=int, default=0, help="override (small profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-max-requests", type=int, default=20_000)
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     w = workloads.ALL[args.workload]
@@ -230,6 +232,10 @@ def main():
         log("[bench] warning: fewer than 3 warm-up steps")
     if args.impl == "reference":
         run_reference(args, w)
+        return
+    if w.name in ("uneven", "serving", "stream"):
+        fn = {"uneven": bench_uneven, "serving": bench_serving, "stream": bench_stream}[w.name]
+        print(json.dumps(fn(args, w)), flush=True)
         return
 
     import torch
@@ -244,7 +250,9 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    offs, cols, qo, qc, _ = make_inputs(w, rank * w.n_rows, w.n_rows, w.n_queries, qseed_off=rank)
+    from paper_2008_03260_b300.multi import job_throughput, max_over_ranks, rank_rows
+    row0, _ = rank_rows(rank, world, w.n_rows)
+    offs, cols, qo, qc, _ = make_inputs(w, row0, w.n_rows, w.n_queries, qseed_off=rank)
     h2d_bytes = offs.nbytes + cols.nbytes + qo.nbytes + qc.nbytes
     d2h_bytes = 2 * 4 * w.n_queries * w.topk
     t = time.time()
@@ -323,11 +331,8 @@ def main():
     ins = [e[1].elapsed_time(e[2]) / 1e3 for e in evs]
     qry = [e[2].elapsed_time(e[3]) / 1e3 for e in evs]
     tot = [e[0].elapsed_time(e[3]) / 1e3 for e in evs]
-    t_ins, t_q, t_step = statistics.mean(ins), statistics.mean(qry), statistics.mean(tot)
-    if dist:
-        v = torch.tensor([t_ins, t_q, t_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(v, op=dist.ReduceOp.MAX)
-        t_ins, t_q, t_step = v.tolist()
+    t_ins, t_q, t_step, t_plain = max_over_ranks(
+        [statistics.mean(ins), statistics.mean(qry), statistics.mean(tot), t_plain], device="cuda")
 
     # e2e: the same calls from pinned host buffers, copies inside the timed region
     e2e = None
@@ -351,12 +356,8 @@ def main():
             if i >= args.warmup:
                 e_ins.append(ev[0].elapsed_time(ev[1]) / 1e3)
                 e_q.append(ev[1].elapsed_time(ev[2]) / 1e3)
-        ei, eq = statistics.mean(e_ins), statistics.mean(e_q)
-        if dist:
-            v = torch.tensor([ei, eq], device="cuda", dtype=torch.float64)
-            dist.all_reduce(v, op=dist.ReduceOp.MAX)
-            ei, eq = v.tolist()
-        e2e = {"value": world * w.n_rows / ei, "unit": "rows/s", "h2d_bytes_per_step": h2d_bytes,
+        ei, eq = max_over_ranks([statistics.mean(e_ins), statistics.mean(e_q)], device="cuda")
+        e2e = {"value": job_throughput(w.n_rows, world, ei), "unit": "rows/s", "h2d_bytes_per_step": h2d_bytes,
                "d2h_bytes_per_step": d2h_bytes, "queries_per_s": world * w.n_queries / eq,
                "insert_ms": 1e3 * ei, "query_ms": 1e3 * eq}
 
@@ -389,7 +390,7 @@ def main():
     path_q_bytes = algo["k_query_fused"]
     out = {
         "metric": METRIC,
-        "value": world * w.n_rows / t_ins,
+        "value": job_throughput(w.n_rows, world, t_ins),
         "unit": "rows/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_step,
@@ -420,6 +421,151 @@ def main():
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+
+# ----------------------------------------------------------------------------- other workloads
+def _gpu_setup(w, shards=None):
+    import torch
+    import paper_2008_03260_b300 as slash
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    return torch, slash
+
+
+def bench_uneven(args, w: workloads.Workload) -> dict:
+    """1M uneven-nnz queries per launch: fused persistent kernel replayed from a
+    captured CUDA graph vs the plain one-launch-per-stage path."""
+    torch, slash = _gpu_setup(w)
+    offs, cols, qo, qc, _ = make_inputs(w, 0, w.n_rows, w.n_queries)
+    dev = lambda a: torch.from_numpy(a.view(np.int64 if a.dtype == np.uint64 else np.int32)).cuda()
+    ix = slash.Index(slash.Params(**w.params()))
+    ix.insert(dev(offs), dev(cols))
+    d_qo, d_qc = dev(qo), dev(qc)
+    ids = torch.empty((w.n_queries, w.topk), dtype=torch.int32, device="cuda")
+    sc = torch.empty_like(ids)
+    sample = min(w.n_queries, 100_000)
+    best, _ = ix.autotune(d_qo[:sample + 1], d_qc, w.topk)
+    log(f"[bench] uneven: tuned {best}")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        ix.query(d_qo, d_qc, w.topk, s, d_ids_out=ids, d_scores_out=sc, mode="fused", threads=best.threads,
+                 ctas_per_sm=best.ctas_per_sm)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        ix.query(d_qo, d_qc, w.topk, s, d_ids_out=ids, d_scores_out=sc, mode="fused", threads=best.threads,
+                 ctas_per_sm=best.ctas_per_sm)
+    torch.cuda.synchronize()
+
+    def timed(fn, n):
+        out = []
+        for i in range(args.warmup + n):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            fn()
+            b.record(s)
+            b.synchronize()
+            if i >= args.warmup:
+                out.append(a.elapsed_time(b) / 1e3)
+        return statistics.mean(out)
+
+    with Clocks(0) as clk:
+        with torch.cuda.stream(s):
+            t_fused = timed(graph.replay, args.steps)
+            ref_ids = ids.clone()
+            t_plain = timed(lambda: ix.query(d_qo, d_qc, w.topk, s, d_ids_out=ids, d_scores_out=sc, mode="plain",
+                                             threads=best.threads), args.steps)
+    same = bool(torch.equal(ref_ids, ids))
+    ix.sync()
+    ix.close()
+    return {"metric": "queries/s, 1M uneven-nnz queries per launch (fused persistent + CUDA graph vs plain)",
+            "value": w.n_queries / t_fused, "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_fused, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": config_of(w, args),
+            "plain_queries_per_s": w.n_queries / t_plain, "speedup_vs_plain": t_plain / t_fused,
+            "schedule": repr(best), "fused_equals_plain": same, "clocks": clk.summary()}
+
+
+def bench_serving(args, w: workloads.Workload, rates=(1_000, 10_000, 100_000)) -> dict:
+    """Poisson request streams against an 8-shard resident index: p50/p99 latency."""
+    torch, slash = _gpu_setup(w)
+    from paper_2008_03260_b300.serve import GpuExecutor, poisson_requests, serve
+    g = datagen.Generator(dim_bits=w.dim_bits)
+    offs, cols = g.rows(w.seed, 0, w.n_rows)
+    qo, qc, _ = g.queries(w.seed, w.qseed, 2_000_000, w.n_rows, **w.query_kwargs())
+    dev = lambda a: torch.from_numpy(a.view(np.int64 if a.dtype == np.uint64 else np.int32)).cuda()
+    ix = slash.Index(slash.Params(**w.params()))
+    ix.insert(dev(offs), dev(cols))
+    ix.sync()
+    per_rate = {}
+    for rate in rates:
+        n_req = int(min(args.serve_seconds * rate, args.serve_max_requests))
+        reqs = poisson_requests(float(rate), n_req, qo, qc, seed=rate)
+        ex = GpuExecutor(ix, topk=w.topk, slots=4)
+        with Clocks(0) as clk:
+            _, summ = serve(reqs, ex, topk=w.topk, slots=4, mem_budget=16 << 30, max_batch_queries=1 << 16)
+        summ["clocks"] = clk.summary()
+        per_rate[str(rate)] = summ
+        log(f"[bench] serving {rate} req/s: {summ}")
+    ix.close()
+    top = per_rate[str(rates[-1])]
+    return {"metric": "serving p50/p99 ms and sustained queries/s (continuous batching, 8 shards)",
+            "value": top["queries_per_s"], "unit": "queries/s", "n_gpus": 1, "steps": len(rates),
+            "warmup": 0, "ms_per_step": top["p50_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": config_of(w, args),
+            "rates": per_rate}
+
+
+def bench_stream(args, w: workloads.Workload) -> dict:
+    """1B rows generated on the device in 16M-row chunks, hashed and inserted,
+    never stored; then 1M planted queries (top-100) against the first 1M rows."""
+    torch, slash = _gpu_setup(w)
+    n_rows = args.rows or w.n_rows
+    chunk = w.extra["chunk_rows"]
+    g = datagen.Generator(dim_bits=w.dim_bits)
+    dg = datagen.DeviceRows(g)
+    ix = slash.Index(slash.Params(**w.params(capacity=n_rows)))
+    st = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    t_gen = t_all = 0.0
+    with Clocks(0) as clk:
+        for r0 in range(0, n_rows, chunk):
+            n = min(chunk, n_rows - r0)
+            a, b, c = ev(), ev(), ev()
+            a.record(st)
+            offs, cols = dg.rows(w.seed, r0, n, lo=w.nnz_lo, hi=w.nnz_hi)
+            b.record(st)
+            ix.insert(offs, cols, st)
+            c.record(st)
+            c.synchronize()
+            t_gen += a.elapsed_time(b) / 1e3
+            t_all += a.elapsed_time(c) / 1e3
+            del offs, cols
+    ix.sync()
+    retained = min(n_rows, 1_000_000)
+    nq = args.queries or w.n_queries
+    qo, qc, src = g.queries(w.seed, w.qseed, nq, retained, **w.query_kwargs())
+    dev = lambda a: torch.from_numpy(a.view(np.int64 if a.dtype == np.uint64 else np.int32)).cuda()
+    d_qo, d_qc = dev(qo), dev(qc)
+    ids = torch.empty((nq, w.topk), dtype=torch.int32, device="cuda")
+    sc = torch.empty_like(ids)
+    ix.query(d_qo, d_qc, w.topk, st, d_ids_out=ids, d_scores_out=sc)
+    a, b = ev(), ev()
+    a.record(st)
+    ix.query(d_qo, d_qc, w.topk, st, d_ids_out=ids, d_scores_out=sc)
+    b.record(st)
+    b.synchronize()
+    t_q = a.elapsed_time(b) / 1e3
+    h_ids = ids.cpu().numpy()
+    recall = float(np.mean((h_ids == src[:, None]).any(axis=1)))
+    ix.close()
+    return {"metric": "streamed insert rows/s (device-generated, never stored) and top-100 queries/s",
+            "value": n_rows / t_all, "unit": "rows/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": 1e3 * t_all, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic (generated on the device)", "config": config_of(w, args),
+            "generate_rows_per_s": n_rows / t_gen, "insert_only_rows_per_s": n_rows / (t_all - t_gen),
+            "queries_per_s": nq / t_q, "planted_recall_at_k": recall, "clocks": clk.summary()}
 
 
 if __name__ == "__main__":

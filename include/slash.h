@@ -115,12 +115,13 @@ int slash_query(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols,
 
 typedef struct {
   uint32_t mode;         /* SLASH_QUERY_FUSED or SLASH_QUERY_PLAIN                     */
-  uint32_t threads;      /* threads per CTA: 256, 512 or 1024 (0 = 512)                  */
+  uint32_t threads;      /* threads per CTA: 256, 512 or 1024 (0 = the index's default)  */
   uint32_t ctas_per_sm;  /* cap on resident CTAs per SM (0 = as many as smem allows)     */
 } slash_query_opts;
 
 /* slash_query with an explicit schedule (opts == NULL: the index's default,
- * initially {FUSED, 512, 0}, replaced by slash_autotune).  Same outputs and
+ * initially {FUSED, smallest CTA holding S*L*R ids at 8 per thread, 0}, replaced
+ * by slash_autotune).  Same outputs and
  * errors as slash_query; SLASH_EINVAL also when the schedule does not fit. */
 int slash_query_ex(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n_queries,
                    uint32_t topk, int32_t *d_ids_out, uint32_t *d_scores_out, const slash_query_opts *opts,

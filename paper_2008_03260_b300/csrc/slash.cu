@@ -36,12 +36,15 @@
 //                   by (pri, id) in smem, keep R
 //   k_merge_big     CTA per heavy bucket: 4-pass radix select of the R-th
 //                   smallest priority, then sort the R survivors
-//   k_query         CTA per query: gather the S*L buckets, count-min in smem,
-//                   de-duplicate with an smem hash set, histogram threshold on
-//                   the estimate + radix select on ties, sort the top-k
+//   k_query         CTA per query: gather the S*L buckets (ids in registers),
+//                   count-min in smem, per-occurrence estimates, a histogram
+//                   cut-off that provably keeps >= k distinct ids, sort the
+//                   small pool above it and keep the first k distinct
+//   k_query_fused   the same, persistent, with the query hashed in smem first
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -77,10 +80,16 @@ __device__ __forceinline__ uint32_t nearest_bin(const uint32_t* mask, uint32_t n
 }
 
 // DOPH of one CSR row by one warp into m[nb] (smem), using mask[nw] (smem).
+// Densification works on lane chunks: lane l owns bins [l*c, l*c + c),
+// c = ceil(nb/32); the nearest non-empty bin inside the chunk comes from bit
+// scans of the chunk's mask bits, and across chunks from a circular pointer-
+// jumping scan over the lanes' first / last non-empty bins.
 __device__ __forceinline__ void doph_row(const Geo& g, const uint32_t* __restrict__ cols, uint64_t b0,
                                          uint64_t b1, uint32_t* m, uint32_t* mask, uint32_t* err,
                                          uint32_t lane) {
-  for (uint32_t j = lane; j < g.nb; j += 32) m[j] = kEmpty;
+  uint4* m4 = reinterpret_cast<uint4*>(m);  // m is 16-byte aligned
+  for (uint32_t j = lane; j < (g.nb >> 2); j += 32) m4[j] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+  for (uint32_t j = (g.nb & ~3u) + lane; j < g.nb; j += 32) m[j] = kEmpty;
   if (lane < g.nw) mask[lane] = 0u;
   __syncwarp();
   bool bad = false;
@@ -94,15 +103,42 @@ __device__ __forceinline__ void doph_row(const Geo& g, const uint32_t* __restric
   }
   if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(err, kErrCol);
   __syncwarp();
-  const uint32_t mw = lane < g.nw ? mask[lane] : 0u;
-  if (__any_sync(0xFFFFFFFFu, mw != 0u)) {
-    // only empty bins are written and only non-empty bins are read: in place
-    for (uint32_t j = lane; j < g.nb; j += 32) {
-      if (!((mask[j >> 5] >> (j & 31u)) & 1u)) {
-        const bool right = (g.dirbits[j >> 5] >> (j & 31u)) & 1u;
-        m[j] = m[nearest_bin(mask, g.nw, j, right)];
-      }
-    }
+  constexpr uint32_t kNone = 0xFFFFFFFFu;
+  const uint32_t c = (g.nb + 31u) >> 5;          // bins per lane (1..32)
+  const uint32_t lo = lane * c;
+  const uint32_t cnt = lo < g.nb ? min(c, g.nb - lo) : 0u;
+  uint32_t cb = 0u, db = 0u;                     // my chunk's non-empty bits and side bits
+  if (cnt) {
+    const uint32_t w = lo >> 5, s = lo & 31u;
+    const uint64_t mw = ((uint64_t)(w + 1 < g.nw ? mask[w + 1] : 0u) << 32) | mask[w];
+    const uint64_t dw = ((uint64_t)(w + 1 < g.nw ? g.dirbits[w + 1] : 0u) << 32) | g.dirbits[w];
+    const uint32_t keep = cnt == 32u ? 0xFFFFFFFFu : ((1u << cnt) - 1u);
+    cb = (uint32_t)(mw >> s) & keep;
+    db = (uint32_t)(dw >> s) & keep;
+  }
+  if (!__any_sync(0xFFFFFFFFu, cb != 0u)) return;  // empty row: every code stays 0xFFFFFFFF
+  const uint32_t first = cb ? lo + (uint32_t)(__ffs(cb) - 1) : kNone;
+  const uint32_t last = cb ? lo + 31u - (uint32_t)__clz(cb) : kNone;
+  // right: first non-empty among lanes l+1, l+2, ... (circular); left: mirror
+  uint32_t rn = __shfl_sync(0xFFFFFFFFu, first, (lane + 1u) & 31u);
+  uint32_t ln = __shfl_sync(0xFFFFFFFFu, last, (lane + 31u) & 31u);
+#pragma unroll
+  for (uint32_t d = 1; d < 32; d <<= 1) {
+    const uint32_t ro = __shfl_sync(0xFFFFFFFFu, rn, (lane + d) & 31u);
+    const uint32_t lo2 = __shfl_sync(0xFFFFFFFFu, ln, (lane + 32u - d) & 31u);
+    if (rn == kNone) rn = ro;
+    if (ln == kNone) ln = lo2;
+  }
+  // branch-free: an empty bin reads the nearest non-empty bin on its side; a
+  // non-empty bin rewrites its own value.  Only non-empty bins are read, and
+  // their values never change, so the update is safe in place.
+  for (uint32_t p = 0; p < cnt; ++p) {
+    const uint32_t above = cb & ((0xFFFFFFFEu << p));            // bits > p (p < 32)
+    const uint32_t below = cb & ((1u << p) - 1u);                // bits < p
+    const uint32_t kr = above ? lo + (uint32_t)(__ffs(above) - 1) : rn;
+    const uint32_t kl = below ? lo + 31u - (uint32_t)__clz(below) : ln;
+    const uint32_t k = ((cb >> p) & 1u) ? lo + p : (((db >> p) & 1u) ? kr : kl);
+    m[lo + p] = m[k];
   }
   __syncwarp();
 }
@@ -123,7 +159,7 @@ k_hash(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
        uint32_t* __restrict__ cnt, uint32_t* __restrict__ err) {
   extern __shared__ uint32_t smem[];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-  const uint32_t per_warp = g.nb + g.nw;
+  const uint32_t per_warp = (g.nb + g.nw + 3u) & ~3u;  // 16-byte aligned per warp
   uint32_t* m = smem + warp * per_warp;
   uint32_t* mask = m + g.nb;
   uint32_t* tile = smem + kHashWarps * per_warp;  // [L][kHashRows]
@@ -191,13 +227,13 @@ __device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* wsum, 
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_reduce(const uint32_t* __restrict__ cnt, uint64_t nk, uint64_t* __restrict__ blocksum) {
+k_scan_reduce(const uint32_t* __restrict__ cnt, uint32_t stride, uint64_t nk, uint64_t* __restrict__ blocksum) {
   __shared__ uint64_t wsum[33];
   const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
   uint64_t s = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i)
-    if (base + i < nk) s += cnt[base + i];
+    if (base + i < nk) s += cnt[(base + i) * stride];
   uint64_t tot;
   block_excl_scan(s, wsum, &tot);
   if (threadIdx.x == 0) blocksum[blockIdx.x] = tot;
@@ -218,40 +254,85 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint64_t* __restrict__ blo
 }
 
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_apply(const uint32_t* __restrict__ cnt, uint64_t nk, const uint64_t* __restrict__ blocksum,
-             uint32_t* __restrict__ off) {
+k_scan_apply(const uint32_t* __restrict__ cnt, uint32_t stride, uint64_t nk, const uint64_t* __restrict__ blocksum,
+             uint32_t* __restrict__ off, uint32_t ostride) {
   __shared__ uint64_t wsum[33];
   const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
   uint32_t v[kScanItems];
   uint64_t s = 0;
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    v[i] = base + i < nk ? cnt[base + i] : 0u;
+    v[i] = base + i < nk ? cnt[(base + i) * stride] : 0u;
     s += v[i];
   }
   uint64_t tot;
   uint64_t run = blocksum[blockIdx.x] + block_excl_scan(s, wsum, &tot);
 #pragma unroll
   for (int i = 0; i < kScanItems; ++i) {
-    if (base + i < nk) off[base + i] = (uint32_t)run;  // < 2^32: a chunk holds < 2^32 (row, table) pairs
+    if (base + i < nk) off[(base + i) * ostride] = (uint32_t)run;  // < 2^32: a chunk holds < 2^32 pairs
     run += v[i];
   }
-  if (base < nk && base + kScanItems >= nk) off[nk] = (uint32_t)run;  // the thread owning the last key
+  if (base < nk && base + kScanItems >= nk) off[nk * ostride] = (uint32_t)run;  // the last key's owner
 }
 
-// ----------------------------------------------------------------------------- scatter
+// ----------------------------------------------------------------------------- insert: plan
+// Per bucket (key) with n new pairs in this chunk: a priority threshold theta
+// and a staging capacity cap, kept with the staging offset and cursor in one
+// 16-byte record meta[key] = {theta, cap, offset, cursor}.  Only new ids with
+// pri < theta are staged:
+//   - a full bucket (fill == R) can only take ids below its largest kept
+//     priority pmax, so theta <= pmax loses nothing;
+//   - a bucket receiving many new ids (n > 1.5 mu) only needs about R of the
+//     smallest: theta = ceil(mu / n * 2^31) with mu = R + sigma*sqrt(R) + 16
+//     keeps ~Binomial(n, theta/2^31) >= R of them with overwhelming probability.
+// The merge checks that at least R candidates lie below theta (else the
+// bucket takes the exact fallback); cap = mean + sigma*sqrt(mean) + 16
+// survivors are reserved (overflow also takes the fallback).
+constexpr uint32_t kNoFilter = 0x80000000u;  // theta that keeps every 31-bit priority
+constexpr uint32_t kFallback = 0xFFFFFFFFu;  // cap marker: bucket handled by the exact fallback
+
+__global__ void __launch_bounds__(256)
+k_plan(const __grid_constant__ Geo g, uint64_t nk, const uint32_t* __restrict__ cnt,
+       const uint32_t* __restrict__ fill, const uint32_t* __restrict__ slots, uint4* __restrict__ meta,
+       float sigma) {
+  // single precision is enough: the merge proves exactness whatever theta is
+  const float mu_t = (float)g.R + sigma * sqrtf((float)g.R) + (sigma > 0.f ? 16.f : 0.f);
+  for (uint64_t key = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; key < nk;
+       key += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t n = cnt[key];
+    if (n == 0) { meta[key] = make_uint4(0u, 0u, 0u, 0u); continue; }
+    const uint32_t t = (uint32_t)((key >> g.B) % g.L);
+    uint32_t th = kNoFilter;
+    if (fill[key] == g.R) th = priority(slots[key * g.R + g.R - 1u], g.sp[t]);
+    if ((float)n > 1.5f * mu_t) {
+      const float te = ceilf(mu_t / (float)n * 2147483648.0f);
+      if (te < (float)th) th = (uint32_t)te;
+    }
+    uint32_t c = n;
+    if (th < kNoFilter) {
+      const float mean = (float)n * ((float)th / 2147483648.0f);
+      const float cc = ceilf(mean + sigma * sqrtf(mean) + (sigma > 0.f ? 16.f : 0.f));
+      c = cc < (float)n ? (uint32_t)cc : n;
+    }
+    meta[key] = make_uint4(th, c, 0u, 0u);
+  }
+}
+
+// ----------------------------------------------------------------------------- insert: scatter
 constexpr int kScatterThreads = 256;
 constexpr int kScatterPerThread = 4;
 constexpr uint32_t kScatterPiece = 1u << 21;  // rows per piece
 
-// Grid (x: rows within a piece, y: table, z: piece).  Blocks run roughly in
-// that order, so the stage region being written at any moment is one table's
-// share of one piece (a few MB): its sectors fill up in L2 before eviction.
+// Grid (x: rows within a piece, y: table, z: piece): blocks run roughly in
+// that order, so the records and the stage region touched at any moment are
+// one table's (a few MB): they stay in L2.  Ids below their bucket's
+// threshold take a slot of its staging range.
 __global__ void __launch_bounds__(kScatterThreads)
 k_scatter(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
-          const uint32_t* __restrict__ bkt, uint64_t ldb, uint32_t n, uint64_t id0,
-          const uint32_t* __restrict__ off, uint32_t* __restrict__ cnt, uint32_t* __restrict__ stage) {
+          const uint32_t* __restrict__ bkt, uint64_t ldb, uint32_t n, uint64_t id0, uint4* __restrict__ meta,
+          uint32_t* __restrict__ stage) {
   const uint32_t t = blockIdx.y;
+  const uint32_t sp = g.sp[t];
   const uint64_t p0 = (uint64_t)blockIdx.z * kScatterPiece;
   const uint64_t pend = min((uint64_t)n, p0 + kScatterPiece);
   const uint64_t base = p0 + (uint64_t)blockIdx.x * (kScatterThreads * kScatterPerThread) + threadIdx.x;
@@ -263,14 +344,16 @@ k_scatter(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
     const uint64_t id = id0 + i;
     const uint32_t s = shard_of(sm, g.S, id);
     const uint64_t key = (((uint64_t)s * g.L + t) << g.B) | b;
-    const uint32_t r = atomicSub(&cnt[key], 1u) - 1u;
-    stage[(uint64_t)off[key] + r] = (uint32_t)id;
+    const uint4 m = meta[key];
+    if (priority((uint32_t)id, sp) >= m.x) continue;
+    const uint32_t r = atomicAdd(&meta[key].w, 1u);
+    if (r < m.y) stage[(uint64_t)m.z + r] = (uint32_t)id;
   }
 }
 
-// ----------------------------------------------------------------------------- merge
-constexpr int kMergeWarps = 4;
-constexpr uint32_t kSmallMax = 1024;  // candidates a warp merges in smem
+// ----------------------------------------------------------------------------- insert: merge
+constexpr int kMergeWarps = 8;
+constexpr uint32_t kSmallMax = 1024;  // most candidates a warp merges in smem (buffer size is per index)
 constexpr uint32_t kInvMul2 = 0x7ED1B41Du;  // 0xC2B2AE35^-1 mod 2^31
 constexpr uint32_t kInvMul1 = 0x25CB9243u;  // 0x85EBCA6B^-1 mod 2^31
 
@@ -308,8 +391,9 @@ __device__ __forceinline__ void block_bitonic(uint64_t* buf, uint32_t n2) {
 // One warp sorts n distinct priorities a[0..n) ascending into b[0..n): a
 // monotone digit d(p) = min(31, p * scale) splits them into 32 buckets (lane d
 // owns bucket d), the buckets are laid out by a warp prefix sum, and each lane
-// insertion-sorts its own bucket.  Priorities are uniform, so the buckets hold
-// n/32 values on average.  Buckets that start at or after `need` stay unsorted.
+// insertion-sorts its own bucket.  With scale = 32 / (max + 1) and roughly
+// uniform priorities the buckets hold n/32 values on average.  Buckets that
+// start at or after `need` stay unsorted.
 __device__ __forceinline__ void warp_digit_sort(const uint32_t* a, uint32_t* b, uint32_t n, uint32_t need,
                                                 float scale, uint32_t* h, uint32_t lane) {
   h[lane] = 0u;
@@ -347,42 +431,81 @@ __device__ __forceinline__ void warp_digit_sort(const uint32_t* a, uint32_t* b, 
   __syncwarp();
 }
 
-constexpr float kScale31 = 32.0f / 2147483648.0f;
-
-// Warp per touched bucket: old slots + new ids -> the R smallest priorities, ascending.
+// Warp per bucket with new pairs: old slots + staged survivors -> the R
+// smallest priorities, ascending.  Resets cnt and the cursor for the next
+// chunk.  Buckets with more than `cap_c` candidates go to the big list (key,
+// stage offset, survivors); buckets whose filter cannot be proven exact, or
+// whose staging overflowed, go to the fallback list (key, n) untouched.
+// Dynamic smem: kMergeWarps x 2 buffers of cap_c words + kMergeWarps x 32.
 __global__ void __launch_bounds__(kMergeWarps * 32)
-k_merge_small(const __grid_constant__ Geo g, uint64_t nk, const uint32_t* __restrict__ off,
-              const uint32_t* __restrict__ stage, uint32_t* __restrict__ slots,
-              uint32_t* __restrict__ fill, uint32_t* __restrict__ big_keys,
-              uint32_t* __restrict__ big_count) {
-  __shared__ uint32_t bufa[kMergeWarps][kSmallMax];
-  __shared__ uint32_t bufb[kMergeWarps][kSmallMax];
-  __shared__ uint32_t hist[kMergeWarps][32];
+k_merge_small(const __grid_constant__ Geo g, uint64_t nk, uint32_t cap_c, uint32_t* __restrict__ cnt,
+              uint4* __restrict__ meta, const uint32_t* __restrict__ stage, uint32_t* __restrict__ slots,
+              uint32_t* __restrict__ fill, uint32_t* __restrict__ big, uint32_t* __restrict__ nbig,
+              uint32_t* __restrict__ fb, uint32_t* __restrict__ nfb) {
+  extern __shared__ uint32_t msm[];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint64_t nwarps = (uint64_t)gridDim.x * kMergeWarps;
-  uint32_t* a = bufa[warp];
-  uint32_t* b = bufb[warp];
+  uint32_t* a = msm + warp * 2u * cap_c;
+  uint32_t* b = a + cap_c;
+  uint32_t* hist = msm + kMergeWarps * 2u * cap_c + warp * 32u;
   for (uint64_t key = (uint64_t)blockIdx.x * kMergeWarps + warp; key < nk; key += nwarps) {
-    const uint32_t lo = off[key], hi = off[key + 1];
-    if (hi == lo) continue;
-    const uint32_t cnew = hi - lo;
+    const uint32_t n = cnt[key];
+    if (n == 0) continue;
+    const uint4 md = meta[key];
+    const uint32_t th = md.x, cp = md.y, lo = md.z, got = md.w;
     const uint32_t t = (uint32_t)((key >> g.B) % g.L);
     const uint32_t sp = g.sp[t];
     const uint32_t fold = fill[key];
-    const uint64_t total = (uint64_t)fold + cnew;
-    if (total > kSmallMax) {
-      if (lane == 0) big_keys[atomicAdd(big_count, 1u)] = (uint32_t)key;
-      continue;
-    }
-    const uint32_t tot = (uint32_t)total;
     uint32_t* bs = slots + key * g.R;
-    for (uint32_t c = lane; c < tot; c += 32) {
-      const uint32_t id = c < fold ? bs[c] : stage[lo + (c - fold)];
-      a[c] = priority(id, sp);
+    // exactness: no filter; or a full bucket filtered at or above its largest
+    // kept priority; or at least R candidates below the threshold
+    bool exact = got <= cp;
+    if (exact && th < kNoFilter) {
+      const bool full_ok = fold == g.R && th >= priority(bs[g.R - 1], sp);
+      if (!full_ok) {
+        uint32_t below = 0;
+        for (uint32_t c = lane; c < fold; c += 32) below += priority(bs[c], sp) < th;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) below += __shfl_xor_sync(0xFFFFFFFFu, below, o);
+        exact = below + got >= g.R;
+      }
     }
     __syncwarp();
+    if (lane == 0) cnt[key] = 0u;
+    if (!exact) {
+      if (lane == 0) {
+        const uint32_t i = atomicAdd(nfb, 1u);
+        fb[2 * i] = (uint32_t)key;
+        fb[2 * i + 1] = n;
+        meta[key].y = kFallback;
+        meta[key].w = i;
+      }
+      continue;
+    }
+    if (lane == 0) meta[key].w = 0u;
+    if (got == 0) continue;  // nothing below the threshold: the bucket is unchanged
+    const uint32_t tot = fold + got;
+    if (tot > cap_c) {
+      if (lane == 0) {
+        const uint32_t i = atomicAdd(nbig, 1u);
+        big[3 * i] = (uint32_t)key;
+        big[3 * i + 1] = lo;
+        big[3 * i + 2] = got;
+      }
+      continue;
+    }
+    uint32_t mx = 0;
+    for (uint32_t c = lane; c < tot; c += 32) {
+      const uint32_t id = c < fold ? bs[c] : stage[lo + (c - fold)];
+      const uint32_t pr = priority(id, sp);
+      a[c] = pr;
+      mx = max(mx, pr);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    __syncwarp();
     const uint32_t keep = min(tot, g.R);
-    warp_digit_sort(a, b, tot, keep, kScale31, hist[warp], lane);
+    warp_digit_sort(a, b, tot, keep, 32.0f / ((float)mx + 1.0f), hist, lane);
     const uint32_t spm = sp & 0x7FFFFFFFu;
     for (uint32_t c = lane; c < g.R; c += 32) bs[c] = c < keep ? (unmix31(b[c]) ^ spm) : kEmpty;
     if (lane == 0) fill[key] = keep;
@@ -390,73 +513,117 @@ k_merge_small(const __grid_constant__ Geo g, uint64_t nk, const uint32_t* __rest
   }
 }
 
+// Single CTA: staging offsets of the fallback buckets (their full new-pair counts).
+__global__ void __launch_bounds__(1024)
+k_fb_offsets(const uint32_t* __restrict__ fb, const uint32_t* __restrict__ nfb, uint32_t* __restrict__ fboff,
+             uint32_t* __restrict__ fbcur) {
+  __shared__ uint64_t wsum[33];
+  const uint32_t nf = *nfb;
+  uint64_t carry = 0;
+  for (uint32_t base = 0; base < nf; base += blockDim.x) {
+    const uint32_t i = base + threadIdx.x;
+    const uint64_t v = i < nf ? fb[2 * i + 1] : 0;
+    uint64_t tot;
+    const uint64_t ex = block_excl_scan(v, wsum, &tot);
+    if (i < nf) { fboff[i] = (uint32_t)(carry + ex); fbcur[i] = 0u; }
+    carry += tot;
+  }
+}
+
+// Exact fallback: every new id of a fallback bucket is staged.  A small
+// grid-stride pass over all pairs that returns at once when no bucket fell back.
+__global__ void __launch_bounds__(kScatterThreads)
+k_fb_collect(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
+             const uint32_t* __restrict__ bkt, uint64_t ldb, uint32_t n, uint64_t id0,
+             const uint4* __restrict__ meta, const uint32_t* __restrict__ nfb,
+             const uint32_t* __restrict__ fboff, uint32_t* __restrict__ fbcur, uint32_t* __restrict__ stage) {
+  if (*nfb == 0u) return;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint32_t t = 0; t < g.L; ++t) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+      const uint32_t b = bkt[t * ldb + i];
+      const uint64_t id = id0 + i;
+      const uint32_t s = shard_of(sm, g.S, id);
+      const uint64_t key = (((uint64_t)s * g.L + t) << g.B) | b;
+      const uint4 m = meta[key];
+      if (m.y != kFallback) continue;
+      stage[(uint64_t)fboff[m.w] + atomicAdd(&fbcur[m.w], 1u)] = (uint32_t)id;
+    }
+  }
+}
+
 constexpr int kBigThreads = 512;
 
-// CTA per heavy bucket (more than kSmallMax candidates): radix-select the R-th
-// smallest priority in four digit passes, collect the R survivors, sort them.
+// CTA per listed bucket: candidates = old slots + `num` staged ids at `lo`;
+// radix-select the R-th smallest priority in four digit passes, collect the
+// R survivors, sort them.  Lists: big (key, lo, num) or fallback (key, n) with
+// lo from fboff; the fallback entries also clear their cursor.
 __global__ void __launch_bounds__(kBigThreads)
-k_merge_big(const __grid_constant__ Geo g, const uint32_t* __restrict__ off,
-            const uint32_t* __restrict__ stage, uint32_t* __restrict__ slots,
-            uint32_t* __restrict__ fill, const uint32_t* __restrict__ big_keys,
-            const uint32_t* __restrict__ big_count) {
+k_merge_big(const __grid_constant__ Geo g, const uint32_t* __restrict__ list, const uint32_t* __restrict__ nlist,
+            int fallback, const uint32_t* __restrict__ fboff, const uint32_t* __restrict__ stage,
+            uint32_t* __restrict__ slots, uint32_t* __restrict__ fill, uint4* __restrict__ meta) {
   __shared__ uint32_t hist[256];
   __shared__ uint32_t sa[SLASH_MAX_R], sb[SLASH_MAX_R];
   __shared__ uint32_t dh[32];
   __shared__ uint32_t s_prefix, s_need, s_ncol;
-  const uint32_t nbig = *big_count;
+  const uint32_t nl = *nlist;
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  for (uint32_t idx = blockIdx.x; idx < nbig; idx += gridDim.x) {
-    const uint64_t key = big_keys[idx];
-    const uint32_t lo = off[key];
-    const uint32_t cnew = off[key + 1] - lo;
+  for (uint32_t idx = blockIdx.x; idx < nl; idx += gridDim.x) {
+    const uint64_t key = fallback ? list[2 * idx] : list[3 * idx];
+    const uint32_t lo = fallback ? fboff[idx] : list[3 * idx + 1];
+    const uint32_t num = fallback ? list[2 * idx + 1] : list[3 * idx + 2];
     const uint32_t t = (uint32_t)((key >> g.B) % g.L);
     const uint32_t sp = g.sp[t];
     uint32_t* bs = slots + key * g.R;
     const uint32_t fold = fill[key];
-    const uint32_t total = fold + cnew;  // > kSmallMax > R
-    uint32_t prefix = 0, need = g.R;
+    const uint32_t total = fold + num;
+    const uint32_t keep = min(total, g.R);
+    uint32_t prefix = 0x7FFFFFFFu, need = keep;
+    if (total > g.R) {
+      prefix = 0;
 #pragma unroll 1
-    for (int p = 0; p < 4; ++p) {
-      const int sh = p == 3 ? 0 : 23 - 8 * p;     // digits: bits 30..23, 22..15, 14..7, 6..0
-      const int wb = p == 3 ? 7 : 8;
-      const int hs = sh + wb;
-      if (threadIdx.x < 256) hist[threadIdx.x] = 0u;
-      __syncthreads();
-      for (uint32_t c = threadIdx.x; c < total; c += blockDim.x) {
-        const uint32_t id = c < fold ? bs[c] : stage[lo + (c - fold)];
-        const uint32_t pr = priority(id, sp);
-        if (hs >= 31 || (pr >> hs) == (prefix >> hs)) atomicAdd(&hist[(pr >> sh) & ((1u << wb) - 1u)], 1u);
-      }
-      __syncthreads();
-      if (warp == 0) {
-        uint32_t v[8], sum = 0;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) { v[i] = hist[lane * 8 + i]; sum += v[i]; }
-        uint32_t inc = sum;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-          if (lane >= (uint32_t)o) inc += u;
+      for (int p = 0; p < 4; ++p) {
+        const int sh = p == 3 ? 0 : 23 - 8 * p;     // digits: bits 30..23, 22..15, 14..7, 6..0
+        const int wb = p == 3 ? 7 : 8;
+        const int hs = sh + wb;
+        if (threadIdx.x < 256) hist[threadIdx.x] = 0u;
+        __syncthreads();
+        for (uint32_t c = threadIdx.x; c < total; c += blockDim.x) {
+          const uint32_t id = c < fold ? bs[c] : stage[lo + (c - fold)];
+          const uint32_t pr = priority(id, sp);
+          if (hs >= 31 || (pr >> hs) == (prefix >> hs)) atomicAdd(&hist[(pr >> sh) & ((1u << wb) - 1u)], 1u);
         }
-        const uint32_t ex = inc - sum;
-        if (ex < need && need <= inc) {
-          uint32_t cum = ex;
+        __syncthreads();
+        if (warp == 0) {
+          uint32_t v[8], sum = 0;
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            if (cum + v[i] >= need) {
-              s_prefix = prefix | ((lane * 8u + i) << sh);
-              s_need = need - cum;
-              break;
+          for (int i = 0; i < 8; ++i) { v[i] = hist[lane * 8 + i]; sum += v[i]; }
+          uint32_t inc = sum;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= (uint32_t)o) inc += u;
+          }
+          const uint32_t ex = inc - sum;
+          if (ex < need && need <= inc) {
+            uint32_t cum = ex;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              if (cum + v[i] >= need) {
+                s_prefix = prefix | ((lane * 8u + i) << sh);
+                s_need = need - cum;
+                break;
+              }
+              cum += v[i];
             }
-            cum += v[i];
           }
         }
+        __syncthreads();
+        prefix = s_prefix;
+        need = s_need;
       }
-      __syncthreads();
-      prefix = s_prefix;
-      need = s_need;
     }
-    // prefix = the R-th smallest priority: exactly R candidates are <= it
+    // prefix = the keep-th smallest priority: exactly `keep` candidates are <= it
     if (threadIdx.x == 0) s_ncol = 0u;
     __syncthreads();
     for (uint32_t c = threadIdx.x; c < total; c += blockDim.x) {
@@ -468,42 +635,32 @@ k_merge_big(const __grid_constant__ Geo g, const uint32_t* __restrict__ off,
       }
     }
     __syncthreads();
-    if (warp == 0) warp_digit_sort(sa, sb, g.R, g.R, 32.0f / ((float)prefix + 1.0f), dh, lane);
+    if (warp == 0) warp_digit_sort(sa, sb, keep, keep, 32.0f / ((float)prefix + 1.0f), dh, lane);
     __syncthreads();
     const uint32_t spm = sp & 0x7FFFFFFFu;
-    for (uint32_t c = threadIdx.x; c < g.R; c += blockDim.x) bs[c] = unmix31(sb[c]) ^ spm;
-    if (threadIdx.x == 0) fill[key] = g.R;
+    for (uint32_t c = threadIdx.x; c < g.R; c += blockDim.x) bs[c] = c < keep ? (unmix31(sb[c]) ^ spm) : kEmpty;
+    if (threadIdx.x == 0) {
+      fill[key] = keep;
+      if (fallback) meta[key].w = 0u;
+    }
     __syncthreads();
   }
 }
 
 // ----------------------------------------------------------------------------- query
 constexpr uint32_t kHistBins = 256;  // estimate histogram; the last bin holds est >= 255
-constexpr int kGatherUnroll = 4;     // 32-id chunks a warp loads before counting them
+constexpr int kRegIds = 8;           // candidate occurrences a thread keeps in registers
 
-enum { C_NDIST = 0, C_NTOP, C_ESTAR, C_M, C_TIE, C_CAP, C_PREFIX_LO, C_PREFIX_HI, C_NEED, C_NCHUNK, C_ANY,
-       C_Q, C_N };
+enum { C_NPOOL = 0, C_ELO, C_Q, C_N };
 
-// Shared-memory carve-up of one query (byte offsets), fixed per index and k.
+// Shared-memory carve-up of one query (byte offsets), fixed per index.
 struct QueryLayout {
-  uint32_t H, hbits;   // hash-set slots (power of two >= 2 * max candidates) and log2
-  uint32_t maxm;       // max candidate occurrences S*L*R (= max distinct ids)
+  uint32_t maxm;       // max candidate occurrences S*L*R
   uint32_t nbk;        // buckets per query, S*L
-  uint32_t topn;       // top buffer entries (power of two >= k)
-  uint32_t off_top, off_cm, off_set, off_ulist, off_bkey, off_bfill, off_cpre, off_m, off_mask, off_hist,
-      off_ctrl, off_est, bytes;
+  uint32_t maxmult;    // most occurrences one id can have, S*L
+  uint32_t npool;      // pool entries: power of two >= maxm
+  uint32_t off_pool, off_cm, off_bkey, off_bfill, off_pre, off_m, off_mask, off_hist, off_ctrl, bytes;
 };
-
-__device__ __forceinline__ bool set_insert(uint32_t* set, uint32_t H, uint32_t hbits, uint32_t id) {
-  uint32_t i = (id * kGold32) >> (32u - hbits);
-  for (uint32_t probe = 0; probe < H; ++probe) {
-    const uint32_t old = atomicCAS(&set[i], kEmpty, id);
-    if (old == kEmpty) return true;
-    if (old == id) return false;
-    i = (i + 1u) & (H - 1u);
-  }
-  return false;
-}
 
 // 16-bit counters packed two per 32-bit word (exact: no cell exceeds S*L*R <= 65535)
 __device__ __forceinline__ void cm_add(uint32_t* cmw, uint32_t idx) {
@@ -518,65 +675,9 @@ __device__ __forceinline__ uint64_t rank_key(uint32_t est, uint32_t id) {
   return ((uint64_t)(0xFFFFu - est) << 32) | id;
 }
 
-// warp 0 helper: digit holding the need-th smallest count of hist[0..256)
-// (lane l holds bins 8l..8l+7); writes the new prefix/need into ctrl
-__device__ __forceinline__ void pick_digit(const uint32_t* hist, uint32_t need, uint64_t prefix, int sh,
-                                           uint32_t* ctrl, uint32_t lane) {
-  uint32_t v[8], sum = 0;
-#pragma unroll
-  for (int i = 0; i < 8; ++i) { v[i] = hist[lane * 8 + i]; sum += v[i]; }
-  uint32_t inc = sum;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-    if (lane >= (uint32_t)o) inc += u;
-  }
-  const uint32_t ex = inc - sum;
-  if (ex < need && need <= inc) {
-    uint32_t cum = ex;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if (cum + v[i] >= need) {
-        const uint64_t np = prefix | ((uint64_t)(lane * 8u + i) << sh);
-        ctrl[C_PREFIX_LO] = (uint32_t)np;
-        ctrl[C_PREFIX_HI] = (uint32_t)(np >> 32);
-        ctrl[C_NEED] = need - cum;
-        break;
-      }
-      cum += v[i];
-    }
-  }
-}
-
-// Block-wide: among distinct candidates whose estimate bin is estar, the m-th
-// smallest key (key = id, or rank_key when estar is the capped bin).
-__device__ uint64_t tie_select(const uint32_t* ulist, const uint16_t* est, uint32_t nd, uint32_t estar,
-                               bool capped, uint32_t m, uint32_t* hist, uint32_t* ctrl) {
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-  uint64_t prefix = 0;
-  uint32_t need = m;
-  const int top = capped ? 48 : 32;
-  for (int sh = top - 8; sh >= 0; sh -= 8) {
-    for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0u;
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < nd; i += blockDim.x) {
-      const uint32_t e = est[i];
-      if (min(e, kHistBins - 1u) != estar) continue;
-      const uint64_t kk = capped ? rank_key(e, ulist[i]) : (uint64_t)ulist[i];
-      if ((kk >> (sh + 8)) == (prefix >> (sh + 8))) atomicAdd(&hist[(kk >> sh) & 255u], 1u);
-    }
-    __syncthreads();
-    if (warp == 0) pick_digit(hist, need, prefix, sh, ctrl, lane);
-    __syncthreads();
-    prefix = ((uint64_t)ctrl[C_PREFIX_HI] << 32) | ctrl[C_PREFIX_LO];
-    need = ctrl[C_NEED];
-  }
-  return prefix;
-}
-
-// exclusive scan of a[0..n) into out[0..n] (out[n] = total), whole CTA, n small
+// exclusive scan of a[0..n) into out[0..n] (out[n] = total), whole CTA, n <= 8192
 __device__ __forceinline__ void block_scan_small(const uint32_t* a, uint32_t* out, uint32_t n, uint32_t* tmp) {
-  // each warp scans 32-element segments sequentially; segment totals chained by thread 0
+  // each warp scans 32-element segments; segment totals chained by thread 0
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const uint32_t nseg = (n + 31u) / 32u;
   for (uint32_t sg = warp; sg < nseg; sg += nwarp) {
@@ -602,139 +703,150 @@ __device__ __forceinline__ void block_scan_small(const uint32_t* a, uint32_t* ou
   __syncthreads();
 }
 
-// Algorithm 2 for one query whose S*L bucket keys are in bkey[] (smem, synced):
-// gather every shard's L buckets into one count-min sketch (= the sum of the
-// shards' sketches), estimate each distinct candidate, write the top-k by
-// (estimate desc, id asc).
+// occurrence i of the candidate multiset (bucket order): binary search over the fill prefix
+__device__ __forceinline__ uint32_t occurrence(const Geo& g, const uint32_t* __restrict__ slots,
+                                               const uint32_t* bkey, const uint32_t* pre, uint32_t nbk,
+                                               uint32_t i) {
+  uint32_t lo = 0, hi = nbk;  // bucket b with pre[b] <= i < pre[b+1]
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (pre[mid] <= i) lo = mid; else hi = mid;
+  }
+  return __ldg(slots + (uint64_t)bkey[lo] * g.R + (i - pre[lo]));
+}
+
+__device__ __forceinline__ uint32_t estimate(const Geo& g, const uint32_t* cmw, uint32_t id) {
+  uint32_t e = 0xFFFFu;
+  for (uint32_t r = 0; r < g.d; ++r) e = min(e, cm_get(cmw, r * g.w + cm_cell(id, g.sc[r], g.w - 1u)));
+  return e;
+}
+
+// Algorithm 2 for one query whose S*L bucket keys are in bkey[] (smem, synced).
+//  1. every shard's L buckets are counted into one count-min sketch (= the
+//     cell-wise sum of the shards' sketches); each thread keeps its
+//     candidate occurrences in registers;
+//  2. every occurrence reads its estimate; a histogram of estimates gives a
+//     lower bound on the number of DISTINCT ids per estimate (an id with
+//     estimate e occurs at most min(e, S*L) times), which fixes a cut-off
+//     e_lo that keeps at least k distinct ids -- so every top-k id is above it;
+//  3. the occurrences at or above e_lo are pooled, sorted by (estimate desc,
+//     id asc) and the first k distinct keys are written.
+// No per-query hash set: duplicates are only resolved inside the small pool.
 __device__ void query_core(const Geo& g, const QueryLayout& lay, unsigned char* qsm,
                            const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill,
                            uint32_t k, int32_t* __restrict__ ids_out, uint32_t* __restrict__ scores_out) {
-  uint64_t* top = reinterpret_cast<uint64_t*>(qsm + lay.off_top);
+  uint64_t* pool = reinterpret_cast<uint64_t*>(qsm + lay.off_pool);
   uint32_t* cmw = reinterpret_cast<uint32_t*>(qsm + lay.off_cm);
-  uint32_t* set = reinterpret_cast<uint32_t*>(qsm + lay.off_set);
-  uint32_t* ulist = reinterpret_cast<uint32_t*>(qsm + lay.off_ulist);
   const uint32_t* bkey = reinterpret_cast<const uint32_t*>(qsm + lay.off_bkey);
   uint32_t* bfill = reinterpret_cast<uint32_t*>(qsm + lay.off_bfill);
-  uint32_t* cpre = reinterpret_cast<uint32_t*>(qsm + lay.off_cpre);
+  uint32_t* pre = reinterpret_cast<uint32_t*>(qsm + lay.off_pre);
   uint32_t* hist = reinterpret_cast<uint32_t*>(qsm + lay.off_hist);
   uint32_t* ctrl = reinterpret_cast<uint32_t*>(qsm + lay.off_ctrl);
-  uint16_t* est = reinterpret_cast<uint16_t*>(qsm + lay.off_est);
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const uint32_t H = lay.H, wmask = g.w - 1u, cmwords = (g.d * g.w) >> 1, nbk = lay.nbk;
-  // -- clear the sketch and the set; fetch the fill of every bucket (chunks of 32 ids)
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, T = blockDim.x;
+  const uint32_t wmask = g.w - 1u, cmwords = (g.d * g.w) >> 1, nbk = lay.nbk;
+  // -- clear the sketch; fetch every bucket's fill
   uint4* cm4 = reinterpret_cast<uint4*>(cmw);
-  for (uint32_t i = threadIdx.x; i < cmwords / 4; i += blockDim.x) cm4[i] = make_uint4(0, 0, 0, 0);
-  uint4* set4 = reinterpret_cast<uint4*>(set);
-  for (uint32_t i = threadIdx.x; i < H / 4; i += blockDim.x) set4[i] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
-  for (uint32_t i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
+  for (uint32_t i = threadIdx.x; i < cmwords / 4; i += T) cm4[i] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x < C_Q) ctrl[threadIdx.x] = 0u;
-  for (uint32_t i = threadIdx.x; i < nbk; i += blockDim.x) bfill[i] = (fill[bkey[i]] + 31u) >> 5;
+  for (uint32_t i = threadIdx.x; i < nbk; i += T) bfill[i] = fill[bkey[i]];
   __syncthreads();
-  block_scan_small(bfill, cpre, nbk, hist);   // chunk prefix; hist used as scratch
-  for (uint32_t i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
-  const uint32_t nchunk = cpre[nbk];
-  // -- merge: warps take 32-id chunks, kGatherUnroll loads in flight per lane
-  for (uint32_t c0 = warp * kGatherUnroll; c0 < nchunk; c0 += nwarp * kGatherUnroll) {
-    uint32_t idv[kGatherUnroll];
+  block_scan_small(bfill, pre, nbk, hist);  // hist as scratch
+  for (uint32_t i = threadIdx.x; i < kHistBins; i += T) hist[i] = 0u;
+  const uint32_t M = pre[nbk];
+  // -- the candidate multiset into registers, then the sketch
+  uint32_t idv[kRegIds];
 #pragma unroll
-    for (int u = 0; u < kGatherUnroll; ++u) {
-      idv[u] = kEmpty;
-      const uint32_t c = c0 + u;
-      if (c < nchunk) {
-        uint32_t lo = 0, hi = nbk;  // bucket with cpre[b] <= c < cpre[b+1]
-        while (hi - lo > 1) { const uint32_t mid = (lo + hi) >> 1; if (cpre[mid] <= c) lo = mid; else hi = mid; }
-        const uint32_t key = bkey[lo];
-        const uint32_t j = (c - cpre[lo]) * 32u + lane;
-        if (j < fill[key]) idv[u] = __ldg(slots + (uint64_t)key * g.R + j);
-      }
-    }
+  for (int u = 0; u < kRegIds; ++u) {
+    const uint32_t i = threadIdx.x + u * T;
+    idv[u] = i < M ? occurrence(g, slots, bkey, pre, nbk, i) : kEmpty;
+  }
 #pragma unroll
-    for (int u = 0; u < kGatherUnroll; ++u) {
-      const uint32_t id = idv[u];
-      if (id == kEmpty) continue;
-      for (uint32_t r = 0; r < g.d; ++r) cm_add(cmw, r * g.w + cm_cell(id, g.sc[r], wmask));
-      if (set_insert(set, H, lay.hbits, id)) ulist[atomicAdd(&ctrl[C_NDIST], 1u)] = id;
-    }
+  for (int u = 0; u < kRegIds; ++u)
+    if (idv[u] != kEmpty)
+      for (uint32_t r = 0; r < g.d; ++r) cm_add(cmw, r * g.w + cm_cell(idv[u], g.sc[r], wmask));
+  for (uint32_t i = threadIdx.x + kRegIds * T; i < M; i += T) {  // beyond the register budget
+    const uint32_t id = occurrence(g, slots, bkey, pre, nbk, i);
+    for (uint32_t r = 0; r < g.d; ++r) cm_add(cmw, r * g.w + cm_cell(id, g.sc[r], wmask));
   }
   __syncthreads();
-  const uint32_t nd = ctrl[C_NDIST];
-  // -- estimate of every distinct candidate; histogram of estimates
-  for (uint32_t i = threadIdx.x; i < nd; i += blockDim.x) {
-    const uint32_t id = ulist[i];
-    uint32_t e = 0xFFFFu;
-    for (uint32_t r = 0; r < g.d; ++r) e = min(e, cm_get(cmw, r * g.w + cm_cell(id, g.sc[r], wmask)));
-    est[i] = (uint16_t)e;
-    atomicAdd(&hist[min(e, kHistBins - 1u)], 1u);
+  // -- estimates and their histogram
+  uint32_t ev[kRegIds];
+#pragma unroll
+  for (int u = 0; u < kRegIds; ++u) {
+    ev[u] = 0u;
+    if (idv[u] != kEmpty) {
+      ev[u] = estimate(g, cmw, idv[u]);
+      atomicAdd(&hist[min(ev[u], kHistBins - 1u)], 1u);
+    }
   }
+  for (uint32_t i = threadIdx.x + kRegIds * T; i < M; i += T)
+    atomicAdd(&hist[min(estimate(g, cmw, occurrence(g, slots, bkey, pre, nbk, i)), kHistBins - 1u)], 1u);
   __syncthreads();
-  // -- threshold bin: fewer than k candidates above it, at least k at or above it
+  // -- cut-off: the largest bin e_lo whose bins at or above it surely hold >= k distinct ids
   if (warp == 0) {
-    if (nd <= k) {
-      if (lane == 0) { ctrl[C_ESTAR] = 0u; ctrl[C_M] = 0u; ctrl[C_TIE] = 0u; ctrl[C_CAP] = 0u; }
-    } else {
-      uint32_t v[8], sum = 0;
+    uint32_t v[8], sum = 0;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) { v[i] = hist[kHistBins - 1u - (lane * 8u + i)]; sum += v[i]; }
-      uint32_t inc = sum;
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t bin = kHistBins - 1u - (lane * 8u + i);  // lane 0 holds the top bins
+      const uint32_t div = bin == kHistBins - 1u ? lay.maxmult : max(1u, min(bin, lay.maxmult));
+      v[i] = bin == 0u ? 0u : (hist[bin] + div - 1u) / div;
+      sum += v[i];
+    }
+    uint32_t inc = sum;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-        if (lane >= (uint32_t)o) inc += u;
-      }
-      const uint32_t ex = inc - sum;
-      if (ex < k && k <= inc) {
-        uint32_t cum = ex;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= (uint32_t)o) inc += u;
+    }
+    const uint32_t ex = inc - sum;
+    if (ex < k && k <= inc) {
+      uint32_t cum = ex;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          if (cum + v[i] >= k) {
-            const uint32_t bin = kHistBins - 1u - (lane * 8u + i);
-            ctrl[C_ESTAR] = bin;
-            ctrl[C_M] = k - cum;
-            ctrl[C_TIE] = v[i];
-            ctrl[C_CAP] = bin == kHistBins - 1u;
-            break;
-          }
-          cum += v[i];
-        }
+      for (int i = 0; i < 8; ++i) {
+        cum += v[i];
+        if (cum >= k) { ctrl[C_ELO] = kHistBins - 1u - (lane * 8u + i); break; }
       }
     }
+    // (no lane crosses k: fewer than k ids are certain -> e_lo stays 0, pool everything)
   }
   __syncthreads();
-  const uint32_t estar = ctrl[C_ESTAR], m = ctrl[C_M], tie = ctrl[C_TIE];
-  const bool capped = ctrl[C_CAP] != 0u;
-  // -- candidates strictly above the threshold bin (fewer than k; all of them when nd <= k)
-  for (uint32_t i = threadIdx.x; i < nd; i += blockDim.x) {
-    const uint32_t e = est[i];
-    if (min(e, kHistBins - 1u) > estar) {
-      const uint32_t pos = atomicAdd(&ctrl[C_NTOP], 1u);
-      if (pos < lay.topn) top[pos] = rank_key(e, ulist[i]);
-    }
+  const uint32_t elo = ctrl[C_ELO];
+  // -- pool the occurrences at or above the cut-off
+#pragma unroll
+  for (int u = 0; u < kRegIds; ++u)
+    if (idv[u] != kEmpty && min(ev[u], kHistBins - 1u) >= elo)
+      pool[atomicAdd(&ctrl[C_NPOOL], 1u)] = rank_key(ev[u], idv[u]);
+  for (uint32_t i = threadIdx.x + kRegIds * T; i < M; i += T) {
+    const uint32_t id = occurrence(g, slots, bkey, pre, nbk, i);
+    const uint32_t e = estimate(g, cmw, id);
+    if (min(e, kHistBins - 1u) >= elo) pool[atomicAdd(&ctrl[C_NPOOL], 1u)] = rank_key(e, id);
   }
-  // -- the m best of the threshold bin
-  if (m > 0) {
-    uint64_t thr = ~0ull;
-    if (tie > m) thr = tie_select(ulist, est, nd, estar, capped, m, hist, ctrl);
-    for (uint32_t i = threadIdx.x; i < nd; i += blockDim.x) {
-      const uint32_t e = est[i];
-      if (min(e, kHistBins - 1u) != estar) continue;
-      const uint64_t kk = capped ? rank_key(e, ulist[i]) : (uint64_t)ulist[i];
-      if (kk <= thr) {
-        const uint32_t pos = atomicAdd(&ctrl[C_NTOP], 1u);
-        if (pos < lay.topn) top[pos] = rank_key(e, ulist[i]);
+  __syncthreads();
+  const uint32_t P = ctrl[C_NPOOL];  // <= M <= maxm <= npool
+  const uint32_t n2 = max(2u, next_pow2(P));
+  for (uint32_t i = P + threadIdx.x; i < n2; i += T) pool[i] = ~0ull;
+  __syncthreads();
+  block_bitonic(pool, n2);
+  // -- the first k distinct keys (duplicates of an id are adjacent: same key)
+  if (warp == 0) {
+    uint32_t out = 0;
+    uint64_t carry = ~0ull;
+    for (uint32_t base = 0; base < P && out < k; base += 32) {
+      const uint32_t i = base + lane;
+      const uint64_t key = i < P ? pool[i] : ~0ull;
+      uint64_t prev = __shfl_up_sync(0xFFFFFFFFu, key, 1);
+      if (lane == 0) prev = carry;
+      const bool fresh = i < P && key != prev;
+      const uint32_t mask = __ballot_sync(0xFFFFFFFFu, fresh);
+      const uint32_t rank = out + __popc(mask & ((1u << lane) - 1u));
+      if (fresh && rank < k) {
+        ids_out[rank] = (int32_t)(uint32_t)key;
+        scores_out[rank] = 0xFFFFu - (uint32_t)(key >> 32);
       }
+      out += __popc(mask);
+      carry = __shfl_sync(0xFFFFFFFFu, key, 31);
     }
-  }
-  __syncthreads();
-  const uint32_t ntop = min(ctrl[C_NTOP], k);
-  const uint32_t n2 = max(2u, next_pow2(ntop));
-  for (uint32_t i = ntop + threadIdx.x; i < n2; i += blockDim.x) top[i] = ~0ull;
-  __syncthreads();
-  block_bitonic(top, n2);
-  for (uint32_t j = threadIdx.x; j < k; j += blockDim.x) {
-    if (j < ntop) {
-      ids_out[j] = (int32_t)(uint32_t)top[j];
-      scores_out[j] = 0xFFFFu - (uint32_t)(top[j] >> 32);
-    } else {
+    for (uint32_t j = min(out, k) + lane; j < k; j += 32) {
       ids_out[j] = -1;
       scores_out[j] = 0u;
     }
@@ -842,16 +954,22 @@ struct slash_index {
   uint32_t* bkt = nullptr;
   uint32_t* stage = nullptr;
   uint32_t* cnt = nullptr;       // [nk], zero between calls
-  uint32_t* off = nullptr;       // [nk + 1], offsets within one chunk's stage
   uint64_t* blocksum = nullptr;  // [ceil(nk / kScanTile)]
-  uint32_t* big_keys = nullptr;
-  uint32_t* big_count = nullptr;
-  uint64_t big_cap = 0;
+  uint4* meta = nullptr;         // [nk + 1] {threshold, capacity, stage offset, cursor} of this chunk
+  uint32_t merge_cap = 0;        // candidates a merge warp holds in smem
+  uint32_t* big = nullptr;       // (key, stage offset, survivors) per bucket merged by a CTA
+  uint32_t* fb = nullptr;        // (key, new pairs) per fallback bucket
+  uint32_t* fboff = nullptr;     // staging offset per fallback bucket
+  uint32_t* fbcur = nullptr;     // staging cursor per fallback bucket
+  uint32_t* ctr = nullptr;       // [0] big entries, [1] fallback entries
+  uint64_t big_cap = 0, fb_cap = 0;
+  float sigma = 8.0f;            // filter margin in binomial standard deviations
   // query workspace (grow-only)
   uint64_t qws = 0;
   uint32_t* qbkt = nullptr;
   slash_query_opts qdef{SLASH_QUERY_FUSED, 512, 0};  // default query schedule (autotuned)
   uint32_t* work = nullptr;                          // ring of fused-kernel work counters
+  int qbps[2][3] = {};                               // CTAs/SM per (mode, threads); -1 = does not fit
   std::atomic<uint32_t> work_next{0};                // next ring slot (one per fused launch)
   // per-launch event profile (off unless slash_profile enables it)
   struct ProfRec { const char* name; cudaEvent_t a, b; };
@@ -924,17 +1042,25 @@ uint64_t insert_chunk_rows(const slash_index* ix) {
 int grow_insert_ws(slash_index* ix, uint64_t rows) {
   if (rows <= ix->ws_rows) return SLASH_OK;
   const uint64_t L = ix->p.L;
-  uint32_t *bkt = nullptr, *stage = nullptr, *big = nullptr;
-  const uint64_t big_cap = (L * rows) / (kSmallMax / 2) + 1;  // cnew > 512 per big bucket
-  if (cudaMalloc(&bkt, sizeof(uint32_t) * L * rows) != cudaSuccess) { cudaGetLastError(); return SLASH_ENOMEM; }
-  if (cudaMalloc(&stage, sizeof(uint32_t) * L * rows) != cudaSuccess) {
-    cudaGetLastError(); cudaFree(bkt); return SLASH_ENOMEM;
+  const uint64_t big_cap = (L * rows) / (kSmallMax / 2) + 1;  // > 512 survivors per big bucket
+  const uint64_t fb_cap = std::min<uint64_t>(ix->nk, L * rows);
+  uint32_t *bkt = nullptr, *stage = nullptr, *big = nullptr, *fb = nullptr, *fboff = nullptr, *fbcur = nullptr;
+  cudaError_t e = cudaMalloc(&bkt, sizeof(uint32_t) * L * rows);
+  if (e == cudaSuccess) e = cudaMalloc(&stage, sizeof(uint32_t) * L * rows);
+  if (e == cudaSuccess) e = cudaMalloc(&big, sizeof(uint32_t) * 3 * big_cap);
+  if (e == cudaSuccess) e = cudaMalloc(&fb, sizeof(uint32_t) * 2 * fb_cap);
+  if (e == cudaSuccess) e = cudaMalloc(&fboff, sizeof(uint32_t) * fb_cap);
+  if (e == cudaSuccess) e = cudaMalloc(&fbcur, sizeof(uint32_t) * fb_cap);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(bkt); cudaFree(stage); cudaFree(big); cudaFree(fb); cudaFree(fboff); cudaFree(fbcur);
+    return SLASH_ENOMEM;
   }
-  if (cudaMalloc(&big, sizeof(uint32_t) * big_cap) != cudaSuccess) {
-    cudaGetLastError(); cudaFree(bkt); cudaFree(stage); return SLASH_ENOMEM;
-  }
-  cudaFree(ix->bkt); cudaFree(ix->stage); cudaFree(ix->big_keys);
-  ix->bkt = bkt; ix->stage = stage; ix->big_keys = big; ix->big_cap = big_cap;
+  cudaFree(ix->bkt); cudaFree(ix->stage); cudaFree(ix->big); cudaFree(ix->fb); cudaFree(ix->fboff);
+  cudaFree(ix->fbcur);
+  ix->bkt = bkt; ix->stage = stage; ix->big = big; ix->fb = fb; ix->fboff = fboff; ix->fbcur = fbcur;
+  ix->big_cap = big_cap;
+  ix->fb_cap = fb_cap;
   ix->ws_rows = rows;
   return SLASH_OK;
 }
@@ -950,7 +1076,8 @@ int grow_query_ws(slash_index* ix, uint64_t nq) {
 }
 
 size_t hash_smem(const slash_index* ix) {
-  return sizeof(uint32_t) * ((size_t)kHashWarps * (ix->geo.nb + ix->geo.nw) + (size_t)ix->p.L * kHashRows);
+  const size_t per_warp = (ix->geo.nb + ix->geo.nw + 3u) & ~3u;
+  return sizeof(uint32_t) * ((size_t)kHashWarps * per_warp + (size_t)ix->p.L * kHashRows);
 }
 
 ShardMap shard_map(const slash_index* ix) {
@@ -960,36 +1087,36 @@ ShardMap shard_map(const slash_index* ix) {
   return m;
 }
 
-QueryLayout make_query_layout(const slash_params& p, uint32_t k) {
+QueryLayout make_query_layout(const slash_params& p) {
   QueryLayout l{};
-  const uint32_t maxm = p.shards * p.L * p.reservoir;  // <= 65535 (checked at build)
-  uint32_t H = 64;
-  while (H < 2u * maxm) H <<= 1;
-  l.H = H;
-  l.hbits = 0;
-  while ((1u << l.hbits) < H) ++l.hbits;
-  l.maxm = maxm;
+  l.maxm = p.shards * p.L * p.reservoir;  // <= 65535 (checked at build)
   l.nbk = p.shards * p.L;
-  uint32_t topn = 2;
-  while (topn < k) topn <<= 1;
-  l.topn = topn;
+  l.maxmult = p.shards * p.L;
+  uint32_t np = 2;
+  while (np < l.maxm) np <<= 1;
+  l.npool = np;
   const uint32_t nb = p.K * p.L, nw = (nb + 31) / 32;
   auto al = [](uint32_t x) { return (x + 15u) & ~15u; };
   uint32_t o = 0;
-  l.off_top = o;   o = al(o + topn * 8u);
+  l.off_pool = o;  o = al(o + np * 8u);
   l.off_cm = o;    o = al(o + (p.cm_rows * p.cm_width / 2u) * 4u);
-  l.off_set = o;   o = al(o + H * 4u);
-  l.off_ulist = o; o = al(o + maxm * 4u);
   l.off_bkey = o;  o = al(o + l.nbk * 4u);
   l.off_bfill = o; o = al(o + l.nbk * 4u);
-  l.off_cpre = o;  o = al(o + (l.nbk + 1u) * 4u);
+  l.off_pre = o;   o = al(o + (l.nbk + 1u) * 4u);
   l.off_m = o;     o = al(o + nb * 4u);
   l.off_mask = o;  o = al(o + nw * 4u);
   l.off_hist = o;  o = al(o + kHistBins * 4u);
   l.off_ctrl = o;  o = al(o + 16u * 4u);
-  l.off_est = o;   o = al(o + maxm * 2u);
   l.bytes = o;
   return l;
+}
+
+// default CTA size: enough threads to hold the largest candidate multiset in registers
+uint32_t default_query_threads(const slash_params& p) {
+  const uint32_t maxm = p.shards * p.L * p.reservoir;
+  uint32_t t = 256;
+  while (t < 1024 && t * kRegIds < maxm) t <<= 1;
+  return t;
 }
 
 int run_hash(slash_index* ix, const uint64_t* offs, const uint32_t* cols, uint32_t n, uint64_t id0,
@@ -1009,23 +1136,30 @@ int run_hash(slash_index* ix, const uint64_t* offs, const uint32_t* cols, uint32
   return SLASH_OK;
 }
 
+// One chunk of Algorithm 1: addresses + counts, staging plan, filtered
+// counting-sort scatter, per-bucket merges, exact fallback.
 int insert_chunk(slash_index* ix, const uint64_t* offs, const uint32_t* cols, uint32_t n, uint64_t id0,
                  cudaStream_t st) {
   const uint64_t nk = ix->nk;
   int rc = run_hash(ix, offs, cols, n, id0, ix->bkt, n, nullptr, true, st);
   if (rc) return rc;
+  const uint32_t kblocks = (uint32_t)std::min<uint64_t>((nk + 255) / 256, (uint64_t)ix->num_sms * 32);
+  {
+    Launch l(ix, "k_plan", st);
+    k_plan<<<kblocks, 256, 0, st>>>(ix->geo, nk, ix->cnt, ix->fill, ix->slots, ix->meta, ix->sigma);
+  }
   const uint32_t nblk = (uint32_t)((nk + kScanTile - 1) / kScanTile);
   {
-    Launch l1(ix, "k_scan_reduce", st);
-    k_scan_reduce<<<nblk, kScanThreads, 0, st>>>(ix->cnt, nk, ix->blocksum);
+    Launch l(ix, "k_scan_reduce", st);
+    k_scan_reduce<<<nblk, kScanThreads, 0, st>>>(&ix->meta->y, 4u, nk, ix->blocksum);
   }
   {
-    Launch l2(ix, "k_scan_blocks", st);
+    Launch l(ix, "k_scan_blocks", st);
     k_scan_blocks<<<1, 1024, 0, st>>>(ix->blocksum, nblk);
   }
   {
-    Launch l3(ix, "k_scan_apply", st);
-    k_scan_apply<<<nblk, kScanThreads, 0, st>>>(ix->cnt, nk, ix->blocksum, ix->off);
+    Launch l(ix, "k_scan_apply", st);
+    k_scan_apply<<<nblk, kScanThreads, 0, st>>>(&ix->meta->y, 4u, nk, ix->blocksum, &ix->meta->z, 4u);
   }
   SLASH_CK(cudaGetLastError());
   const ShardMap sm = shard_map(ix);
@@ -1033,21 +1167,37 @@ int insert_chunk(slash_index* ix, const uint64_t* offs, const uint32_t* cols, ui
   const dim3 sgrid((piece_rows + kScatterThreads * kScatterPerThread - 1) / (kScatterThreads * kScatterPerThread),
                    ix->p.L, (n + kScatterPiece - 1) / kScatterPiece);
   {
-    Launch l4(ix, "k_scatter", st);
-    k_scatter<<<sgrid, kScatterThreads, 0, st>>>(ix->geo, sm, ix->bkt, n, n, id0, ix->off, ix->cnt, ix->stage);
+    Launch l(ix, "k_scatter", st);
+    k_scatter<<<sgrid, kScatterThreads, 0, st>>>(ix->geo, sm, ix->bkt, n, n, id0, ix->meta, ix->stage);
   }
-  SLASH_CK(cudaMemsetAsync(ix->big_count, 0, sizeof(uint32_t), st));
-  const uint64_t mblocks = std::min<uint64_t>((nk + kMergeWarps - 1) / kMergeWarps,
-                                              (uint64_t)ix->num_sms * 16);
+  SLASH_CK(cudaMemsetAsync(ix->ctr, 0, 2 * sizeof(uint32_t), st));
+  const uint64_t mblocks = std::min<uint64_t>((nk + kMergeWarps - 1) / kMergeWarps, (uint64_t)ix->num_sms * 16);
+  const size_t msmem = sizeof(uint32_t) * ((size_t)kMergeWarps * 2 * ix->merge_cap + kMergeWarps * 32);
   {
-    Launch l5(ix, "k_merge_small", st);
-    k_merge_small<<<(uint32_t)mblocks, kMergeWarps * 32, 0, st>>>(ix->geo, nk, ix->off, ix->stage, ix->slots,
-                                                                ix->fill, ix->big_keys, ix->big_count);
+    Launch l(ix, "k_merge_small", st);
+    k_merge_small<<<(uint32_t)mblocks, kMergeWarps * 32, msmem, st>>>(ix->geo, nk, ix->merge_cap, ix->cnt, ix->meta,
+                                                                      ix->stage, ix->slots, ix->fill, ix->big,
+                                                                      ix->ctr, ix->fb, ix->ctr + 1);
   }
   {
-    Launch l6(ix, "k_merge_big", st);
-    k_merge_big<<<ix->num_sms * 2, kBigThreads, 0, st>>>(ix->geo, ix->off, ix->stage, ix->slots, ix->fill,
-                                                       ix->big_keys, ix->big_count);
+    Launch l(ix, "k_merge_big", st);
+    k_merge_big<<<ix->num_sms * 2, kBigThreads, 0, st>>>(ix->geo, ix->big, ix->ctr, 0, nullptr, ix->stage,
+                                                       ix->slots, ix->fill, ix->meta);
+  }
+  // exact fallback (does nothing unless a bucket was listed)
+  {
+    Launch l(ix, "k_fb_offsets", st);
+    k_fb_offsets<<<1, 1024, 0, st>>>(ix->fb, ix->ctr + 1, ix->fboff, ix->fbcur);
+  }
+  {
+    Launch l(ix, "k_fb_collect", st);
+    k_fb_collect<<<ix->num_sms * 4, kScatterThreads, 0, st>>>(ix->geo, sm, ix->bkt, n, n, id0, ix->meta,
+                                                              ix->ctr + 1, ix->fboff, ix->fbcur, ix->stage);
+  }
+  {
+    Launch l(ix, "k_merge_fallback", st);
+    k_merge_big<<<ix->num_sms * 2, kBigThreads, 0, st>>>(ix->geo, ix->fb, ix->ctr + 1, 1, ix->fboff, ix->stage,
+                                                       ix->slots, ix->fill, ix->meta);
   }
   SLASH_CK(cudaGetLastError());
   return SLASH_OK;
@@ -1114,8 +1264,23 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
   for (uint32_t j = 0; j < g.nb; ++j)
     if (mix32(j ^ g.dirseed) & 1u) g.dirbits[j >> 5] |= 1u << (j & 31u);
   ix->nk = ((uint64_t)p->shards * p->L) << p->log2_buckets;
+  if (const char* env = std::getenv("SLASH_FILTER_SIGMA")) {
+    const double v = std::atof(env);
+    if (v >= 0.0 && v < 1e3) ix->sigma = (float)v;
+  }
   {
-    const QueryLayout l = make_query_layout(*p, SLASH_MAX_TOPK);
+    // largest candidate count of a merge: R old ids + the staged ids, which are
+    // at most 1.5 mu unfiltered, or the filtered capacity mu + sigma sqrt(mu) + 16
+    const double sg = ix->sigma, R = p->reservoir;
+    const double mu = R + sg * std::sqrt(R) + (sg > 0 ? 16.0 : 0.0);
+    const double most = R + std::max(1.5 * mu, mu + sg * std::sqrt(mu) + 16.0) + 1.0;
+    uint32_t c = 64;
+    while (c < most && c < kSmallMax) c <<= 1;
+    ix->merge_cap = c;  // buckets beyond it take the CTA merge
+  }
+  ix->qdef.threads = default_query_threads(*p);
+  {
+    const QueryLayout l = make_query_layout(*p);
     if (l.bytes > ix->smem_optin || hash_smem(ix) > ix->smem_optin) { delete ix; return SLASH_EINVAL; }
   }
   const uint64_t nblk = (ix->nk + kScanTile - 1) / kScanTile;
@@ -1123,14 +1288,15 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
   if (e == cudaSuccess) e = cudaMalloc(&ix->slots, sizeof(uint32_t) * ix->nk * p->reservoir);
   if (e == cudaSuccess) e = cudaMalloc(&ix->fill, sizeof(uint32_t) * ix->nk);
   if (e == cudaSuccess) e = cudaMalloc(&ix->cnt, sizeof(uint32_t) * ix->nk);
-  if (e == cudaSuccess) e = cudaMalloc(&ix->off, sizeof(uint32_t) * (ix->nk + 1));
   if (e == cudaSuccess) e = cudaMalloc(&ix->blocksum, sizeof(uint64_t) * nblk);
   if (e == cudaSuccess) e = cudaMalloc(&ix->err, sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&ix->big_count, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&ix->meta, sizeof(uint4) * (ix->nk + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&ix->ctr, sizeof(uint32_t) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&ix->work, sizeof(uint32_t) * kWorkRing);
   if (e == cudaSuccess) e = cudaMemsetAsync(ix->slots, 0xFF, sizeof(uint32_t) * ix->nk * p->reservoir, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ix->fill, 0, sizeof(uint32_t) * ix->nk, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ix->cnt, 0, sizeof(uint32_t) * ix->nk, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ix->meta, 0, sizeof(uint4) * (ix->nk + 1), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ix->err, 0, sizeof(uint32_t), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
@@ -1146,6 +1312,7 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
   cudaFuncSetAttribute(k_query_fused<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_query_fused<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_query_fused<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_merge_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ix->smem_optin);
   cudaFuncSetAttribute(k_hash<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ix->smem_optin);
   cudaFuncSetAttribute(k_hash<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ix->smem_optin);
   *out = ix;
@@ -1182,20 +1349,28 @@ int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
   if (!ix || topk == 0 || topk > SLASH_MAX_TOPK) return SLASH_EINVAL;
   const slash_query_opts o = opts ? *opts : ix->qdef;
   if (o.mode != SLASH_QUERY_PLAIN && o.mode != SLASH_QUERY_FUSED) return SLASH_EINVAL;
-  const uint32_t thr = o.threads ? o.threads : 512u;
+  const uint32_t thr = o.threads ? o.threads : default_query_threads(ix->p);
   if (thr != 256u && thr != 512u && thr != 1024u) return SLASH_EINVAL;
   if (n_queries == 0) return SLASH_OK;
   if (!d_offs || !d_cols || !d_ids_out || !d_scores_out) return SLASH_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  const QueryLayout lay = make_query_layout(ix->p, topk);
+  const QueryLayout lay = make_query_layout(ix->p);
   const void* fn = nullptr;
   if (o.mode == SLASH_QUERY_PLAIN)
     fn = thr == 256 ? (const void*)k_query<256> : thr == 512 ? (const void*)k_query<512> : (const void*)k_query<1024>;
   else
     fn = thr == 256 ? (const void*)k_query_fused<256>
                     : thr == 512 ? (const void*)k_query_fused<512> : (const void*)k_query_fused<1024>;
-  int bps = 0;
-  SLASH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, (int)thr, lay.bytes));
+  // resident CTAs per SM for this schedule, looked up once per index (so that
+  // later calls, e.g. under stream capture, make no occupancy query)
+  const int ti = thr == 256 ? 0 : thr == 512 ? 1 : 2;
+  int& cached = ix->qbps[o.mode == SLASH_QUERY_PLAIN ? 1 : 0][ti];
+  if (cached == 0) {
+    int b = 0;
+    SLASH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, (int)thr, lay.bytes));
+    cached = b > 0 ? b : -1;
+  }
+  int bps = cached;
   if (bps < 1) return SLASH_EINVAL;
   if (o.ctas_per_sm) bps = std::min<int>(bps, (int)o.ctas_per_sm);
   const uint64_t slots_per_gpu = (uint64_t)ix->num_sms * bps;
@@ -1284,8 +1459,9 @@ int slash_free(slash_index* ix) {
   if (!ix) return SLASH_OK;
   cudaDeviceSynchronize();
   cudaFree(ix->slots); cudaFree(ix->fill); cudaFree(ix->err);
-  cudaFree(ix->bkt); cudaFree(ix->stage); cudaFree(ix->cnt); cudaFree(ix->off);
-  cudaFree(ix->blocksum); cudaFree(ix->big_keys); cudaFree(ix->big_count); cudaFree(ix->qbkt);
+  cudaFree(ix->bkt); cudaFree(ix->stage); cudaFree(ix->cnt);
+  cudaFree(ix->blocksum); cudaFree(ix->meta); cudaFree(ix->big);
+  cudaFree(ix->fb); cudaFree(ix->fboff); cudaFree(ix->fbcur); cudaFree(ix->ctr); cudaFree(ix->qbkt);
   cudaFree(ix->work);
   for (auto& r : ix->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ix->prof_pool) cudaEventDestroy(e);
@@ -1440,7 +1616,7 @@ extern "C" int slash_query_static(slash_index* ix, const uint64_t* d_offs, const
   int rc = static_scratch(cur, &qbkt);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  const QueryLayout lay = make_query_layout(ix->p, topk);
+  const QueryLayout lay = make_query_layout(ix->p);
   int bps = 0;
   SLASH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_query<512>, 512, lay.bytes));
   if (bps < 1) return SLASH_EINVAL;

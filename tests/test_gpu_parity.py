@@ -287,3 +287,50 @@ def test_uneven_queries_bit_exact():
             ix.sync()
             assert np.array_equal(ids.cpu().numpy(), want_ids), mode
             assert np.array_equal(_host_u32(sc), want_sc), mode
+
+
+@pytest.mark.parametrize("sigma", ["0", "0.5", "3"])
+def test_insert_filter_and_exact_fallback_bit_exact(sigma, monkeypatch):
+    """The staging filter keeps ~R + sigma*sqrt(R) of a heavy bucket's new ids and
+    proves in the merge that nothing below the R-th priority was dropped; with a
+    small sigma that proof often fails (or the staging overflows) and the
+    bucket takes the exact fallback.  Every sigma gives the oracle's index."""
+    monkeypatch.setenv("SLASH_FILTER_SIGMA", sigma)
+    s = _slash()
+    g = datagen.Generator()
+    n = 40_000
+    offs, cols = g.rows(14, 0, n)
+    p = s.Params(K=4, L=16, log2_buckets=5, reservoir=32, cm_rows=4, cm_width=4096, capacity=n, seed=14)
+    want_slots, want_fill = _oracle_index(p, offs, cols).export()
+    with s.Index(p) as ix:
+        _gpu_insert(ix, offs, cols, [0, 3000, 3001, 25_000, n])
+        ix.sync()
+        slots, fill = ix.export()
+    assert np.array_equal(fill, want_fill) and np.array_equal(slots, want_slots)
+
+
+def test_streamed_device_rows_top100_bit_exact():
+    """The `stream` shape scaled down: K=8, L=32, R=256, rows generated on the
+    device chunk by chunk and inserted without being stored; top-100 queries."""
+    from datagen.workloads import STREAM as w
+    s = _slash()
+    g = datagen.Generator()
+    dg = datagen.DeviceRows(g)
+    n, chunk = 200_000, 60_000
+    p = s.Params(**w.params(capacity=n, log2_buckets=12))
+    with s.Index(p) as ix:
+        for r0 in range(0, n, chunk):
+            o, c = dg.rows(w.seed, r0, min(chunk, n - r0))
+            ix.insert(o, c)
+        offs, cols = g.rows(w.seed, 0, n)
+        qo, qc, src = g.queries(w.seed, w.qseed, 400, n, **w.query_kwargs())
+        ids, sc = ix.query(_dev(qo), _dev(qc), w.topk)
+        ix.sync()
+        slots, fill = ix.export()
+    oix = _oracle_index(p, offs, cols)
+    ws, wf = oix.export()
+    assert np.array_equal(fill, wf) and np.array_equal(slots, ws)
+    want_ids, want_sc = oix.query(qo, qc, w.topk)
+    assert np.array_equal(ids.cpu().numpy(), want_ids)
+    assert np.array_equal(_host_u32(sc), want_sc)
+    assert np.mean((ids.cpu().numpy() == src[:, None]).any(axis=1)) > 0.9  # planted rows are found
