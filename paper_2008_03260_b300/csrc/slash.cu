@@ -193,6 +193,124 @@ k_hash(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
   }
 }
 
+// Specialisation for nb = 32*C bins with C a multiple of K (each lane's chunk
+// of C bins holds C/K whole tables): the lane keeps its chunk's codes in
+// registers and computes its own tables from them.  The bin minima live in a
+// padded smem row (bin j at j + j/C): with C+1 odd, the 32 lanes' chunk reads
+// hit 32 different banks.  Non-empty bins are recognised by value; the one
+// feature whose hash is 0xFFFFFFFF (it lands in bin nb-1) is flagged apart.
+template <int C, int K, bool kCount>
+__global__ void __launch_bounds__(kHashWarps * 32)
+k_hash_reg(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
+           const uint64_t* __restrict__ offs, const uint32_t* __restrict__ cols, uint32_t n, uint64_t id0,
+           uint32_t* __restrict__ bkt, uint64_t ldb, uint32_t* __restrict__ codes,
+           uint32_t* __restrict__ cnt, uint32_t* __restrict__ err) {
+  constexpr uint32_t NB = 32u * C, TPL = C / K, ROW = ((NB + 32u + 1u) + 3u) & ~3u;  // padded row + flag
+  extern __shared__ uint32_t smem[];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  uint32_t* m = smem + warp * ROW;        // padded bin minima; m[ROW-1] = flag word
+  uint32_t* flag = m + ROW - 1u;
+  uint32_t* tile = smem + kHashWarps * ROW;  // [L][kHashRows]
+  const uint64_t row0 = (uint64_t)blockIdx.x * kHashRows;
+  for (uint32_t kk = 0; kk < kRowsPerWarp; ++kk) {
+    const uint32_t lr = warp * kRowsPerWarp + kk;
+    const uint64_t r = row0 + lr;
+    if (r >= n) break;
+    uint64_t b0 = offs[r], b1 = offs[r + 1];
+    if (b1 < b0) {
+      if (lane == 0) atomicOr(err, kErrOffs);
+      b1 = b0;
+    }
+    uint4* m4 = reinterpret_cast<uint4*>(m);
+    for (uint32_t j = lane; j < ROW / 4u; j += 32) m4[j] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+    __syncwarp();
+    if (lane == 0) *flag = 0u;
+    __syncwarp();
+    bool bad = false;
+    for (uint64_t i = b0 + lane; i < b1; i += 32) {
+      const uint32_t f = __ldg(cols + i);
+      if (f >= g.dim) { bad = true; continue; }
+      const uint32_t h = mix32(f ^ g.a);
+      const uint32_t bin = __umulhi(h, NB);
+      atomicMin(&m[bin + bin / C], h);
+      if (h == kEmpty) atomicOr(flag, 1u);
+    }
+    if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(err, kErrCol);
+    __syncwarp();
+    // my chunk: bins [lane*C, lane*C + C) at m[lane*(C+1) + p]
+    uint32_t v[C];
+    uint32_t cb = 0u;
+#pragma unroll
+    for (int p = 0; p < C; ++p) {
+      v[p] = m[lane * (C + 1) + p];
+      cb |= (uint32_t)(v[p] != kEmpty) << p;
+    }
+    if (lane == 31u && *flag) cb |= 1u << (C - 1);  // bin nb-1 holds the 0xFFFFFFFF feature
+    uint32_t code[C];
+    if (__any_sync(0xFFFFFFFFu, cb != 0u)) {
+      constexpr uint32_t kNone = 0xFFFFFFFFu;
+      const uint32_t lo = lane * C;
+      const uint32_t first = cb ? lo + (uint32_t)(__ffs(cb) - 1) : kNone;
+      const uint32_t last = cb ? lo + 31u - (uint32_t)__clz(cb) : kNone;
+      uint32_t rn = __shfl_sync(0xFFFFFFFFu, first, (lane + 1u) & 31u);
+      uint32_t ln = __shfl_sync(0xFFFFFFFFu, last, (lane + 31u) & 31u);
+#pragma unroll
+      for (uint32_t d = 1; d < 32; d <<= 1) {
+        const uint32_t ro = __shfl_sync(0xFFFFFFFFu, rn, (lane + d) & 31u);
+        const uint32_t lo2 = __shfl_sync(0xFFFFFFFFu, ln, (lane + 32u - d) & 31u);
+        if (rn == kNone) rn = ro;
+        if (ln == kNone) ln = lo2;
+      }
+      // values of the nearest non-empty bins beyond my chunk on either side (circular)
+      const uint32_t vr = m[rn + rn / C], vl = m[ln + ln / C];
+      const uint32_t w = lo >> 5, s = lo & 31u;
+      const uint64_t dw = ((uint64_t)(w + 1 < g.nw ? g.dirbits[w + 1] : 0u) << 32) | g.dirbits[w];
+      const uint32_t db = (uint32_t)(dw >> s);
+      // right neighbours: scan the chunk from its right end; left: from its left end
+      uint32_t right[C];
+      uint32_t nxt = vr;
+#pragma unroll
+      for (int p = C - 1; p >= 0; --p) {
+        right[p] = nxt;
+        if ((cb >> p) & 1u) nxt = v[p];
+      }
+      uint32_t prv = vl;
+#pragma unroll
+      for (int p = 0; p < C; ++p) {
+        const bool full = (cb >> p) & 1u;
+        code[p] = full ? v[p] : (((db >> p) & 1u) ? right[p] : prv);
+        if (full) prv = v[p];
+      }
+    } else {
+#pragma unroll
+      for (int p = 0; p < C; ++p) code[p] = kEmpty;  // empty row
+    }
+    uint32_t s = 0;
+    if (kCount) s = shard_of(sm, g.S, id0 + r);
+#pragma unroll
+    for (int tt = 0; tt < TPL; ++tt) {
+      const uint32_t t = lane * TPL + tt;
+      uint32_t acc = g.st[t];
+#pragma unroll
+      for (int j = 0; j < K; ++j) acc = (acc ^ code[tt * K + j]) * kGold32;
+      const uint32_t b = mix32(acc) >> (32u - g.B);
+      tile[t * kHashRows + lr] = b;
+      if (kCount) atomicAdd(&cnt[(((uint64_t)s * g.L + t) << g.B) | b], 1u);
+    }
+    if (codes) {
+#pragma unroll
+      for (int p = 0; p < C; ++p) codes[r * NB + lane * C + p] = code[p];
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  for (uint32_t idx = threadIdx.x; idx < g.L * kHashRows; idx += blockDim.x) {
+    const uint32_t t = idx / kHashRows, lr = idx - t * kHashRows;
+    const uint64_t r = row0 + lr;
+    if (r < n) bkt[t * ldb + r] = tile[idx];
+  }
+}
+
 // ----------------------------------------------------------------------------- scan
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
@@ -651,7 +769,7 @@ k_merge_big(const __grid_constant__ Geo g, const uint32_t* __restrict__ list, co
 constexpr uint32_t kHistBins = 256;  // estimate histogram; the last bin holds est >= 255
 constexpr int kRegIds = 8;           // candidate occurrences a thread keeps in registers
 
-enum { C_NPOOL = 0, C_ELO, C_Q, C_N };
+enum { C_NPOOL = 0, C_ELO, C_PFX, C_NEED, C_Q, C_N };
 
 // Shared-memory carve-up of one query (byte offsets), fixed per index.
 struct QueryLayout {
@@ -659,7 +777,9 @@ struct QueryLayout {
   uint32_t nbk;        // buckets per query, S*L
   uint32_t maxmult;    // most occurrences one id can have, S*L
   uint32_t npool;      // pool entries: power of two >= maxm
-  uint32_t off_pool, off_cm, off_bkey, off_bfill, off_pre, off_m, off_mask, off_hist, off_ctrl, bytes;
+  uint32_t nchunkmax;  // most 32-id chunks of a query: S*L*ceil(R/32)
+  uint32_t off_pool, off_cm, off_bkey, off_bfill, off_pre, off_m, off_mask, off_hist, off_ctrl, off_cbk,
+      off_cells, bytes;
 };
 
 // 16-bit counters packed two per 32-bit word (exact: no cell exceeds S*L*R <= 65535)
@@ -703,18 +823,6 @@ __device__ __forceinline__ void block_scan_small(const uint32_t* a, uint32_t* ou
   __syncthreads();
 }
 
-// occurrence i of the candidate multiset (bucket order): binary search over the fill prefix
-__device__ __forceinline__ uint32_t occurrence(const Geo& g, const uint32_t* __restrict__ slots,
-                                               const uint32_t* bkey, const uint32_t* pre, uint32_t nbk,
-                                               uint32_t i) {
-  uint32_t lo = 0, hi = nbk;  // bucket b with pre[b] <= i < pre[b+1]
-  while (hi - lo > 1) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (pre[mid] <= i) lo = mid; else hi = mid;
-  }
-  return __ldg(slots + (uint64_t)bkey[lo] * g.R + (i - pre[lo]));
-}
-
 __device__ __forceinline__ uint32_t estimate(const Geo& g, const uint32_t* cmw, uint32_t id) {
   uint32_t e = 0xFFFFu;
   for (uint32_t r = 0; r < g.d; ++r) e = min(e, cm_get(cmw, r * g.w + cm_cell(id, g.sc[r], g.w - 1u)));
@@ -723,15 +831,20 @@ __device__ __forceinline__ uint32_t estimate(const Geo& g, const uint32_t* cmw, 
 
 // Algorithm 2 for one query whose S*L bucket keys are in bkey[] (smem, synced).
 //  1. every shard's L buckets are counted into one count-min sketch (= the
-//     cell-wise sum of the shards' sketches); each thread keeps its
-//     candidate occurrences in registers;
+//     cell-wise sum of the shards' sketches); warps take 32-id chunks of the
+//     buckets and keep their candidate occurrences in registers;
 //  2. every occurrence reads its estimate; a histogram of estimates gives a
 //     lower bound on the number of DISTINCT ids per estimate (an id with
 //     estimate e occurs at most min(e, S*L) times), which fixes a cut-off
-//     e_lo that keeps at least k distinct ids -- so every top-k id is above it;
-//  3. the occurrences at or above e_lo are pooled, sorted by (estimate desc,
-//     id asc) and the first k distinct keys are written.
-// No per-query hash set: duplicates are only resolved inside the small pool.
+//     bin e_lo holding, together with the bins above it, at least k distinct
+//     ids -- so every top-k id is at or above e_lo.  The bins strictly above
+//     e_lo hold fewer than k*S*L occurrences;
+//  3. those are pooled; from bin e_lo itself (ties on the estimate, ranked by
+//     id) only the m*mu smallest ids are needed (m = k, mu = the bin's most
+//     occurrences per id): a radix select over the occurrences in registers
+//     finds that id bound;
+//  4. the pool is sorted by (estimate desc, id asc) and the first k distinct
+//     keys are written (duplicates of an id share its key and are adjacent).
 __device__ void query_core(const Geo& g, const QueryLayout& lay, unsigned char* qsm,
                            const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill,
                            uint32_t k, int32_t* __restrict__ ids_out, uint32_t* __restrict__ scores_out) {
@@ -739,34 +852,69 @@ __device__ void query_core(const Geo& g, const QueryLayout& lay, unsigned char* 
   uint32_t* cmw = reinterpret_cast<uint32_t*>(qsm + lay.off_cm);
   const uint32_t* bkey = reinterpret_cast<const uint32_t*>(qsm + lay.off_bkey);
   uint32_t* bfill = reinterpret_cast<uint32_t*>(qsm + lay.off_bfill);
-  uint32_t* pre = reinterpret_cast<uint32_t*>(qsm + lay.off_pre);
+  uint32_t* cpre = reinterpret_cast<uint32_t*>(qsm + lay.off_pre);
   uint32_t* hist = reinterpret_cast<uint32_t*>(qsm + lay.off_hist);
   uint32_t* ctrl = reinterpret_cast<uint32_t*>(qsm + lay.off_ctrl);
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, T = blockDim.x;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, T = blockDim.x, NW = T >> 5;
   const uint32_t wmask = g.w - 1u, cmwords = (g.d * g.w) >> 1, nbk = lay.nbk;
-  // -- clear the sketch; fetch every bucket's fill
+  // -- clear the sketch; every bucket's fill and 32-id chunk count
   uint4* cm4 = reinterpret_cast<uint4*>(cmw);
   for (uint32_t i = threadIdx.x; i < cmwords / 4; i += T) cm4[i] = make_uint4(0, 0, 0, 0);
   if (threadIdx.x < C_Q) ctrl[threadIdx.x] = 0u;
   for (uint32_t i = threadIdx.x; i < nbk; i += T) bfill[i] = fill[bkey[i]];
   __syncthreads();
-  block_scan_small(bfill, pre, nbk, hist);  // hist as scratch
+  uint32_t* cnts = reinterpret_cast<uint32_t*>(pool);  // scratch: 32-id chunks per bucket
+  for (uint32_t i = threadIdx.x; i < nbk; i += T) cnts[i] = (bfill[i] + 31u) >> 5;
+  __syncthreads();
+  block_scan_small(cnts, cpre, nbk, hist);  // chunk prefix
   for (uint32_t i = threadIdx.x; i < kHistBins; i += T) hist[i] = 0u;
-  const uint32_t M = pre[nbk];
-  // -- the candidate multiset into registers, then the sketch
+  const uint32_t nchunk = cpre[nbk];
+  uint32_t* cbk = reinterpret_cast<uint32_t*>(qsm + lay.off_cbk);  // chunk -> bucket
+  for (uint32_t b = threadIdx.x; b < nbk; b += T)
+    for (uint32_t c = cpre[b]; c < cpre[b + 1]; ++c) cbk[c] = b;
+  __syncthreads();
+  uint2* cells = reinterpret_cast<uint2*>(qsm + lay.off_cells);  // [kRegIds][T]
+  const bool cache_cells = g.d <= 4u && g.w <= 65536u;          // cells fit 4 x 16 bits
+  // -- candidate occurrences: chunk c -> warp c % NW, register slot c / NW
   uint32_t idv[kRegIds];
 #pragma unroll
   for (int u = 0; u < kRegIds; ++u) {
-    const uint32_t i = threadIdx.x + u * T;
-    idv[u] = i < M ? occurrence(g, slots, bkey, pre, nbk, i) : kEmpty;
+    idv[u] = kEmpty;
+    const uint32_t c = warp + (uint32_t)u * NW;
+    if (c < nchunk) {
+      const uint32_t b = cbk[c];
+      const uint32_t j = (c - cpre[b]) * 32u + lane;
+      if (j < bfill[b]) idv[u] = __ldg(slots + (uint64_t)bkey[b] * g.R + j);
+    }
   }
+  auto chunk_id = [&](uint32_t c) -> uint32_t {  // beyond the register budget: reload
+    const uint32_t b = cbk[c];
+    const uint32_t j = (c - cpre[b]) * 32u + lane;
+    return j < bfill[b] ? __ldg(slots + (uint64_t)bkey[b] * g.R + j) : kEmpty;
+  };
+  // count; keep each occurrence's cells (16 bits per row) for its estimate
 #pragma unroll
-  for (int u = 0; u < kRegIds; ++u)
-    if (idv[u] != kEmpty)
+  for (int u = 0; u < kRegIds; ++u) {
+    if (idv[u] == kEmpty) continue;
+    if (cache_cells) {
+      uint32_t packed[2] = {0u, 0u};
+#pragma unroll
+      for (uint32_t r = 0; r < 4; ++r) {
+        if (r < g.d) {
+          const uint32_t cell = cm_cell(idv[u], g.sc[r], wmask);
+          cm_add(cmw, r * g.w + cell);
+          packed[r >> 1] |= cell << ((r & 1u) << 4);
+        }
+      }
+      cells[u * T + threadIdx.x] = make_uint2(packed[0], packed[1]);
+    } else {
       for (uint32_t r = 0; r < g.d; ++r) cm_add(cmw, r * g.w + cm_cell(idv[u], g.sc[r], wmask));
-  for (uint32_t i = threadIdx.x + kRegIds * T; i < M; i += T) {  // beyond the register budget
-    const uint32_t id = occurrence(g, slots, bkey, pre, nbk, i);
-    for (uint32_t r = 0; r < g.d; ++r) cm_add(cmw, r * g.w + cm_cell(id, g.sc[r], wmask));
+    }
+  }
+  for (uint32_t c = warp + kRegIds * NW; c < nchunk; c += NW) {
+    const uint32_t id = chunk_id(c);
+    if (id != kEmpty)
+      for (uint32_t r = 0; r < g.d; ++r) cm_add(cmw, r * g.w + cm_cell(id, g.sc[r], wmask));
   }
   __syncthreads();
   // -- estimates and their histogram
@@ -775,12 +923,23 @@ __device__ void query_core(const Geo& g, const QueryLayout& lay, unsigned char* 
   for (int u = 0; u < kRegIds; ++u) {
     ev[u] = 0u;
     if (idv[u] != kEmpty) {
-      ev[u] = estimate(g, cmw, idv[u]);
+      if (cache_cells) {
+        const uint2 cc = cells[u * T + threadIdx.x];
+        uint32_t e = cm_get(cmw, cc.x & 0xFFFFu);
+        if (g.d > 1u) e = min(e, cm_get(cmw, g.w + (cc.x >> 16)));
+        if (g.d > 2u) e = min(e, cm_get(cmw, 2u * g.w + (cc.y & 0xFFFFu)));
+        if (g.d > 3u) e = min(e, cm_get(cmw, 3u * g.w + (cc.y >> 16)));
+        ev[u] = e;
+      } else {
+        ev[u] = estimate(g, cmw, idv[u]);
+      }
       atomicAdd(&hist[min(ev[u], kHistBins - 1u)], 1u);
     }
   }
-  for (uint32_t i = threadIdx.x + kRegIds * T; i < M; i += T)
-    atomicAdd(&hist[min(estimate(g, cmw, occurrence(g, slots, bkey, pre, nbk, i)), kHistBins - 1u)], 1u);
+  for (uint32_t c = warp + kRegIds * NW; c < nchunk; c += NW) {
+    const uint32_t id = chunk_id(c);
+    if (id != kEmpty) atomicAdd(&hist[min(estimate(g, cmw, id), kHistBins - 1u)], 1u);
+  }
   __syncthreads();
   // -- cut-off: the largest bin e_lo whose bins at or above it surely hold >= k distinct ids
   if (warp == 0) {
@@ -807,22 +966,118 @@ __device__ void query_core(const Geo& g, const QueryLayout& lay, unsigned char* 
         if (cum >= k) { ctrl[C_ELO] = kHistBins - 1u - (lane * 8u + i); break; }
       }
     }
-    // (no lane crosses k: fewer than k ids are certain -> e_lo stays 0, pool everything)
+    // no lane crosses k: fewer than k ids are certain -> e_lo stays 0 (everything is pooled)
   }
   __syncthreads();
   const uint32_t elo = ctrl[C_ELO];
-  // -- pool the occurrences at or above the cut-off
+  // -- ties in bin e_lo (not the capped bin): the (k*mu)-th smallest occurrence id bounds them
+  uint32_t idmax = 0xFFFFFFFFu;
+  const bool tie_bin = elo > 0u && elo < kHistBins - 1u;
+  const uint32_t mu = tie_bin ? min(elo, lay.maxmult) : 0u;
+  const uint32_t need0 = k * mu;
+  if (tie_bin && hist[elo] > need0) {
+    uint32_t prefix = 0, need = need0;
+    for (int sh = 24; sh >= 0; sh -= 8) {
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < 256; i += T) pool[i] = 0ull;  // 256 counters in the pool area
+      __syncthreads();
+      uint32_t* h2 = reinterpret_cast<uint32_t*>(pool);
 #pragma unroll
-  for (int u = 0; u < kRegIds; ++u)
-    if (idv[u] != kEmpty && min(ev[u], kHistBins - 1u) >= elo)
-      pool[atomicAdd(&ctrl[C_NPOOL], 1u)] = rank_key(ev[u], idv[u]);
-  for (uint32_t i = threadIdx.x + kRegIds * T; i < M; i += T) {
-    const uint32_t id = occurrence(g, slots, bkey, pre, nbk, i);
+      for (int u = 0; u < kRegIds; ++u) {
+        const uint32_t id = idv[u];
+        if (id != kEmpty && ev[u] == elo && (sh == 24 || (id >> (sh + 8)) == (prefix >> (sh + 8))))
+          atomicAdd(&h2[(id >> sh) & 255u], 1u);
+      }
+      for (uint32_t c = warp + kRegIds * NW; c < nchunk; c += NW) {
+        const uint32_t id = chunk_id(c);
+        if (id != kEmpty && estimate(g, cmw, id) == elo &&
+            (sh == 24 || (id >> (sh + 8)) == (prefix >> (sh + 8))))
+          atomicAdd(&h2[(id >> sh) & 255u], 1u);
+      }
+      __syncthreads();
+      if (warp == 0) {
+        uint32_t v[8], sum = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { v[i] = h2[lane * 8 + i]; sum += v[i]; }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+          if (lane >= (uint32_t)o) inc += u;
+        }
+        const uint32_t ex = inc - sum;
+        if (ex < need && need <= inc) {
+          uint32_t cum = ex;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            if (cum + v[i] >= need) {
+              ctrl[C_PFX] = prefix | ((lane * 8u + i) << sh);
+              ctrl[C_NEED] = need - cum;
+              break;
+            }
+            cum += v[i];
+          }
+        }
+      }
+      __syncthreads();
+      prefix = ctrl[C_PFX];
+      need = ctrl[C_NEED];
+    }
+    idmax = prefix;  // >= k*mu occurrences (so >= k distinct ids) of the bin are <= idmax
+    __syncthreads();
+  }
+  // -- pool: every occurrence above the bin, and the bin's occurrences up to idmax
+  if (threadIdx.x == 0) ctrl[C_NPOOL] = 0u;
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < kRegIds; ++u) {
+    const uint32_t id = idv[u];
+    if (id == kEmpty) continue;
+    const uint32_t b = min(ev[u], kHistBins - 1u);
+    if (b > elo || (b == elo && id <= idmax)) pool[atomicAdd(&ctrl[C_NPOOL], 1u)] = rank_key(ev[u], id);
+  }
+  for (uint32_t c = warp + kRegIds * NW; c < nchunk; c += NW) {
+    const uint32_t id = chunk_id(c);
+    if (id == kEmpty) continue;
     const uint32_t e = estimate(g, cmw, id);
-    if (min(e, kHistBins - 1u) >= elo) pool[atomicAdd(&ctrl[C_NPOOL], 1u)] = rank_key(e, id);
+    const uint32_t b = min(e, kHistBins - 1u);
+    if (b > elo || (b == elo && id <= idmax)) pool[atomicAdd(&ctrl[C_NPOOL], 1u)] = rank_key(e, id);
   }
   __syncthreads();
-  const uint32_t P = ctrl[C_NPOOL];  // <= M <= maxm <= npool
+  const uint32_t P = ctrl[C_NPOOL];  // <= occurrences <= maxm <= npool
+  if ((uint64_t)k * ((P + 31u) / 32u) <= 512u) {
+    // small pool: warp 0 picks the k smallest distinct keys by repeated minimum
+    // (a key equal to the last one picked is a duplicate of the same id: skipped)
+    if (warp == 0) {
+      uint64_t last = 0ull;
+      bool have = false;
+      for (uint32_t j = 0; j < k; ++j) {
+        uint64_t best = ~0ull;
+        for (uint32_t i = lane; i < P; i += 32) {
+          const uint64_t key = pool[i];
+          if ((!have || key > last) && key < best) best = key;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const uint64_t other = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+          best = other < best ? other : best;
+        }
+        if (lane == 0) {
+          if (best != ~0ull) {
+            ids_out[j] = (int32_t)(uint32_t)best;
+            scores_out[j] = 0xFFFFu - (uint32_t)(best >> 32);
+          } else {
+            ids_out[j] = -1;
+            scores_out[j] = 0u;
+          }
+        }
+        last = best;
+        have = true;
+      }
+    }
+    __syncthreads();
+    return;
+  }
   const uint32_t n2 = max(2u, next_pow2(P));
   for (uint32_t i = P + threadIdx.x; i < n2; i += T) pool[i] = ~0ull;
   __syncthreads();
@@ -856,7 +1111,7 @@ __device__ void query_core(const Geo& g, const QueryLayout& lay, unsigned char* 
 
 // Plain path: one CTA per query (grid-stride); addresses from k_hash, qbkt[t*ldq + q].
 template <int kThreads>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 1)
 k_query(const __grid_constant__ Geo g, const QueryLayout lay, const uint32_t* __restrict__ qbkt, uint64_t ldq,
         uint32_t nq, uint32_t k, const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill,
         int32_t* __restrict__ ids_out, uint32_t* __restrict__ scores_out) {
@@ -876,7 +1131,7 @@ k_query(const __grid_constant__ Geo g, const QueryLayout lay, const uint32_t* __
 // hashed (DOPH, densification, L addresses) by the whole CTA in smem and then
 // answered by query_core -- no intermediate HBM traffic, one launch per batch.
 template <int kThreads>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 1)
 k_query_fused(const __grid_constant__ Geo g, const QueryLayout lay, const uint64_t* __restrict__ offs,
               const uint32_t* __restrict__ cols, uint32_t nq, uint32_t k, const uint32_t* __restrict__ slots,
               const uint32_t* __restrict__ fill, int32_t* __restrict__ ids_out,
@@ -1107,6 +1362,9 @@ QueryLayout make_query_layout(const slash_params& p) {
   l.off_mask = o;  o = al(o + nw * 4u);
   l.off_hist = o;  o = al(o + kHistBins * 4u);
   l.off_ctrl = o;  o = al(o + 16u * 4u);
+  l.nchunkmax = l.nbk * ((p.reservoir + 31u) / 32u);
+  l.off_cbk = o;   o = al(o + l.nchunkmax * 4u);
+  l.off_cells = o; o = al(o + kRegIds * 1024u * 8u);  // 4 x 16-bit cells per register occurrence
   l.bytes = o;
   return l;
 }
@@ -1122,10 +1380,32 @@ uint32_t default_query_threads(const slash_params& p) {
 int run_hash(slash_index* ix, const uint64_t* offs, const uint32_t* cols, uint32_t n, uint64_t id0,
              uint32_t* bkt, uint64_t ldb, uint32_t* codes, bool count, cudaStream_t st) {
   if (n == 0) return SLASH_OK;
-  const size_t smem = hash_smem(ix);
   const ShardMap sm = shard_map(ix);
   const dim3 grid((n + kHashRows - 1) / kHashRows);
   Launch lg(ix, count ? "k_hash_insert" : "k_hash", st);
+  const uint32_t nb = ix->geo.nb, K = ix->p.K;
+  const uint32_t C = nb % 32u == 0u ? nb / 32u : 0u;
+  const size_t rsmem = sizeof(uint32_t) * ((size_t)kHashWarps * (((nb + 33u) + 3u) & ~3u) +
+                                           (size_t)ix->p.L * kHashRows);
+#define SLASH_HREG(CC, KK)                                                                              \
+  if (C == CC && K == KK) {                                                                          \
+    if (count)                                                                                       \
+      k_hash_reg<CC, KK, true><<<grid, kHashWarps * 32, rsmem, st>>>(ix->geo, sm, offs, cols, n, id0, \
+                                                                   bkt, ldb, codes, ix->cnt, ix->err); \
+    else                                                                                             \
+      k_hash_reg<CC, KK, false><<<grid, kHashWarps * 32, rsmem, st>>>(ix->geo, sm, offs, cols, n, id0, \
+                                                                    bkt, ldb, codes, nullptr, ix->err); \
+    SLASH_CK(cudaGetLastError());                                                                    \
+    return SLASH_OK;                                                                                 \
+  }
+  SLASH_HREG(12, 6)
+  SLASH_HREG(12, 4)
+  SLASH_HREG(8, 8)
+  SLASH_HREG(8, 4)
+  SLASH_HREG(4, 4)
+  SLASH_HREG(16, 8)
+#undef SLASH_HREG
+  const size_t smem = hash_smem(ix);
   if (count)
     k_hash<true><<<grid, kHashWarps * 32, smem, st>>>(ix->geo, sm, offs, cols, n, id0, bkt, ldb, codes,
                                                       ix->cnt, ix->err);
@@ -1314,6 +1594,11 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
   cudaFuncSetAttribute(k_query_fused<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_merge_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ix->smem_optin);
   cudaFuncSetAttribute(k_hash<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ix->smem_optin);
+#define SLASH_HATTR(CC, KK)                                                                              \
+  cudaFuncSetAttribute(k_hash_reg<CC, KK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);    \
+  cudaFuncSetAttribute(k_hash_reg<CC, KK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  SLASH_HATTR(12, 6) SLASH_HATTR(12, 4) SLASH_HATTR(8, 8) SLASH_HATTR(8, 4) SLASH_HATTR(4, 4) SLASH_HATTR(16, 8)
+#undef SLASH_HATTR
   cudaFuncSetAttribute(k_hash<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ix->smem_optin);
   *out = ix;
   return SLASH_OK;

@@ -1,0 +1,48 @@
+"""Full-size parity: the `criteo` workload (50M rows, K=6, L=64, 2^18 buckets,
+R=128) inserted in one call and queried with the index's default schedule, as
+the benchmark runs it.  The oracle cannot build the whole index quickly, so it
+builds only the sampled buckets -- every bucket of 200 sampled queries (chosen
+by the oracle's own hashes) plus 2000 random buckets -- from all 50M rows, and
+the GPU's copies of those buckets and its answers to those queries must match
+bit for bit."""
+import numpy as np
+import pytest
+import torch
+
+import datagen
+import oracle
+from datagen.workloads import CRITEO as w
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def _dev(a):
+    return torch.from_numpy(a.view(np.int64 if a.dtype == np.uint64 else np.int32)).cuda()
+
+
+def test_criteo_full_size_sampled_parity():
+    import paper_2008_03260_b300 as s
+    g = datagen.Generator()
+    offs, cols = g.rows(w.seed, 0, w.n_rows)
+    qo, qc, _ = g.queries(w.seed, w.qseed, 200, w.n_rows, **w.query_kwargs())
+    p = s.Params(**w.params())
+    with s.Index(p) as ix:
+        ix.insert(_dev(offs), _dev(cols))
+        ids, sc = ix.query(_dev(qo), _dev(qc), w.topk)
+        ix.sync()
+        _, qbk = oracle.hash_rows(w.K, w.L, w.log2_buckets, w.seed, w.cm_rows, qo, qc, want_codes=False)
+        rng = np.random.default_rng(5)
+        rt = np.concatenate([np.tile(np.arange(w.L), len(qo) - 1), rng.integers(0, w.L, 2000)]).astype(np.uint32)
+        rb = np.concatenate([qbk.ravel(), rng.integers(0, 1 << w.log2_buckets, 2000)]).astype(np.uint32)
+        gslots, gfill = ix.buckets(np.zeros_like(rt), rt, rb)
+        gids, gsc = ids.cpu().numpy(), sc.cpu().numpy().view(np.uint32)
+    oix = oracle.Index(K=w.K, L=w.L, log2_buckets=w.log2_buckets, reservoir=w.reservoir, cm_rows=w.cm_rows,
+                       cm_width=w.cm_width, seed=w.seed, capacity=w.n_rows, partial=(rt, rb))
+    oix.insert(offs, cols, threads=datagen.default_threads())
+    for i in range(len(rt)):
+        want, wf = oix.bucket(int(rt[i]), int(rb[i]))
+        assert gfill[i] == wf and np.array_equal(gslots[i], want), (int(rt[i]), int(rb[i]))
+    assert gfill.max() == w.reservoir  # the sample includes full (sub-sampled) buckets
+    want_ids, want_sc = oix.query(qo, qc, w.topk)
+    assert np.array_equal(gids, want_ids)
+    assert np.array_equal(gsc, want_sc)
