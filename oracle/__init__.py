@@ -84,6 +84,16 @@ def _load():
             lib.or_query.argtypes = [vp, vp, vp, u64, u32, vp, vp]
             lib.or_next_id.restype = u64
             lib.or_next_id.argtypes = [vp]
+            lib.or_tk_update.argtypes = [ctypes.POINTER(u32), ctypes.POINTER(u32), u32]
+            lib.or_tk_merge_cell.argtypes = [ctypes.POINTER(u32), ctypes.POINTER(u32), u32, u32]
+            lib.or_tk_new.restype = vp
+            lib.or_tk_new.argtypes = [u32, u32, u32, u32, u32, u32, u64, u64]
+            lib.or_tk_free.argtypes = [vp]
+            lib.or_tk_insert.restype = i32
+            lib.or_tk_insert.argtypes = [vp, vp, vp, u64, ctypes.POINTER(u64)]
+            lib.or_tk_export.argtypes = [vp, vp]
+            lib.or_tk_query.restype = i32
+            lib.or_tk_query.argtypes = [vp, vp, vp, u64, u32, vp, vp]
             _lib = lib
     return _lib
 
@@ -248,3 +258,56 @@ class Index:
         m, u = int(ml.value), int(ul.value)
         return {"ids": ids, "scores": scores, "M": M[:m].copy(), "U": U[:u].copy(),
                 "est": est[:u].copy(), "cnt": cnt[:u].copy(), "cm": cm.reshape(self.d, self.w)}
+
+
+# ---------------------------------------------------------------- TopKAPI buckets
+def tk_update(cell: tuple[int, int], x: int) -> tuple[int, int]:
+    """One Appendix 2 insertion into a (heavy hitter, count) cell."""
+    h, c = ctypes.c_uint32(cell[0]), ctypes.c_uint32(cell[1])
+    _load().or_tk_update(ctypes.byref(h), ctypes.byref(c), x)
+    return int(h.value), int(c.value)
+
+
+def tk_merge(a: tuple[int, int], b: tuple[int, int]) -> tuple[int, int]:
+    """Appendix 2 merge of two cells (count 0 = empty)."""
+    h, c = ctypes.c_uint32(a[0]), ctypes.c_uint32(a[1])
+    _load().or_tk_merge_cell(ctypes.byref(h), ctypes.byref(c), b[0], b[1])
+    return int(h.value), int(c.value)
+
+
+class TkIndex:
+    """Oracle index whose buckets are TopKAPI sketches of W rows x C cells."""
+
+    def __init__(self, *, K: int, L: int, log2_buckets: int, rows: int, cells: int, shards: int = 1,
+                 seed: int = 0, capacity: int):
+        self._lib = _load()
+        self.K, self.L, self.B, self.W, self.C, self.S = K, L, log2_buckets, rows, cells, shards
+        self._h = self._lib.or_tk_new(K, L, log2_buckets, rows, cells, shards, seed, capacity)
+        if not self._h:
+            raise MemoryError("oracle sketch allocation failed")
+
+    def __del__(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h:
+            self._lib.or_tk_free(h)
+
+    def insert(self, offs, cols) -> int:
+        offs, cols = _u64(offs), _u32(cols)
+        first = ctypes.c_uint64()
+        if self._lib.or_tk_insert(self._h, _p(offs), _p(cols), offs.size - 1, ctypes.byref(first)):
+            raise ValueError("oracle insert failed: capacity exceeded")
+        return int(first.value)
+
+    def export(self) -> np.ndarray:
+        """cells [S][L][2^B][W][C][2] = (heavy hitter or EMPTY, count)."""
+        out = np.empty((self.S, self.L, 1 << self.B, self.W, self.C, 2), dtype=np.uint32)
+        self._lib.or_tk_export(self._h, _p(out))
+        return out
+
+    def query(self, offs, cols, k: int):
+        offs, cols = _u64(offs), _u32(cols)
+        nq = offs.size - 1
+        ids = np.empty((nq, k), dtype=np.int32)
+        scores = np.empty((nq, k), dtype=np.uint32)
+        self._lib.or_tk_query(self._h, _p(offs), _p(cols), nq, k, _p(ids), _p(scores))
+        return ids, scores

@@ -466,3 +466,132 @@ int or_query(const void *p, const uint64_t *offs, const uint32_t *cols, uint64_t
 }
 
 uint64_t or_next_id(const void *p) { return ((const or_index *)p)->next_id; }
+
+/* ------------------------------------------------------------------ TopKAPI buckets
+ * SLASH's own bucket (Sec. 3.1 and Appendix 2): every bucket address holds a
+ * TopKAPI sketch of W rows x Bc cells, each cell a (heavy hitter, count) pair,
+ * instead of an id list.  Fixed readings:
+ *   cell_i(id)   mix32(id ^ tk[i]) & (Bc - 1); tk = the d = W row seeds drawn
+ *                after st and sp (same order as the count-min seeds)
+ *   insert x     Appendix 2, read in the order written: if the cell holds x,
+ *                count + 1; otherwise count - 1, and when the count is then 0
+ *                (or the cell was empty) the cell becomes (x, 1).  A cell is
+ *                empty exactly when its count is 0.
+ *   order        a bucket takes its ids in ascending id (= data) order
+ *   merge        same heavy hitter: counts add; different: the larger count
+ *                wins with the difference; equal counts cancel to an empty cell
+ *   query        fold the query's buckets, shard-major then table order, into
+ *                an empty sketch; each heavy hitter's score is its largest
+ *                count over the cells; rank by (score desc, id asc), pad (-1,0)
+ */
+typedef struct {
+  uint32_t K, L, B, W, C, S;
+  uint64_t capacity, next_id;
+  uint32_t *seeds;       /* 2 + 2L + W */
+  uint32_t *hh, *cnt;    /* [S][L][2^B][W][C] */
+} or_tk;
+
+void or_tk_update(uint32_t *hh, uint32_t *cnt, uint32_t x) {
+  if (*cnt > 0 && *hh == x) { *cnt += 1; return; }
+  if (*cnt > 0) *cnt -= 1;
+  if (*cnt == 0) { *hh = x; *cnt = 1; }
+}
+
+void or_tk_merge_cell(uint32_t *hh, uint32_t *cnt, uint32_t bh, uint32_t bc) {
+  if (bc == 0) return;
+  if (*cnt == 0) { *hh = bh; *cnt = bc; return; }
+  if (*hh == bh) { *cnt += bc; return; }
+  if (bc > *cnt) { *hh = bh; *cnt = bc - *cnt; return; }
+  *cnt -= bc;   /* equal counts leave an empty cell */
+}
+
+void *or_tk_new(uint32_t K, uint32_t L, uint32_t B, uint32_t W, uint32_t C, uint32_t S, uint64_t seed,
+                uint64_t capacity) {
+  or_tk *ix = (or_tk *)calloc(1, sizeof(or_tk));
+  ix->K = K; ix->L = L; ix->B = B; ix->W = W; ix->C = C; ix->S = S; ix->capacity = capacity;
+  ix->seeds = (uint32_t *)malloc(sizeof(uint32_t) * (2 + 2 * L + W));
+  or_derive_seeds(seed, L, W, ix->seeds);
+  uint64_t n = ((uint64_t)S * L << B) * W * C;
+  ix->hh = (uint32_t *)calloc(n, sizeof(uint32_t));
+  ix->cnt = (uint32_t *)calloc(n, sizeof(uint32_t));
+  if (!ix->hh || !ix->cnt) { free(ix->hh); free(ix->cnt); free(ix->seeds); free(ix); return NULL; }
+  return ix;
+}
+
+void or_tk_free(void *p) {
+  or_tk *ix = (or_tk *)p;
+  if (!ix) return;
+  free(ix->seeds); free(ix->hh); free(ix->cnt); free(ix);
+}
+
+/* Algorithm 1 with sketches: each row's id goes into one sketch per table. */
+int or_tk_insert(void *p, const uint64_t *offs, const uint32_t *cols, uint64_t n, uint64_t *first_id) {
+  or_tk *ix = (or_tk *)p;
+  if (ix->next_id + n > ix->capacity) return -1;
+  uint32_t nb = ix->K * ix->L;
+  uint32_t *codes = (uint32_t *)malloc(sizeof(uint32_t) * nb);
+  const uint32_t *st = ix->seeds + 2, *tk = ix->seeds + 2 + 2 * ix->L;
+  *first_id = ix->next_id;
+  for (uint64_t i = 0; i < n; ++i) {
+    uint64_t id = ix->next_id++;
+    uint32_t s = (uint32_t)(((unsigned __int128)id * ix->S) / ix->capacity);
+    or_doph(cols + (offs[i] - offs[0]), offs[i + 1] - offs[i], nb, ix->seeds[0], ix->seeds[1], codes, NULL);
+    for (uint32_t t = 0; t < ix->L; ++t) {
+      uint32_t b = or_table_address(codes, t, ix->K, ix->B, st[t]);
+      uint64_t base = ((((uint64_t)s * ix->L + t) << ix->B) + b) * ix->W * ix->C;
+      for (uint32_t r = 0; r < ix->W; ++r) {
+        uint64_t c = base + (uint64_t)r * ix->C + (or_mix32((uint32_t)id ^ tk[r]) & (ix->C - 1));
+        or_tk_update(ix->hh + c, ix->cnt + c, (uint32_t)id);
+      }
+    }
+  }
+  free(codes);
+  return 0;
+}
+
+/* cells [S][L][2^B][W][C][2] = (heavy hitter or 0xFFFFFFFF when empty, count) */
+void or_tk_export(const void *p, uint32_t *out) {
+  const or_tk *ix = (const or_tk *)p;
+  uint64_t n = ((uint64_t)ix->S * ix->L << ix->B) * ix->W * ix->C;
+  for (uint64_t c = 0; c < n; ++c) {
+    out[2 * c] = ix->cnt[c] ? ix->hh[c] : OR_EMPTY;
+    out[2 * c + 1] = ix->cnt[c];
+  }
+}
+
+/* Algorithm 2 with sketches: merge the query's buckets, report the top-k heavy hitters. */
+int or_tk_query(const void *p, const uint64_t *offs, const uint32_t *cols, uint64_t nq, uint32_t k,
+                int32_t *ids, uint32_t *scores) {
+  const or_tk *ix = (const or_tk *)p;
+  uint32_t nb = ix->K * ix->L, WC = ix->W * ix->C;
+  const uint32_t *st = ix->seeds + 2;
+  uint32_t *codes = (uint32_t *)malloc(sizeof(uint32_t) * nb);
+  uint32_t *mh = (uint32_t *)malloc(sizeof(uint32_t) * WC), *mc = (uint32_t *)malloc(sizeof(uint32_t) * WC);
+  or_cand *cand = (or_cand *)malloc(sizeof(or_cand) * (WC + 1));
+  for (uint64_t q = 0; q < nq; ++q) {
+    or_doph(cols + (offs[q] - offs[0]), offs[q + 1] - offs[q], nb, ix->seeds[0], ix->seeds[1], codes, NULL);
+    for (uint32_t c = 0; c < WC; ++c) { mh[c] = OR_EMPTY; mc[c] = 0; }
+    for (uint32_t s = 0; s < ix->S; ++s)
+      for (uint32_t t = 0; t < ix->L; ++t) {
+        uint32_t b = or_table_address(codes, t, ix->K, ix->B, st[t]);
+        uint64_t base = ((((uint64_t)s * ix->L + t) << ix->B) + b) * WC;
+        for (uint32_t c = 0; c < WC; ++c) or_tk_merge_cell(mh + c, mc + c, ix->hh[base + c], ix->cnt[base + c]);
+      }
+    /* distinct heavy hitters, each with its largest count */
+    uint32_t nc = 0;
+    for (uint32_t c = 0; c < WC; ++c) {
+      if (mc[c] == 0) continue;
+      uint32_t j = 0;
+      while (j < nc && cand[j].id != mh[c]) ++j;
+      if (j == nc) { cand[nc].id = mh[c]; cand[nc].est = mc[c]; ++nc; }
+      else if (mc[c] > cand[j].est) cand[j].est = mc[c];
+    }
+    qsort(cand, nc, sizeof(or_cand), cmp_cand);
+    for (uint32_t i = 0; i < k; ++i) {
+      ids[q * k + i] = i < nc ? (int32_t)cand[i].id : -1;
+      scores[q * k + i] = i < nc ? cand[i].est : 0;
+    }
+  }
+  free(codes); free(mh); free(mc); free(cand);
+  return 0;
+}

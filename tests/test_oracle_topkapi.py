@@ -1,0 +1,92 @@
+"""Pins of the oracle's TopKAPI buckets (Sec. 3.1 / Appendix 2) to properties
+that do not depend on the oracle's own code."""
+import numpy as np
+
+import datagen
+import oracle
+
+EMPTY = 0xFFFFFFFF
+
+
+def _run(stream):
+    cell = (EMPTY, 0)
+    for x in stream:
+        cell = oracle.tk_update(cell, x)
+    return cell
+
+
+def test_cell_keeps_a_strict_majority():
+    """A frequent-items cell: an element with a strict majority of a stream ends
+    as the cell's heavy hitter, whatever the order (the Boyer-Moore guarantee)."""
+    rng = np.random.default_rng(0)
+    for _ in range(300):
+        n = int(rng.integers(1, 40))
+        maj = int(rng.integers(0, 1000))
+        k = n // 2 + 1
+        others = [int(v) for v in rng.integers(1000, 1100, n - k)]
+        stream = [maj] * k + others
+        rng.shuffle(stream)
+        h, c = _run(stream)
+        assert h == maj and 1 <= c <= k
+
+
+def test_cell_single_element_and_distinct_streams():
+    assert _run([7] * 13) == (7, 13)
+    # distinct ids (every bucket stream, since ids are unique): each arrival meets
+    # an empty cell or a different id with count 1, so the cell ends (last id, 1)
+    rng = np.random.default_rng(1)
+    for _ in range(100):
+        stream = [int(v) for v in rng.choice(10**6, size=int(rng.integers(1, 60)), replace=False)]
+        assert _run(stream) == (stream[-1], 1)
+
+
+def test_merge_rules():
+    assert oracle.tk_merge((EMPTY, 0), (5, 3)) == (5, 3)
+    assert oracle.tk_merge((5, 3), (EMPTY, 0)) == (5, 3)
+    assert oracle.tk_merge((5, 3), (5, 4)) == (5, 7)
+    assert oracle.tk_merge((5, 3), (6, 1)) == (5, 2)
+    assert oracle.tk_merge((5, 1), (6, 3)) == (6, 2)
+    assert oracle.tk_merge((5, 2), (6, 2))[1] == 0          # equal counts cancel
+    rng = np.random.default_rng(2)
+    for _ in range(500):  # commutative up to the identity of an empty cell
+        a = (int(rng.integers(0, 4)), int(rng.integers(0, 5)))
+        b = (int(rng.integers(0, 4)), int(rng.integers(0, 5)))
+        x, y = oracle.tk_merge(a, b), oracle.tk_merge(b, a)
+        assert x[1] == y[1] and (x[1] == 0 or x[0] == y[0])
+
+
+def test_merged_cells_keep_a_majority_holder():
+    """Folding cells that each hold one id with count 1: an id holding the cell
+    in more than half of the sketches is the merged heavy hitter."""
+    rng = np.random.default_rng(3)
+    for _ in range(300):
+        n = int(rng.integers(1, 64))
+        k = n // 2 + 1
+        seq = [(9, 1)] * k + [(int(v), 1) for v in rng.integers(10, 20, n - k)]
+        rng.shuffle(seq)
+        acc = (EMPTY, 0)
+        for cell in seq:
+            acc = oracle.tk_merge(acc, cell)
+        assert acc[0] == 9 and acc[1] >= 1
+
+
+def test_sketch_index_shape_and_recall():
+    """Buckets hold only ids hashed to them; planted neighbours are reported."""
+    g = datagen.Generator()
+    n = 4000
+    offs, cols = g.rows(0, 0, n)
+    ix = oracle.TkIndex(K=4, L=16, log2_buckets=12, rows=4, cells=32, capacity=n)
+    ix.insert(offs, cols)
+    cells = ix.export()
+    _, bk = oracle.hash_rows(4, 16, 12, 0, 4, offs, cols, want_codes=False)
+    occupied = cells[..., 1] > 0
+    assert np.all(cells[..., 1][occupied] == 1)             # unique ids: counts stay 1
+    hh = cells[..., 0][occupied]
+    assert hh.max() < n
+    # every kept id was hashed to that bucket
+    s, t, b, r, c = np.nonzero(occupied)
+    assert np.all(bk[cells[s, t, b, r, c, 0], t] == b)
+    qo, qc, src = g.queries(0, 1, 300, n, p_perturb=0.2)
+    ids, sc = ix.query(qo, qc, 10)
+    assert np.mean([src[i] in ids[i] for i in range(300)]) > 0.85
+    assert np.all(sc[:, 0] >= 1)
