@@ -4,8 +4,9 @@
 One step = reset the index, insert the workload's rows (Algorithm 1), run its
 query batch (Algorithm 2), all through the C ABI with inputs resident in HBM.
 `value` is inserts/s over all ranks; queries/s is reported beside it.  `e2e`
-repeats the step through the same public calls from pinned HOST buffers, with
-the host->device copies of the inputs and the device->host read of the
+repeats the step from pinned HOST buffers through the public calls
+(slash_insert_host for the rows, host->device copy + slash_query for the
+queries), with every host->device copy and the device->host read of the
 results inside the timed region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload criteo|tiny|uneven]
@@ -342,9 +343,7 @@ def main():
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
             ix.reset(st)
             ev[0].record(st)
-            d_offs.copy_(h_offs, non_blocking=True)
-            d_cols.copy_(h_cols, non_blocking=True)
-            ix.insert(d_offs, d_cols, st)
+            ix.insert_host(h_offs, h_cols, st)   # host CSR: copies overlap the hashing
             ev[1].record(st)
             d_qo.copy_(h_qo, non_blocking=True)
             d_qc.copy_(h_qc, non_blocking=True)

@@ -98,6 +98,17 @@ int slash_build_index(const slash_params *p, void *cuda_stream, slash_index **ou
 int slash_insert(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n_rows,
                  uint64_t *first_id_out, void *cuda_stream);
 
+/* slash_insert from HOST memory: h_offs (n_rows+1 offsets into h_cols, checked on
+ * the host: decreasing offsets give SLASH_EINVAL) and h_cols.  Pieces of up to 2M
+ * rows are copied to two library-owned device staging slots on an internal copy
+ * stream while the previous piece is hashed on `cuda_stream`; the per-bucket
+ * merge then runs once per chunk.  Page-locked host buffers give overlapped
+ * copies; pageable ones still work.  The caller keeps both buffers unchanged
+ * until `cuda_stream`'s work completes.  Same results and errors as slash_insert
+ * (plus SLASH_ENOMEM for the staging slots). */
+int slash_insert_host(slash_index *ix, const uint64_t *h_offs, const uint32_t *h_cols, uint32_t n_rows,
+                      uint64_t *first_id_out, void *cuda_stream);
+
 /* Querying (Algorithm 2): for each query, hash it into its L buckets, gather
  * the ids they hold in every shard, count them in a d x w count-min sketch
  * (shard sketches summed), estimate each distinct candidate's frequency as the

@@ -77,6 +77,7 @@ def _load() -> ctypes.CDLL:
         "slash_build_index": (i32, [P(slash_params), vp, P(vp)]),
         "slash_insert": (i32, [vp, vp, vp, u32, P(u64), vp]),
         "slash_query": (i32, [vp, vp, vp, u32, u32, vp, vp, vp]),
+        "slash_insert_host": (i32, [vp, vp, vp, u32, P(u64), vp]),
         "slash_free": (i32, [vp]),
         "slash_strerror": (ctypes.c_char_p, [i32]),
         "slash_sync": (i32, [vp, vp]),
@@ -169,6 +170,20 @@ def slash_insert(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, stream=Non
     first = ctypes.c_uint64()
     _check(_lib.slash_insert(ix, _dev_ptr(d_offs, 8, "d_offs"), _dev_ptr(d_cols, 4, "d_cols"), n,
                              ctypes.byref(first), _stream(stream)), "slash_insert")
+    return int(first.value)
+
+
+def slash_insert_host(ix: int, h_offs: torch.Tensor, h_cols: torch.Tensor, stream=None) -> int:
+    """Insert rows held in (preferably pinned) host memory; copies overlap the hashing."""
+    if h_offs.is_cuda or h_cols.is_cuda:
+        raise TypeError("slash_insert_host takes host tensors")
+    if h_offs.element_size() != 8 or h_cols.element_size() != 4 or not (h_offs.is_contiguous() and
+                                                                        h_cols.is_contiguous()):
+        raise TypeError("h_offs: contiguous 8-byte ints, h_cols: contiguous 4-byte ints")
+    n = h_offs.numel() - 1
+    first = ctypes.c_uint64()
+    _check(_lib.slash_insert_host(ix, h_offs.data_ptr(), h_cols.data_ptr(), n, ctypes.byref(first),
+                                  _stream(stream)), "slash_insert_host")
     return int(first.value)
 
 
@@ -302,6 +317,9 @@ class Index:
 
     def insert(self, d_offs, d_cols, stream=None) -> int:
         return slash_insert(self.h, d_offs, d_cols, stream)
+
+    def insert_host(self, h_offs, h_cols, stream=None) -> int:
+        return slash_insert_host(self.h, h_offs, h_cols, stream)
 
     def query(self, d_offs, d_cols, topk: int, stream=None, **kw):
         return slash_query(self.h, d_offs, d_cols, topk, stream=stream, **kw)

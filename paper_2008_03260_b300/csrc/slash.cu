@@ -66,24 +66,31 @@ constexpr int kHashWarps = 8;
 constexpr int kRowsPerWarp = 4;
 constexpr int kHashRows = kHashWarps * kRowsPerWarp;  // rows per CTA
 
-// nearest non-empty bin to j on one side, circularly (the row has >= 1 feature)
-__device__ __forceinline__ uint32_t nearest_bin(const uint32_t* mask, uint32_t nw, uint32_t j, bool right) {
-  uint32_t w = j >> 5, b = j & 31u;
-  uint32_t word = right ? (b == 31u ? 0u : (mask[w] & (0xFFFFFFFFu << (b + 1u))))
-                        : (mask[w] & ((1u << b) - 1u));
-  for (uint32_t it = 0; it <= nw; ++it) {
-    if (word) return (w << 5) + (right ? (uint32_t)(__ffs(word) - 1) : (31u - (uint32_t)__clz(word)));
-    w = right ? (w + 1u == nw ? 0u : w + 1u) : (w == 0u ? nw - 1u : w - 1u);
-    word = mask[w];
-  }
-  return j;
-}
-
 // DOPH of one CSR row by one warp into m[nb] (smem), using mask[nw] (smem).
 // Densification works on lane chunks: lane l owns bins [l*c, l*c + c),
 // c = ceil(nb/32); the nearest non-empty bin inside the chunk comes from bit
 // scans of the chunk's mask bits, and across chunks from a circular pointer-
 // jumping scan over the lanes' first / last non-empty bins.
+// Binning of Sec. 4.1 (Eq. 3) by threads [i0, i0+stride) of a cooperating
+// group: each feature's hash goes to its bin's minimum, its bit to the mask.
+// Returns whether this thread skipped a feature id >= dim.
+__device__ __forceinline__ bool doph_scatter(const Geo& g, const uint32_t* __restrict__ cols, uint64_t b0,
+                                             uint64_t b1, uint32_t* m, uint32_t* mask, uint32_t i0,
+                                             uint32_t stride) {
+  bool bad = false;
+  for (uint64_t i = b0 + i0; i < b1; i += stride) {
+    const uint32_t f = __ldg(cols + i);
+    if (f >= g.dim) { bad = true; continue; }
+    const uint32_t h = mix32(f ^ g.a);
+    const uint32_t bin = __umulhi(h, g.nb);
+    atomicMin(&m[bin], h);
+    atomicOr(&mask[bin >> 5], 1u << (bin & 31u));
+  }
+  return bad;
+}
+
+__device__ __forceinline__ void doph_densify(const Geo& g, uint32_t* m, const uint32_t* mask, uint32_t lane);
+
 __device__ __forceinline__ void doph_row(const Geo& g, const uint32_t* __restrict__ cols, uint64_t b0,
                                          uint64_t b1, uint32_t* m, uint32_t* mask, uint32_t* err,
                                          uint32_t lane) {
@@ -92,17 +99,14 @@ __device__ __forceinline__ void doph_row(const Geo& g, const uint32_t* __restric
   for (uint32_t j = (g.nb & ~3u) + lane; j < g.nb; j += 32) m[j] = kEmpty;
   if (lane < g.nw) mask[lane] = 0u;
   __syncwarp();
-  bool bad = false;
-  for (uint64_t i = b0 + lane; i < b1; i += 32) {
-    const uint32_t f = __ldg(cols + i);
-    if (f >= g.dim) { bad = true; continue; }
-    const uint32_t h = mix32(f ^ g.a);
-    const uint32_t bin = __umulhi(h, g.nb);
-    atomicMin(&m[bin], h);
-    atomicOr(&mask[bin >> 5], 1u << (bin & 31u));
-  }
+  const bool bad = doph_scatter(g, cols, b0, b1, m, mask, lane, 32u);
   if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(err, kErrCol);
   __syncwarp();
+  doph_densify(g, m, mask, lane);
+}
+
+// Densification of Sec. 4.1 by one warp, after the binning is complete.
+__device__ __forceinline__ void doph_densify(const Geo& g, uint32_t* m, const uint32_t* mask, uint32_t lane) {
   constexpr uint32_t kNone = 0xFFFFFFFFu;
   const uint32_t c = (g.nb + 31u) >> 5;          // bins per lane (1..32)
   const uint32_t lo = lane * c;
@@ -178,8 +182,13 @@ k_hash(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
     if (kCount) s = shard_of(sm, g.S, id0 + r);
     for (uint32_t t = lane; t < g.L; t += 32) {
       const uint32_t b = table_address(g, m, t);
-      tile[t * kHashRows + lr] = b;
-      if (kCount) atomicAdd(&cnt[(((uint64_t)s * g.L + t) << g.B) | b], 1u);
+      uint32_t out = b;
+      if (kCount) {
+        // the count's old value is this pair's rank in its bucket: kept in the low bits
+        const uint32_t rank = atomicAdd(&cnt[(((uint64_t)s * g.L + t) << g.B) | b], 1u);
+        if (g.rbits) out = (b << g.rbits) | min(rank, (1u << g.rbits) - 1u);
+      }
+      tile[t * kHashRows + lr] = out;
     }
     if (codes)
       for (uint32_t j = lane; j < g.nb; j += 32) codes[r * g.nb + j] = m[j];
@@ -294,8 +303,13 @@ k_hash_reg(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
 #pragma unroll
       for (int j = 0; j < K; ++j) acc = (acc ^ code[tt * K + j]) * kGold32;
       const uint32_t b = mix32(acc) >> (32u - g.B);
-      tile[t * kHashRows + lr] = b;
-      if (kCount) atomicAdd(&cnt[(((uint64_t)s * g.L + t) << g.B) | b], 1u);
+      uint32_t out = b;
+      if (kCount) {
+        // the count's old value is this pair's rank in its bucket: kept in the low bits
+        const uint32_t rank = atomicAdd(&cnt[(((uint64_t)s * g.L + t) << g.B) | b], 1u);
+        if (g.rbits) out = (b << g.rbits) | min(rank, (1u << g.rbits) - 1u);
+      }
+      tile[t * kHashRows + lr] = out;
     }
     if (codes) {
 #pragma unroll
@@ -458,11 +472,16 @@ k_scatter(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
   for (int k = 0; k < kScatterPerThread; ++k) {
     const uint64_t i = base + (uint64_t)k * kScatterThreads;
     if (i >= pend) break;
-    const uint32_t b = bkt[t * ldb + i];
+    const uint32_t v = bkt[t * ldb + i];
+    const uint32_t b = g.rbits ? v >> g.rbits : v;
     const uint64_t id = id0 + i;
     const uint32_t s = shard_of(sm, g.S, id);
     const uint64_t key = (((uint64_t)s * g.L + t) << g.B) | b;
     const uint4 m = meta[key];
+    if (g.rbits && m.x == kNoFilter) {  // unfiltered bucket: every pair staged at its rank
+      stage[(uint64_t)m.z + (v & ((1u << g.rbits) - 1u))] = (uint32_t)id;
+      continue;
+    }
     if (priority((uint32_t)id, sp) >= m.x) continue;
     const uint32_t r = atomicAdd(&meta[key].w, 1u);
     if (r < m.y) stage[(uint64_t)m.z + r] = (uint32_t)id;
@@ -570,7 +589,8 @@ k_merge_small(const __grid_constant__ Geo g, uint64_t nk, uint32_t cap_c, uint32
     const uint32_t n = cnt[key];
     if (n == 0) continue;
     const uint4 md = meta[key];
-    const uint32_t th = md.x, cp = md.y, lo = md.z, got = md.w;
+    const uint32_t th = md.x, cp = md.y, lo = md.z;
+    const uint32_t got = (g.rbits && th == kNoFilter) ? n : md.w;  // ranked buckets: all n staged
     const uint32_t t = (uint32_t)((key >> g.B) % g.L);
     const uint32_t sp = g.sp[t];
     const uint32_t fold = fill[key];
@@ -659,7 +679,8 @@ k_fb_collect(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint32_t t = 0; t < g.L; ++t) {
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-      const uint32_t b = bkt[t * ldb + i];
+      const uint32_t v = bkt[t * ldb + i];
+      const uint32_t b = g.rbits ? v >> g.rbits : v;
       const uint64_t id = id0 + i;
       const uint32_t s = shard_of(sm, g.S, id);
       const uint64_t key = (((uint64_t)s * g.L + t) << g.B) | b;
@@ -847,7 +868,8 @@ __device__ __forceinline__ uint32_t estimate(const Geo& g, const uint32_t* cmw, 
 //     keys are written (duplicates of an id share its key and are adjacent).
 __device__ void query_core(const Geo& g, const QueryLayout& lay, unsigned char* qsm,
                            const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill,
-                           uint32_t k, int32_t* __restrict__ ids_out, uint32_t* __restrict__ scores_out) {
+                           uint32_t k, int32_t* __restrict__ ids_out, uint32_t* __restrict__ scores_out,
+                           bool cm_ready = false) {
   uint64_t* pool = reinterpret_cast<uint64_t*>(qsm + lay.off_pool);
   uint32_t* cmw = reinterpret_cast<uint32_t*>(qsm + lay.off_cm);
   const uint32_t* bkey = reinterpret_cast<const uint32_t*>(qsm + lay.off_bkey);
@@ -858,8 +880,10 @@ __device__ void query_core(const Geo& g, const QueryLayout& lay, unsigned char* 
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, T = blockDim.x, NW = T >> 5;
   const uint32_t wmask = g.w - 1u, cmwords = (g.d * g.w) >> 1, nbk = lay.nbk;
   // -- clear the sketch; every bucket's fill and 32-id chunk count
-  uint4* cm4 = reinterpret_cast<uint4*>(cmw);
-  for (uint32_t i = threadIdx.x; i < cmwords / 4; i += T) cm4[i] = make_uint4(0, 0, 0, 0);
+  if (!cm_ready) {  // (the fused kernel clears it while the query is hashed)
+    uint4* cm4 = reinterpret_cast<uint4*>(cmw);
+    for (uint32_t i = threadIdx.x; i < cmwords / 4; i += T) cm4[i] = make_uint4(0, 0, 0, 0);
+  }
   if (threadIdx.x < C_Q) ctrl[threadIdx.x] = 0u;
   for (uint32_t i = threadIdx.x; i < nbk; i += T) bfill[i] = fill[bkey[i]];
   __syncthreads();
@@ -1141,45 +1165,44 @@ k_query_fused(const __grid_constant__ Geo g, const QueryLayout lay, const uint64
   uint32_t* m = reinterpret_cast<uint32_t*>(qsm + lay.off_m);
   uint32_t* mask = reinterpret_cast<uint32_t*>(qsm + lay.off_mask);
   uint32_t* ctrl = reinterpret_cast<uint32_t*>(qsm + lay.off_ctrl);
+  uint32_t* cmw = reinterpret_cast<uint32_t*>(qsm + lay.off_cm);
+  const uint32_t cm4n = (g.d * g.w) >> 3;  // uint4 words of the packed sketch
+  const uint32_t lane = threadIdx.x & 31u;
   for (;;) {
+    // fetch the next query while resetting the bins and clearing the sketch
     if (threadIdx.x == 0) ctrl[C_Q] = atomicAdd(work, 1u);
     for (uint32_t j = threadIdx.x; j < g.nb; j += blockDim.x) m[j] = kEmpty;
     if (threadIdx.x < g.nw) mask[threadIdx.x] = 0u;
+    uint4* cm4 = reinterpret_cast<uint4*>(cmw);
+    for (uint32_t i = threadIdx.x; i < cm4n; i += blockDim.x) cm4[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
     const uint32_t q = ctrl[C_Q];
     if (q >= nq) break;
+    // the whole block bins the query's features ...
     uint64_t b0 = offs[q], b1 = offs[q + 1];
     if (b1 < b0) {
       if (threadIdx.x == 0) atomicOr(err, kErrOffs);
       b1 = b0;
     }
-    bool bad = false;
-    for (uint64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-      const uint32_t f = __ldg(cols + i);
-      if (f >= g.dim) { bad = true; continue; }
-      const uint32_t h = mix32(f ^ g.a);
-      const uint32_t bin = __umulhi(h, g.nb);
-      atomicMin(&m[bin], h);
-      atomicOr(&mask[bin >> 5], 1u << (bin & 31u));
-    }
-    if (bad) atomicOr(err, kErrCol);
-    const int any = __syncthreads_or(threadIdx.x < g.nw && mask[threadIdx.x] != 0u);
-    if (any) {
-      for (uint32_t j = threadIdx.x; j < g.nb; j += blockDim.x) {
-        if (!((mask[j >> 5] >> (j & 31u)) & 1u)) {
-          const bool right = (g.dirbits[j >> 5] >> (j & 31u)) & 1u;
-          m[j] = m[nearest_bin(mask, g.nw, j, right)];
-        }
+    if (doph_scatter(g, cols, b0, b1, m, mask, threadIdx.x, blockDim.x)) atomicOr(err, kErrCol);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      // ... then warp 0 densifies and addresses the tables
+      doph_densify(g, m, mask, lane);
+      for (uint32_t it = lane; it < lay.nbk; it += 32) {
+        const uint32_t s = it / g.L, t = it - s * g.L;
+        bkey[it] = ((s * g.L + t) << g.B) | table_address(g, m, t);
       }
     }
     __syncthreads();
-    for (uint32_t it = threadIdx.x; it < lay.nbk; it += blockDim.x) {
-      const uint32_t s = it / g.L, t = it - s * g.L;
-      bkey[it] = ((s * g.L + t) << g.B) | table_address(g, m, t);
-    }
-    __syncthreads();
-    query_core(g, lay, qsm, slots, fill, k, ids_out + (uint64_t)q * k, scores_out + (uint64_t)q * k);
+    query_core(g, lay, qsm, slots, fill, k, ids_out + (uint64_t)q * k, scores_out + (uint64_t)q * k, true);
   }
+}
+
+// Offsets staged from a host CSR array, made relative to their first column.
+__global__ void k_rebase(uint64_t* __restrict__ offs, uint64_t n, uint64_t base) {
+  const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) offs[i] -= base;
 }
 
 // ----------------------------------------------------------------------------- host side
@@ -1219,6 +1242,12 @@ struct slash_index {
   uint32_t* ctr = nullptr;       // [0] big entries, [1] fallback entries
   uint64_t big_cap = 0, fb_cap = 0;
   float sigma = 8.0f;            // filter margin in binomial standard deviations
+  // host-fed insert: two device staging slots for CSR pieces, an internal copy stream
+  cudaStream_t copy_st = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  uint64_t* h2d_offs[2] = {nullptr, nullptr};
+  uint32_t* h2d_cols[2] = {nullptr, nullptr};
+  uint64_t h2d_rows = 0, h2d_nnz = 0;
   // query workspace (grow-only)
   uint64_t qws = 0;
   uint32_t* qbkt = nullptr;
@@ -1418,11 +1447,18 @@ int run_hash(slash_index* ix, const uint64_t* offs, const uint32_t* cols, uint32
 
 // One chunk of Algorithm 1: addresses + counts, staging plan, filtered
 // counting-sort scatter, per-bucket merges, exact fallback.
+int insert_tail(slash_index* ix, uint32_t n, uint64_t id0, cudaStream_t st);
+
 int insert_chunk(slash_index* ix, const uint64_t* offs, const uint32_t* cols, uint32_t n, uint64_t id0,
                  cudaStream_t st) {
-  const uint64_t nk = ix->nk;
   int rc = run_hash(ix, offs, cols, n, id0, ix->bkt, n, nullptr, true, st);
   if (rc) return rc;
+  return insert_tail(ix, n, id0, st);
+}
+
+// Everything after the addresses and counts of a chunk's n rows are in place.
+int insert_tail(slash_index* ix, uint32_t n, uint64_t id0, cudaStream_t st) {
+  const uint64_t nk = ix->nk;
   const uint32_t kblocks = (uint32_t)std::min<uint64_t>((nk + 255) / 256, (uint64_t)ix->num_sms * 32);
   {
     Launch l(ix, "k_plan", st);
@@ -1557,6 +1593,9 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
     uint32_t c = 64;
     while (c < most && c < kSmallMax) c <<= 1;
     ix->merge_cap = c;  // buckets beyond it take the CTA merge
+    // an unfiltered bucket gets at most 1.5 mu new pairs: their ranks must fit in 32-B bits
+    const uint32_t rb = 32u - p->log2_buckets;
+    ix->geo.rbits = (rb < 32u && (double)(1ull << rb) > 1.5 * mu + 1.0) ? rb : 0u;
   }
   ix->qdef.threads = default_query_threads(*p);
   {
@@ -1621,6 +1660,86 @@ int slash_insert(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_cols
   for (uint64_t r0 = 0; r0 < n_rows; r0 += chunk) {
     const uint32_t n = (uint32_t)std::min<uint64_t>(chunk, n_rows - r0);
     rc = insert_chunk(ix, d_offs + r0, d_cols, n, first + r0, st);
+    if (rc) return rc;
+  }
+  ix->next_id = first + n_rows;
+  if (first_id_out) *first_id_out = first;
+  return SLASH_OK;
+}
+
+int slash_insert_host(slash_index* ix, const uint64_t* h_offs, const uint32_t* h_cols, uint32_t n_rows,
+                      uint64_t* first_id_out, void* cuda_stream) {
+  if (!ix) return SLASH_EINVAL;
+  if (n_rows == 0) {
+    if (first_id_out) *first_id_out = ix->next_id;
+    return SLASH_OK;
+  }
+  if (!h_offs || !h_cols) return SLASH_EINVAL;
+  if (ix->next_id + n_rows > ix->p.capacity) return SLASH_EFULL;
+  for (uint64_t i = 0; i < n_rows; ++i)
+    if (h_offs[i + 1] < h_offs[i]) return SLASH_EINVAL;  // host offsets are checked here
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const uint64_t chunk = std::min<uint64_t>(insert_chunk_rows(ix), n_rows);
+  int rc = grow_insert_ws(ix, chunk);
+  if (rc) return rc;
+  // pieces of at most 2M rows are copied while the previous piece is hashed
+  const uint64_t piece = std::min<uint64_t>(chunk, 1ull << 21);
+  uint64_t most_nnz = 0;
+  for (uint64_t r0 = 0; r0 < n_rows; r0 += piece) {
+    const uint64_t r1 = std::min<uint64_t>(n_rows, r0 + piece);
+    most_nnz = std::max<uint64_t>(most_nnz, h_offs[r1] - h_offs[r0]);
+  }
+  if (!ix->copy_st) {
+    SLASH_CK(cudaStreamCreateWithFlags(&ix->copy_st, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      SLASH_CK(cudaEventCreateWithFlags(&ix->ev_copied[i], cudaEventDisableTiming));
+      SLASH_CK(cudaEventCreateWithFlags(&ix->ev_free[i], cudaEventDisableTiming));
+    }
+  }
+  if (piece > ix->h2d_rows || most_nnz > ix->h2d_nnz) {
+    SLASH_CK(cudaStreamSynchronize(st));
+    SLASH_CK(cudaStreamSynchronize(ix->copy_st));
+    for (int i = 0; i < 2; ++i) {
+      cudaFree(ix->h2d_offs[i]); cudaFree(ix->h2d_cols[i]);
+      ix->h2d_offs[i] = nullptr; ix->h2d_cols[i] = nullptr;
+    }
+    ix->h2d_rows = ix->h2d_nnz = 0;
+    for (int i = 0; i < 2; ++i) {
+      SLASH_CK(cudaMalloc(&ix->h2d_offs[i], sizeof(uint64_t) * (piece + 1)));
+      SLASH_CK(cudaMalloc(&ix->h2d_cols[i], sizeof(uint32_t) * std::max<uint64_t>(most_nnz, 1)));
+    }
+    ix->h2d_rows = piece;
+    ix->h2d_nnz = most_nnz;
+  }
+  const uint64_t first = ix->next_id;
+  // the copy stream starts after the work already queued on the caller's stream
+  SLASH_CK(cudaEventRecord(ix->ev_free[0], st));
+  SLASH_CK(cudaEventRecord(ix->ev_free[1], st));
+  uint32_t slot = 0;
+  for (uint64_t c0 = 0; c0 < n_rows; c0 += chunk) {
+    const uint32_t n = (uint32_t)std::min<uint64_t>(chunk, n_rows - c0);
+    for (uint64_t r0 = c0; r0 < c0 + n; r0 += piece) {
+      const uint64_t r1 = std::min<uint64_t>(c0 + n, r0 + piece);
+      const uint64_t base = h_offs[r0], nnz = h_offs[r1] - base;
+      SLASH_CK(cudaStreamWaitEvent(ix->copy_st, ix->ev_free[slot], 0));
+      SLASH_CK(cudaMemcpyAsync(ix->h2d_offs[slot], h_offs + r0, sizeof(uint64_t) * (r1 - r0 + 1),
+                               cudaMemcpyHostToDevice, ix->copy_st));
+      if (nnz)
+        SLASH_CK(cudaMemcpyAsync(ix->h2d_cols[slot], h_cols + base, sizeof(uint32_t) * nnz,
+                                 cudaMemcpyHostToDevice, ix->copy_st));
+      SLASH_CK(cudaEventRecord(ix->ev_copied[slot], ix->copy_st));
+      SLASH_CK(cudaStreamWaitEvent(st, ix->ev_copied[slot], 0));
+      {
+        Launch l(ix, "k_rebase", st);  // the staged offsets index the whole host array: make them relative
+        k_rebase<<<(uint32_t)((r1 - r0 + 1 + 255) / 256), 256, 0, st>>>(ix->h2d_offs[slot], r1 - r0 + 1, base);
+      }
+      rc = run_hash(ix, ix->h2d_offs[slot], ix->h2d_cols[slot], (uint32_t)(r1 - r0), first + r0,
+                    ix->bkt + (r0 - c0), n, nullptr, true, st);
+      if (rc) return rc;
+      SLASH_CK(cudaEventRecord(ix->ev_free[slot], st));
+      slot ^= 1u;
+    }
+    rc = insert_tail(ix, n, first + c0, st);
     if (rc) return rc;
   }
   ix->next_id = first + n_rows;
@@ -1748,6 +1867,12 @@ int slash_free(slash_index* ix) {
   cudaFree(ix->blocksum); cudaFree(ix->meta); cudaFree(ix->big);
   cudaFree(ix->fb); cudaFree(ix->fboff); cudaFree(ix->fbcur); cudaFree(ix->ctr); cudaFree(ix->qbkt);
   cudaFree(ix->work);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(ix->h2d_offs[i]); cudaFree(ix->h2d_cols[i]);
+    if (ix->ev_copied[i]) cudaEventDestroy(ix->ev_copied[i]);
+    if (ix->ev_free[i]) cudaEventDestroy(ix->ev_free[i]);
+  }
+  if (ix->copy_st) cudaStreamDestroy(ix->copy_st);
   for (auto& r : ix->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ix->prof_pool) cudaEventDestroy(e);
   delete ix;

@@ -48,6 +48,7 @@ __device__ __forceinline__ uint32_t cm_cell(uint32_t id, uint32_t sc_r, uint32_t
 // Index geometry and seeds, passed by value to every kernel (constant bank).
 struct Geo {
   uint32_t dim, K, L, nb, nw, B, R, d, w, S;
+  uint32_t rbits;                        // insert addresses carry the pair's rank in 32-B low bits (0: off)
   uint64_t capacity;
   uint32_t a, dirseed;
   uint32_t st[SLASH_MAX_L];              // table seeds

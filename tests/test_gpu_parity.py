@@ -334,3 +334,25 @@ def test_streamed_device_rows_top100_bit_exact():
     assert np.array_equal(ids.cpu().numpy(), want_ids)
     assert np.array_equal(_host_u32(sc), want_sc)
     assert np.mean((ids.cpu().numpy() == src[:, None]).any(axis=1)) > 0.9  # planted rows are found
+
+
+@pytest.mark.parametrize("chunk_rows", ["7000", "0"])
+def test_insert_from_host_memory_bit_exact(chunk_rows, monkeypatch):
+    """slash_insert_host (pinned host CSR, copies overlapped with hashing, many
+    pieces and chunks) builds the same index as the device-fed insert and the oracle."""
+    if chunk_rows != "0":
+        monkeypatch.setenv("SLASH_INSERT_CHUNK_ROWS", chunk_rows)
+    s = _slash()
+    g = datagen.Generator()
+    n = 50_000
+    offs, cols = g.rows(16, 0, n)
+    p = s.Params(K=6, L=64, log2_buckets=9, reservoir=16, cm_rows=4, cm_width=4096, capacity=n, seed=16)
+    want_slots, want_fill = _oracle_index(p, offs, cols).export()
+    h_offs = torch.from_numpy(offs.view(np.int64)).pin_memory()
+    h_cols = torch.from_numpy(cols.view(np.int32)).pin_memory()
+    with s.Index(p) as ix:
+        assert ix.insert_host(h_offs[:20_001], h_cols) == 0
+        assert ix.insert_host(h_offs[20_000:], h_cols) == 20_000
+        ix.sync()
+        slots, fill = ix.export()
+    assert np.array_equal(fill, want_fill) and np.array_equal(slots, want_slots)
