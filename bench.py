@@ -37,6 +37,7 @@ import datagen  # noqa: E402
 from datagen import workloads  # noqa: E402
 
 METRIC = "inserts/s and queries/s on 1 B300 (bit-exact), batched vs plain; serving p50/p99 ms"
+TK_METRIC = "inserts/s and queries/s with TopKAPI sketch buckets on 1 B300 (bit-exact)"
 
 
 def log(*a):
@@ -158,6 +159,7 @@ def run_reference(args, w: workloads.Workload) -> None:
     if rank != 0:
         return
     import oracle
+    tk = "tk_rows" in w.extra
     per_step = 30_000 if w.L >= 32 else 150_000
     total = per_step * (args.steps + args.warmup)
     g = datagen.Generator(dim_bits=w.dim_bits)
@@ -167,9 +169,13 @@ def run_reference(args, w: workloads.Workload) -> None:
         a, b = i * per_step, (i + 1) * per_step
         o = offs[a:b + 1]
         c = cols[int(o[0]):int(o[-1])]
-        ix = oracle.Index(K=w.K, L=w.L, log2_buckets=w.log2_buckets, reservoir=w.reservoir,
-                          cm_rows=w.cm_rows, cm_width=w.cm_width, shards=w.shards, seed=w.seed,
-                          capacity=w.n_rows)
+        if tk:
+            ix = oracle.TkIndex(K=w.K, L=w.L, log2_buckets=w.log2_buckets, rows=w.extra["tk_rows"],
+                                cells=w.extra["tk_cells"], shards=w.shards, seed=w.seed, capacity=w.n_rows)
+        else:
+            ix = oracle.Index(K=w.K, L=w.L, log2_buckets=w.log2_buckets, reservoir=w.reservoir,
+                              cm_rows=w.cm_rows, cm_width=w.cm_width, shards=w.shards, seed=w.seed,
+                              capacity=w.n_rows)
         t = time.perf_counter()
         ix.insert(o, c)
         dt = time.perf_counter() - t
@@ -177,19 +183,25 @@ def run_reference(args, w: workloads.Workload) -> None:
         if i >= args.warmup:
             times.append(dt)
     v = per_step / statistics.mean(times)
-    out = {"metric": METRIC, "value": v, "unit": "rows/s", "n_gpus": args.gpus, "steps": args.steps,
+    out = {"metric": TK_METRIC if tk else METRIC, "value": v, "unit": "rows/s", "n_gpus": args.gpus,
+           "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
            "impl": "reference",
            "config": config_of(w, args),
            "cpu_baseline": {"value": v, "unit": "rows/s", "cores": 1, "kind": "oracle",
                             "sample": f"{per_step} rows of the {w.name} workload per step, each step into "
-                                      f"a fresh dense oracle index (single thread)"},
+                                      f"a fresh {'sketch' if tk else 'dense'} oracle index (single thread)"},
            "e2e": {"value": v, "unit": "rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
 def config_of(w, args) -> dict:
+    if "tk_rows" in w.extra:
+        return {"workload": w.name, "rows_per_gpu": w.n_rows, "queries_per_gpu": w.n_queries, "K": w.K,
+                "L": w.L, "log2_buckets": w.log2_buckets, "sketch": f"{w.extra['tk_rows']}x{w.extra['tk_cells']}",
+                "topk": w.topk, "shards": w.shards, "parallelism": f"rows{args.gpus}",
+                "l2": "inputs larger than L2 (CSR and sketch arrays are GBs), no flush"}
     return {"workload": w.name, "rows_per_gpu": w.n_rows, "queries_per_gpu": w.n_queries, "K": w.K, "L": w.L,
             "log2_buckets": w.log2_buckets, "reservoir": w.reservoir, "cm": f"{w.cm_rows}x{w.cm_width}",
             "topk": w.topk, "shards": w.shards, "parallelism": f"rows{args.gpus}",
@@ -234,8 +246,9 @@ def main():
     if args.impl == "reference":
         run_reference(args, w)
         return
-    if w.name in ("uneven", "serving", "stream"):
-        fn = {"uneven": bench_uneven, "serving": bench_serving, "stream": bench_stream}[w.name]
+    if w.name in ("uneven", "serving", "stream", "topkapi", "sweep"):
+        fn = {"uneven": bench_uneven, "serving": bench_serving, "stream": bench_stream,
+              "topkapi": bench_topkapi, "sweep": bench_sweep}[w.name]
         print(json.dumps(fn(args, w)), flush=True)
         return
 
@@ -565,6 +578,163 @@ def bench_stream(args, w: workloads.Workload) -> dict:
             "dtype": "u32", "data": "synthetic (generated on the device)", "config": config_of(w, args),
             "generate_rows_per_s": n_rows / t_gen, "insert_only_rows_per_s": n_rows / (t_all - t_gen),
             "queries_per_s": nq / t_q, "planted_recall_at_k": recall, "clocks": clk.summary()}
+
+
+def bench_topkapi(args, w: workloads.Workload) -> dict:
+    """Sketch buckets (Sec. 3.1, Appendix 2): reset + insert the rows + answer
+    the queries per step, inputs resident in HBM; events around each call."""
+    torch, slash = _gpu_setup(w)
+    offs, cols, qo, qc, src = make_inputs(w, 0, w.n_rows, w.n_queries)
+    dev = lambda a: torch.from_numpy(a.view(np.int64 if a.dtype == np.uint64 else np.int32)).cuda()
+    d_offs, d_cols, d_qo, d_qc = dev(offs), dev(cols), dev(qo), dev(qc)
+    W, C = w.extra["tk_rows"], w.extra["tk_cells"]
+    p = slash.TkParams(dim=w.dim, K=w.K, L=w.L, log2_buckets=w.log2_buckets, rows=W, cells=C,
+                       shards=w.shards, seed=w.seed, capacity=w.n_rows)
+    ix = slash.TkIndex(p)
+    ids = torch.empty((w.n_queries, w.topk), dtype=torch.int32, device="cuda")
+    sc = torch.empty_like(ids)
+    st = torch.cuda.current_stream()
+
+    def step():
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(st)
+        ix.reset(st)
+        ev[1].record(st)
+        ix.insert(d_offs, d_cols, st)
+        ev[2].record(st)
+        slash.slash_tk_query(ix.h, d_qo, d_qc, w.topk, 0, ids, sc, st)
+        ev[3].record(st)
+        return ev
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    l0 = ix.launches
+    with Clocks(0) as clk:
+        evs = [step() for _ in range(args.steps)]
+        torch.cuda.synchronize()
+    launches = ix.launches - l0
+    ix.sync(st)
+    t_ins = statistics.mean(e[1].elapsed_time(e[2]) / 1e3 for e in evs)
+    t_q = statistics.mean(e[2].elapsed_time(e[3]) / 1e3 for e in evs)
+    t_step = statistics.mean(e[0].elapsed_time(e[3]) / 1e3 for e in evs)
+    recall = float(np.mean((ids.cpu().numpy() == src[:, None]).any(axis=1)))
+    pk = peaks()
+    nnz, qnnz = int(len(cols)), int(len(qc))
+    ins_bytes = 8 * w.n_rows + 4 * nnz + 8 * w.L * W * w.n_rows
+    q_bytes = 8 * w.n_queries + 4 * qnnz + 4 * w.shards * w.L * W * C * w.n_queries + 8 * w.topk * w.n_queries
+    kern = {"k_tk_insert": {"launches": args.steps, "ms_per_launch": 1e3 * t_ins},
+            "k_tk_query": {"launches": args.steps, "ms_per_launch": 1e3 * t_q}}
+    dom, b, t = ("k_tk_insert", ins_bytes, t_ins) if t_ins >= t_q else ("k_tk_query", q_bytes, t_q)
+    ach = b / t / 1e9
+    out = {"metric": TK_METRIC,
+           "value": w.n_rows / t_ins, "unit": "rows/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded Criteo-shaped generator)",
+           "config": config_of(w, args), "queries_per_s": w.n_queries / t_q,
+           "insert_ms": 1e3 * t_ins, "query_ms": 1e3 * t_q, "planted_recall_at_k": recall,
+           "roofline": {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": pk["source"],
+                        "algorithmic_bytes_per_launch": b,
+                        "bytes_def": ("8 + 4*nnz (CSR) + 8*L*W (cell word read + written) per row"
+                                      if dom == "k_tk_insert" else
+                                      "8 + 4*nnz (CSR) + 4*S*L*W*C (sketches) + 8*k (outputs) per query")},
+           "kernels": kern, "gpu_launches": int(launches), "clocks": clk.summary()}
+    ix.close()
+    if not args.no_cpu_baseline:
+        import oracle
+        n_s, nq = 100_000, 1000
+        ox = oracle.TkIndex(K=w.K, L=w.L, log2_buckets=w.log2_buckets, rows=W, cells=C, shards=w.shards,
+                            seed=w.seed, capacity=w.n_rows)
+        o = offs[:n_s + 1]
+        t0 = time.perf_counter()
+        ox.insert(o, cols[:int(o[-1])])
+        ti = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        ox.query(qo[:nq + 1], qc[:int(qo[nq])], w.topk)
+        tq = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": n_s / ti, "unit": "rows/s", "cores": 1, "kind": "oracle",
+                               "sample": f"first {n_s} rows inserted into the oracle's sketch index "
+                                         f"(single thread, {ti:.1f}s); queries/s {nq / tq:.1f} on {nq} queries",
+                               "queries_per_s": nq / tq}
+    return out
+
+
+def s_at_k(offs, cols, qo, qc, ids: np.ndarray, k: int) -> float:
+    """S@k of Sec. 6: mean cosine similarity between each query and its first k
+    reported rows (binary vectors: |x & q| / sqrt(|x| |q|)); -1 padding is skipped."""
+    tot, cnt = 0.0, 0
+    for i in range(ids.shape[0]):
+        q = qc[int(qo[i]):int(qo[i + 1])]
+        for j in ids[i, :k]:
+            if j < 0:
+                continue
+            x = cols[int(offs[j]):int(offs[j + 1])]
+            if len(x) == 0 or len(q) == 0:
+                cnt += 1
+                continue
+            tot += len(np.intersect1d(x, q, assume_unique=True)) / np.sqrt(len(x) * len(q))
+            cnt += 1
+    return tot / max(cnt, 1)
+
+
+def bench_sweep(args, w: workloads.Workload) -> dict:
+    """Quality/time sweep over L (K fixed at 4, as in Sec. 6): reservoir buckets
+    with count-min ranking, and TopKAPI sketch buckets of the same size."""
+    torch, slash = _gpu_setup(w)
+    offs, cols, qo, qc, src = make_inputs(w, 0, w.n_rows, w.n_queries)
+    qc_s = np.concatenate([np.sort(qc[int(qo[i]):int(qo[i + 1])]) for i in range(len(qo) - 1)]) if len(qc) else qc
+    dev = lambda a: torch.from_numpy(a.view(np.int64 if a.dtype == np.uint64 else np.int32)).cuda()
+    d_offs, d_cols, d_qo, d_qc = dev(offs), dev(cols), dev(qo), dev(qc)
+    st = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    n_eval = min(w.n_queries, 2000)
+    rows = []
+    with Clocks(0) as clk:
+        for L in w.extra["L_values"]:
+            for kind in ("reservoir", "topkapi"):
+                if kind == "reservoir":
+                    ix = slash.Index(slash.Params(**w.params(L=L)))
+                    q = lambda: ix.query(d_qo, d_qc, w.topk, st)
+                else:
+                    ix = slash.TkIndex(slash.TkParams(dim=w.dim, K=w.K, L=L, log2_buckets=w.log2_buckets,
+                                                      rows=w.extra["tk_rows_sweep"],
+                                                      cells=w.extra["tk_cells_sweep"], seed=w.seed,
+                                                      capacity=w.n_rows))
+                    q = lambda: ix.query(d_qo, d_qc, w.topk, stream=st)
+                t_i, t_q = [], []
+                for it in range(args.warmup + args.steps):
+                    a, b, c = ev(), ev(), ev()
+                    ix.reset(st)
+                    a.record(st)
+                    ix.insert(d_offs, d_cols, st)
+                    b.record(st)
+                    ids, _ = q()
+                    c.record(st)
+                    c.synchronize()
+                    if it >= args.warmup:
+                        t_i.append(a.elapsed_time(b) / 1e3)
+                        t_q.append(b.elapsed_time(c) / 1e3)
+                ix.sync(st)
+                h = ids.cpu().numpy()
+                rows.append({"L": L, "buckets": kind, "insert_rows_per_s": w.n_rows / statistics.mean(t_i),
+                             "queries_per_s": w.n_queries / statistics.mean(t_q),
+                             "S@1": s_at_k(offs, cols, qo, qc_s, h[:n_eval], 1),
+                             "S@64": s_at_k(offs, cols, qo, qc_s, h[:n_eval], 64),
+                             "planted_recall_at_64": float(np.mean((h == src[:, None]).any(axis=1)))})
+                log(f"[bench] sweep {rows[-1]}")
+                ix.close()
+    best = rows[-2]
+    return {"metric": "S@1 / S@64 and inserts/s, queries/s across L (K=4), reservoir vs TopKAPI buckets",
+            "value": best["queries_per_s"], "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * w.n_queries / best["queries_per_s"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+            "data": "synthetic", "config": {"workload": w.name, "rows": w.n_rows, "queries": w.n_queries,
+                                            "K": w.K, "L": list(w.extra["L_values"]),
+                                            "log2_buckets": w.log2_buckets, "reservoir": w.reservoir,
+                                            "sketch": f"{w.extra['tk_rows_sweep']}x{w.extra['tk_cells_sweep']}",
+                                            "topk": w.topk, "s_at_k_queries": n_eval},
+            "sweep": rows, "clocks": clk.summary()}
 
 
 if __name__ == "__main__":

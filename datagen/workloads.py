@@ -14,6 +14,12 @@ per row, power-law feature popularity), reduced to what one device holds:
              requests of 1..4096 queries (log-uniform), queries as `uneven`
   stream     1B rows streamed in 16M-row chunks, K=8 L=32 2^20 buckets R=256
              (~34 GB of buckets), 4x8192 sketch, 1M queries, top-100
+  topkapi    rows and queries of `criteo`, TopKAPI sketch buckets of 4 rows x
+             32 cells (512 B per bucket, the size of an R=128 reservoir;
+             ~8.6 GB), top-10
+  sweep      quality sweep of Sec. 6 (K = 4; L = 16, 24, 32): 1M rows, 2^16
+             buckets, R=32 or TopKAPI 4x8 (same bytes), 10k planted queries
+             (20% resampled), S@1 and S@64
 """
 from __future__ import annotations
 
@@ -70,7 +76,13 @@ SERVING = Workload("serving", 100_000, 4, 16, 16, 32, 4, 8192, 0, 10, shards=8,
 STREAM = Workload("stream", 1_000_000_000, 8, 32, 20, 256, 4, 8192, 1_000_000, 100, p_perturb=0.1,
                   extra={"chunk_rows": 16 << 20, "retain_every": 1000})
 
-ALL = {w.name: w for w in (TINY, CRITEO, UNEVEN, SERVING, STREAM)}
+TOPKAPI = Workload("topkapi", 50_000_000, 6, 64, 18, 0, 0, 0, 100_000, 10, p_perturb=0.1,
+                   extra={"tk_rows": 4, "tk_cells": 32})
+
+SWEEP = Workload("sweep", 1_000_000, 4, 32, 16, 32, 4, 8192, 10_000, 64, p_perturb=0.2,
+                 extra={"L_values": (16, 24, 32), "tk_rows_sweep": 4, "tk_cells_sweep": 8})
+
+ALL = {w.name: w for w in (TINY, CRITEO, UNEVEN, SERVING, STREAM, TOPKAPI, SWEEP)}
 
 LOGNORMAL_MU = math.log(40.0)
 LOGNORMAL_SIGMA = 1.0

@@ -54,6 +54,7 @@ extern "C" {
 #define SLASH_EBUSY    (-5)  /* admission refused (serving layer)                  */
 #define SLASH_ETIMEOUT (-6)  /* a bounded device wait gave up                      */
 #define SLASH_EDATA    (-7)  /* the device found invalid input data (see above)    */
+#define SLASH_EIO      (-8)  /* a checkpoint file could not be opened, written or read */
 
 #define SLASH_EMPTY 0xFFFFFFFFu /* an unused bucket slot */
 
@@ -161,6 +162,24 @@ int slash_autotune(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_co
  * work overlaps on the GPU (other streams, or without ordering) race on it. */
 int slash_query_static(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n_queries,
                        uint32_t topk, int32_t *d_ids_out, uint32_t *d_scores_out, void *cuda_stream);
+
+/* Checkpoint (no counterpart in the paper, whose index lives only for one run):
+ * write the whole index state -- parameters, the next id, fill counts and
+ * bucket slots -- to the file `path` (created or truncated), after a header
+ * with a 64-bit checksum of the arrays.  Synchronises the device.
+ * Errors: SLASH_EINVAL (NULL), SLASH_EIO (file), SLASH_ECUDA, SLASH_ENOMEM
+ * (the 64 MiB page-locked staging buffer). */
+int slash_save(slash_index *ix, const char *path);
+
+/* Build an index on the current device from a slash_save file; inserts and
+ * queries then continue exactly as on the saved index (same ids, buckets and
+ * results).  Synchronises.  Errors: SLASH_EIO (cannot open), SLASH_EINVAL (not
+ * such a checkpoint, parameters outside the limits, truncated, trailing bytes
+ * or checksum mismatch; nothing is returned), SLASH_ENOMEM, SLASH_ECUDA. */
+int slash_load(const char *path, void *cuda_stream, slash_index **out);
+
+/* The parameters the index was built (or loaded) with.  Errors: SLASH_EINVAL. */
+int slash_get_params(const slash_index *ix, slash_params *out);
 
 /* Release the index and its workspace (synchronises the device first).
  * NULL is accepted.  Always SLASH_OK unless a CUDA call fails. */

@@ -93,7 +93,7 @@ def _load():
             lib.or_tk_insert.argtypes = [vp, vp, vp, u64, ctypes.POINTER(u64)]
             lib.or_tk_export.argtypes = [vp, vp]
             lib.or_tk_query.restype = i32
-            lib.or_tk_query.argtypes = [vp, vp, vp, u64, u32, vp, vp]
+            lib.or_tk_query.argtypes = [vp, vp, vp, u64, u32, u32, vp, vp]
             _lib = lib
     return _lib
 
@@ -304,10 +304,11 @@ class TkIndex:
         self._lib.or_tk_export(self._h, _p(out))
         return out
 
-    def query(self, offs, cols, k: int):
+    def query(self, offs, cols, k: int, threshold: int = 0):
+        """Top-k heavy hitters of the merged sketch whose count exceeds ``threshold``."""
         offs, cols = _u64(offs), _u32(cols)
         nq = offs.size - 1
         ids = np.empty((nq, k), dtype=np.int32)
         scores = np.empty((nq, k), dtype=np.uint32)
-        self._lib.or_tk_query(self._h, _p(offs), _p(cols), nq, k, _p(ids), _p(scores))
+        self._lib.or_tk_query(self._h, _p(offs), _p(cols), nq, k, threshold, _p(ids), _p(scores))
         return ids, scores

@@ -482,7 +482,8 @@ uint64_t or_next_id(const void *p) { return ((const or_index *)p)->next_id; }
  *                wins with the difference; equal counts cancel to an empty cell
  *   query        fold the query's buckets, shard-major then table order, into
  *                an empty sketch; each heavy hitter's score is its largest
- *                count over the cells; rank by (score desc, id asc), pad (-1,0)
+ *                count over the cells; those with a score above the threshold
+ *                (Appendix 2, "Querying") rank by (score desc, id asc); pad (-1,0)
  */
 typedef struct {
   uint32_t K, L, B, W, C, S;
@@ -559,9 +560,10 @@ void or_tk_export(const void *p, uint32_t *out) {
   }
 }
 
-/* Algorithm 2 with sketches: merge the query's buckets, report the top-k heavy hitters. */
+/* Algorithm 2 with sketches: merge the query's S*L buckets (shard-major, then table) into one
+ * sketch, report its top-k heavy hitters by (count descending, id ascending). */
 int or_tk_query(const void *p, const uint64_t *offs, const uint32_t *cols, uint64_t nq, uint32_t k,
-                int32_t *ids, uint32_t *scores) {
+                uint32_t threshold, int32_t *ids, uint32_t *scores) {
   const or_tk *ix = (const or_tk *)p;
   uint32_t nb = ix->K * ix->L, WC = ix->W * ix->C;
   const uint32_t *st = ix->seeds + 2;
@@ -577,10 +579,11 @@ int or_tk_query(const void *p, const uint64_t *offs, const uint32_t *cols, uint6
         uint64_t base = ((((uint64_t)s * ix->L + t) << ix->B) + b) * WC;
         for (uint32_t c = 0; c < WC; ++c) or_tk_merge_cell(mh + c, mc + c, ix->hh[base + c], ix->cnt[base + c]);
       }
-    /* distinct heavy hitters, each with its largest count */
+    /* distinct heavy hitters, each with its largest count; Appendix 2 reports
+     * those whose count exceeds the threshold */
     uint32_t nc = 0;
     for (uint32_t c = 0; c < WC; ++c) {
-      if (mc[c] == 0) continue;
+      if (mc[c] == 0 || mc[c] <= threshold) continue;
       uint32_t j = 0;
       while (j < nc && cand[j].id != mh[c]) ++j;
       if (j == nc) { cand[nc].id = mh[c]; cand[nc].est = mc[c]; ++nc; }

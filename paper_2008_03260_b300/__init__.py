@@ -34,6 +34,7 @@ SLASH_EFULL = -4
 SLASH_EBUSY = -5
 SLASH_ETIMEOUT = -6
 SLASH_EDATA = -7
+SLASH_EIO = -8
 SLASH_EMPTY = 0xFFFFFFFF
 SLASH_MAX_TOPK = 256
 
@@ -64,6 +65,13 @@ class slash_params(ctypes.Structure):
                 ("capacity", ctypes.c_uint64)]
 
 
+class slash_tk_params(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_uint32), ("K", ctypes.c_uint32), ("L", ctypes.c_uint32),
+                ("log2_buckets", ctypes.c_uint32), ("rows", ctypes.c_uint32), ("cells", ctypes.c_uint32),
+                ("shards", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("capacity", ctypes.c_uint64)]
+
+
 def _load() -> ctypes.CDLL:
     from . import build as _build
     if _build.needs_build():  # compile the CUDA library in place (nvcc); no fallback if that fails
@@ -91,6 +99,21 @@ def _load() -> ctypes.CDLL:
         "slash_query_static": (i32, [vp, vp, vp, u32, u32, vp, vp, vp]),
         "slash_profile": (i32, [vp, i32]),
         "slash_profile_read": (i32, [vp, u32, vp, vp, vp, P(u32), P(u64)]),
+        "slash_tk_build": (i32, [P(slash_tk_params), vp, P(vp)]),
+        "slash_tk_insert": (i32, [vp, vp, vp, u32, P(u64), vp]),
+        "slash_tk_query": (i32, [vp, vp, vp, u32, u32, u32, vp, vp, vp]),
+        "slash_tk_export": (i32, [vp, vp]),
+        "slash_tk_sync": (i32, [vp, vp]),
+        "slash_tk_reset": (i32, [vp, vp]),
+        "slash_tk_size": (u64, [vp]),
+        "slash_tk_launches": (u64, [vp]),
+        "slash_tk_free": (i32, [vp]),
+        "slash_save": (i32, [vp, ctypes.c_char_p]),
+        "slash_load": (i32, [ctypes.c_char_p, vp, P(vp)]),
+        "slash_get_params": (i32, [vp, P(slash_params)]),
+        "slash_tk_save": (i32, [vp, ctypes.c_char_p]),
+        "slash_tk_load": (i32, [ctypes.c_char_p, vp, P(vp)]),
+        "slash_tk_get_params": (i32, [vp, P(slash_tk_params)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -308,12 +331,40 @@ def slash_profile_read(ix: int, max_kernels: int = 32) -> tuple[dict, int]:
     return out, int(tot.value)
 
 
-class Index:
-    """Owning wrapper: ``Index(Params(...))``, ``.insert``, ``.query``, ``.close``."""
+def slash_save(ix: int, path: str) -> None:
+    _check(_lib.slash_save(ix, os.fsencode(path)), "slash_save")
 
-    def __init__(self, p: Params, stream=None):
-        self.p = p
-        self.h = slash_build_index(p, stream)
+
+def slash_load(path: str, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.slash_load(os.fsencode(path), _stream(stream), ctypes.byref(h)), "slash_load")
+    return h.value
+
+
+def slash_get_params(ix: int) -> Params:
+    cp = slash_params()
+    _check(_lib.slash_get_params(ix, ctypes.byref(cp)), "slash_get_params")
+    return Params(**{f: getattr(cp, f) for f, _ in slash_params._fields_})
+
+
+class Index:
+    """Owning wrapper: ``Index(Params(...))``, ``.insert``, ``.query``, ``.close``;
+    ``Index.load(path)`` reopens a ``.save(path)`` checkpoint."""
+
+    def __init__(self, p: Params | None, stream=None, _handle: int | None = None):
+        if _handle is not None:
+            self.h = _handle
+            self.p = slash_get_params(_handle)
+        else:
+            self.p = p
+            self.h = slash_build_index(p, stream)
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Index":
+        return cls(None, stream, _handle=slash_load(path, stream))
+
+    def save(self, path: str) -> None:
+        slash_save(self.h, path)
 
     def insert(self, d_offs, d_cols, stream=None) -> int:
         return slash_insert(self.h, d_offs, d_cols, stream)
@@ -356,6 +407,154 @@ class Index:
         h, self.h = self.h, None
         if h:
             slash_free(h)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------- TopKAPI buckets
+@dataclass(frozen=True)
+class TkParams:
+    """Sketch-bucket index parameters (see ``slash_tk_params`` in include/slash_topkapi.h)."""
+    dim: int = 1 << 20
+    K: int = 4
+    L: int = 16
+    log2_buckets: int = 12
+    rows: int = 4
+    cells: int = 32
+    shards: int = 1
+    seed: int = 0
+    capacity: int = 100_000
+
+    def c(self) -> slash_tk_params:
+        return slash_tk_params(self.dim, self.K, self.L, self.log2_buckets, self.rows, self.cells,
+                               self.shards, 0, self.seed, self.capacity)
+
+    @property
+    def index_bytes(self) -> int:
+        return (self.shards * self.L << self.log2_buckets) * self.rows * self.cells * 4
+
+
+def slash_tk_build(p: TkParams, stream=None) -> int:
+    h = ctypes.c_void_p()
+    cp = p.c()
+    _check(_lib.slash_tk_build(ctypes.byref(cp), _stream(stream), ctypes.byref(h)), "slash_tk_build")
+    return h.value
+
+
+def slash_tk_insert(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, stream=None) -> int:
+    n = d_offs.numel() - 1
+    if n < 0:
+        raise ValueError("d_offs needs n+1 entries")
+    first = ctypes.c_uint64()
+    _check(_lib.slash_tk_insert(ix, _dev_ptr(d_offs, 8, "d_offs"), _dev_ptr(d_cols, 4, "d_cols"), n,
+                                ctypes.byref(first), _stream(stream)), "slash_tk_insert")
+    return int(first.value)
+
+
+def slash_tk_query(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, topk: int, threshold: int = 0,
+                   d_ids_out: torch.Tensor | None = None, d_scores_out: torch.Tensor | None = None,
+                   stream=None) -> tuple[torch.Tensor, torch.Tensor]:
+    nq = d_offs.numel() - 1
+    if nq < 0:
+        raise ValueError("d_offs needs n+1 entries")
+    dev = d_offs.device
+    if d_ids_out is None:
+        d_ids_out = torch.empty((nq, topk), dtype=torch.int32, device=dev)
+    if d_scores_out is None:
+        d_scores_out = torch.empty((nq, topk), dtype=torch.int32, device=dev)
+    if d_ids_out.numel() < nq * topk or d_scores_out.numel() < nq * topk:
+        raise ValueError("output tensors too small")
+    _check(_lib.slash_tk_query(ix, _dev_ptr(d_offs, 8, "d_offs"), _dev_ptr(d_cols, 4, "d_cols"), nq, topk,
+                               threshold, _dev_ptr(d_ids_out, 4, "d_ids_out"),
+                               _dev_ptr(d_scores_out, 4, "d_scores_out"), _stream(stream)), "slash_tk_query")
+    return d_ids_out, d_scores_out
+
+
+def slash_tk_export(ix: int, p: TkParams):
+    """Cell words [S][L][2^B][W][C]: 0 = empty, else heavy hitter id + 1 (count 1)."""
+    import numpy as np
+    out = np.empty((p.shards, p.L, 1 << p.log2_buckets, p.rows, p.cells), dtype=np.uint32)
+    _check(_lib.slash_tk_export(ix, out.ctypes.data), "slash_tk_export")
+    return out
+
+
+def slash_tk_free(ix: int) -> None:
+    if ix:
+        _check(_lib.slash_tk_free(ix), "slash_tk_free")
+
+
+def slash_tk_save(ix: int, path: str) -> None:
+    _check(_lib.slash_tk_save(ix, os.fsencode(path)), "slash_tk_save")
+
+
+def slash_tk_load(path: str, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.slash_tk_load(os.fsencode(path), _stream(stream), ctypes.byref(h)), "slash_tk_load")
+    return h.value
+
+
+def slash_tk_get_params(ix: int) -> TkParams:
+    cp = slash_tk_params()
+    _check(_lib.slash_tk_get_params(ix, ctypes.byref(cp)), "slash_tk_get_params")
+    return TkParams(**{f: getattr(cp, f) for f, _ in slash_tk_params._fields_ if f != "reserved"})
+
+
+class TkIndex:
+    """Owning wrapper of a sketch-bucket index: ``.insert``, ``.query``, ``.export``;
+    ``TkIndex.load(path)`` reopens a ``.save(path)`` checkpoint."""
+
+    def __init__(self, p: TkParams | None, stream=None, _handle: int | None = None):
+        if _handle is not None:
+            self.h = _handle
+            self.p = slash_tk_get_params(_handle)
+        else:
+            self.p = p
+            self.h = slash_tk_build(p, stream)
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "TkIndex":
+        return cls(None, stream, _handle=slash_tk_load(path, stream))
+
+    def save(self, path: str) -> None:
+        slash_tk_save(self.h, path)
+
+    def insert(self, d_offs, d_cols, stream=None) -> int:
+        return slash_tk_insert(self.h, d_offs, d_cols, stream)
+
+    def query(self, d_offs, d_cols, topk: int, threshold: int = 0, stream=None):
+        return slash_tk_query(self.h, d_offs, d_cols, topk, threshold, stream=stream)
+
+    def export(self):
+        return slash_tk_export(self.h, self.p)
+
+    def sync(self, stream=None) -> None:
+        _check(int(_lib.slash_tk_sync(self.h, _stream(stream))), "slash_tk_sync")
+
+    def reset(self, stream=None) -> None:
+        _check(_lib.slash_tk_reset(self.h, _stream(stream)), "slash_tk_reset")
+
+    @property
+    def size(self) -> int:
+        return int(_lib.slash_tk_size(self.h))
+
+    @property
+    def launches(self) -> int:
+        return int(_lib.slash_tk_launches(self.h))
+
+    def close(self) -> None:
+        h, self.h = self.h, None
+        if h:
+            slash_tk_free(h)
 
     def __enter__(self):
         return self

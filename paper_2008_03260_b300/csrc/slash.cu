@@ -56,6 +56,7 @@
 
 #include "slash.h"
 #include "slash_device.cuh"
+#include "slash_io.h"
 
 using namespace slash;
 
@@ -65,93 +66,6 @@ namespace {
 constexpr int kHashWarps = 8;
 constexpr int kRowsPerWarp = 4;
 constexpr int kHashRows = kHashWarps * kRowsPerWarp;  // rows per CTA
-
-// DOPH of one CSR row by one warp into m[nb] (smem), using mask[nw] (smem).
-// Densification works on lane chunks: lane l owns bins [l*c, l*c + c),
-// c = ceil(nb/32); the nearest non-empty bin inside the chunk comes from bit
-// scans of the chunk's mask bits, and across chunks from a circular pointer-
-// jumping scan over the lanes' first / last non-empty bins.
-// Binning of Sec. 4.1 (Eq. 3) by threads [i0, i0+stride) of a cooperating
-// group: each feature's hash goes to its bin's minimum, its bit to the mask.
-// Returns whether this thread skipped a feature id >= dim.
-__device__ __forceinline__ bool doph_scatter(const Geo& g, const uint32_t* __restrict__ cols, uint64_t b0,
-                                             uint64_t b1, uint32_t* m, uint32_t* mask, uint32_t i0,
-                                             uint32_t stride) {
-  bool bad = false;
-  for (uint64_t i = b0 + i0; i < b1; i += stride) {
-    const uint32_t f = __ldg(cols + i);
-    if (f >= g.dim) { bad = true; continue; }
-    const uint32_t h = mix32(f ^ g.a);
-    const uint32_t bin = __umulhi(h, g.nb);
-    atomicMin(&m[bin], h);
-    atomicOr(&mask[bin >> 5], 1u << (bin & 31u));
-  }
-  return bad;
-}
-
-__device__ __forceinline__ void doph_densify(const Geo& g, uint32_t* m, const uint32_t* mask, uint32_t lane);
-
-__device__ __forceinline__ void doph_row(const Geo& g, const uint32_t* __restrict__ cols, uint64_t b0,
-                                         uint64_t b1, uint32_t* m, uint32_t* mask, uint32_t* err,
-                                         uint32_t lane) {
-  uint4* m4 = reinterpret_cast<uint4*>(m);  // m is 16-byte aligned
-  for (uint32_t j = lane; j < (g.nb >> 2); j += 32) m4[j] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
-  for (uint32_t j = (g.nb & ~3u) + lane; j < g.nb; j += 32) m[j] = kEmpty;
-  if (lane < g.nw) mask[lane] = 0u;
-  __syncwarp();
-  const bool bad = doph_scatter(g, cols, b0, b1, m, mask, lane, 32u);
-  if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicOr(err, kErrCol);
-  __syncwarp();
-  doph_densify(g, m, mask, lane);
-}
-
-// Densification of Sec. 4.1 by one warp, after the binning is complete.
-__device__ __forceinline__ void doph_densify(const Geo& g, uint32_t* m, const uint32_t* mask, uint32_t lane) {
-  constexpr uint32_t kNone = 0xFFFFFFFFu;
-  const uint32_t c = (g.nb + 31u) >> 5;          // bins per lane (1..32)
-  const uint32_t lo = lane * c;
-  const uint32_t cnt = lo < g.nb ? min(c, g.nb - lo) : 0u;
-  uint32_t cb = 0u, db = 0u;                     // my chunk's non-empty bits and side bits
-  if (cnt) {
-    const uint32_t w = lo >> 5, s = lo & 31u;
-    const uint64_t mw = ((uint64_t)(w + 1 < g.nw ? mask[w + 1] : 0u) << 32) | mask[w];
-    const uint64_t dw = ((uint64_t)(w + 1 < g.nw ? g.dirbits[w + 1] : 0u) << 32) | g.dirbits[w];
-    const uint32_t keep = cnt == 32u ? 0xFFFFFFFFu : ((1u << cnt) - 1u);
-    cb = (uint32_t)(mw >> s) & keep;
-    db = (uint32_t)(dw >> s) & keep;
-  }
-  if (!__any_sync(0xFFFFFFFFu, cb != 0u)) return;  // empty row: every code stays 0xFFFFFFFF
-  const uint32_t first = cb ? lo + (uint32_t)(__ffs(cb) - 1) : kNone;
-  const uint32_t last = cb ? lo + 31u - (uint32_t)__clz(cb) : kNone;
-  // right: first non-empty among lanes l+1, l+2, ... (circular); left: mirror
-  uint32_t rn = __shfl_sync(0xFFFFFFFFu, first, (lane + 1u) & 31u);
-  uint32_t ln = __shfl_sync(0xFFFFFFFFu, last, (lane + 31u) & 31u);
-#pragma unroll
-  for (uint32_t d = 1; d < 32; d <<= 1) {
-    const uint32_t ro = __shfl_sync(0xFFFFFFFFu, rn, (lane + d) & 31u);
-    const uint32_t lo2 = __shfl_sync(0xFFFFFFFFu, ln, (lane + 32u - d) & 31u);
-    if (rn == kNone) rn = ro;
-    if (ln == kNone) ln = lo2;
-  }
-  // branch-free: an empty bin reads the nearest non-empty bin on its side; a
-  // non-empty bin rewrites its own value.  Only non-empty bins are read, and
-  // their values never change, so the update is safe in place.
-  for (uint32_t p = 0; p < cnt; ++p) {
-    const uint32_t above = cb & ((0xFFFFFFFEu << p));            // bits > p (p < 32)
-    const uint32_t below = cb & ((1u << p) - 1u);                // bits < p
-    const uint32_t kr = above ? lo + (uint32_t)(__ffs(above) - 1) : rn;
-    const uint32_t kl = below ? lo + 31u - (uint32_t)__clz(below) : ln;
-    const uint32_t k = ((cb >> p) & 1u) ? lo + p : (((db >> p) & 1u) ? kr : kl);
-    m[lo + p] = m[k];
-  }
-  __syncwarp();
-}
-
-__device__ __forceinline__ uint32_t table_address(const Geo& g, const uint32_t* m, uint32_t t) {
-  uint32_t acc = g.st[t];
-  for (uint32_t j = 0; j < g.K; ++j) acc = (acc ^ m[t * g.K + j]) * kGold32;
-  return mix32(acc) >> (32u - g.B);
-}
 
 // Rows [blockIdx.x*32, +32): addresses -> bkt[t*ldb + row] (table-major),
 // optional codes [n][nb], optional per-bucket counts (insert).
@@ -1206,15 +1120,63 @@ __global__ void k_rebase(uint64_t* __restrict__ offs, uint64_t n, uint64_t base)
 }
 
 // ----------------------------------------------------------------------------- host side
-uint64_t splitmix64_next(uint64_t* s) {
-  *s += 0x9E3779B97F4A7C15ull;
-  uint64_t z = *s;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
 
 }  // namespace
+
+namespace slash {
+
+size_t hash_smem_bytes(const Geo& g) {
+  const size_t per_warp = (g.nb + g.nw + 3u) & ~3u;
+  return sizeof(uint32_t) * ((size_t)kHashWarps * per_warp + (size_t)g.L * kHashRows);
+}
+
+void init_hash_kernels(int smem_optin) {
+  const int so = smem_optin;
+  cudaFuncSetAttribute(k_hash<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_hash<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+#define SLASH_HATTR(CC, KK)                                                                              \
+  cudaFuncSetAttribute(k_hash_reg<CC, KK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);    \
+  cudaFuncSetAttribute(k_hash_reg<CC, KK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  SLASH_HATTR(12, 6) SLASH_HATTR(12, 4) SLASH_HATTR(8, 8) SLASH_HATTR(8, 4) SLASH_HATTR(4, 4) SLASH_HATTR(16, 8)
+#undef SLASH_HATTR
+}
+
+int launch_hash(const Geo& g, const ShardMap& sm, const uint64_t* offs, const uint32_t* cols, uint32_t n,
+                uint64_t id0, uint32_t* bkt, uint64_t ldb, uint32_t* codes, uint32_t* cnt, uint32_t* err,
+                cudaStream_t st) {
+  if (n == 0) return SLASH_OK;
+  const dim3 grid((n + kHashRows - 1) / kHashRows);
+  const bool count = cnt != nullptr;
+  const uint32_t nb = g.nb, K = g.K;
+  const uint32_t C = nb % 32u == 0u ? nb / 32u : 0u;
+  const size_t rsmem = sizeof(uint32_t) * ((size_t)kHashWarps * (((nb + 33u) + 3u) & ~3u) +
+                                           (size_t)g.L * kHashRows);
+#define SLASH_HREG(CC, KK)                                                                                  \
+  if (C == CC && K == KK) {                                                                              \
+    if (count)                                                                                           \
+      k_hash_reg<CC, KK, true><<<grid, kHashWarps * 32, rsmem, st>>>(g, sm, offs, cols, n, id0, bkt, ldb,  \
+                                                                   codes, cnt, err);                     \
+    else                                                                                                 \
+      k_hash_reg<CC, KK, false><<<grid, kHashWarps * 32, rsmem, st>>>(g, sm, offs, cols, n, id0, bkt, ldb, \
+                                                                    codes, nullptr, err);                \
+    return cudaGetLastError() == cudaSuccess ? SLASH_OK : SLASH_ECUDA;                                   \
+  }
+  SLASH_HREG(12, 6)
+  SLASH_HREG(12, 4)
+  SLASH_HREG(8, 8)
+  SLASH_HREG(8, 4)
+  SLASH_HREG(4, 4)
+  SLASH_HREG(16, 8)
+#undef SLASH_HREG
+  const size_t smem = hash_smem_bytes(g);
+  if (count)
+    k_hash<true><<<grid, kHashWarps * 32, smem, st>>>(g, sm, offs, cols, n, id0, bkt, ldb, codes, cnt, err);
+  else
+    k_hash<false><<<grid, kHashWarps * 32, smem, st>>>(g, sm, offs, cols, n, id0, bkt, ldb, codes, nullptr, err);
+  return cudaGetLastError() == cudaSuccess ? SLASH_OK : SLASH_ECUDA;
+}
+
+}  // namespace slash
 
 struct slash_index {
   slash_params p{};
@@ -1359,19 +1321,12 @@ int grow_query_ws(slash_index* ix, uint64_t nq) {
   return SLASH_OK;
 }
 
-size_t hash_smem(const slash_index* ix) {
-  const size_t per_warp = (ix->geo.nb + ix->geo.nw + 3u) & ~3u;
-  return sizeof(uint32_t) * ((size_t)kHashWarps * per_warp + (size_t)ix->p.L * kHashRows);
-}
+size_t hash_smem(const slash_index* ix) { return hash_smem_bytes(ix->geo); }
 
-ShardMap shard_map(const slash_index* ix) {
-  ShardMap m{};
-  const uint64_t S = ix->p.shards, C = ix->p.capacity;
-  for (uint64_t s = 0; s <= S && s <= kMaxShards; ++s) m.start[s] = (s * C + S - 1) / S;  // ceil(s*C/S)
-  return m;
-}
+ShardMap shard_map(const slash_index* ix) { return make_shard_map(ix->p.shards, ix->p.capacity); }
 
-QueryLayout make_query_layout(const slash_params& p) {
+// Shared-memory layout of a query CTA of `threads` threads.
+QueryLayout make_query_layout(const slash_params& p, uint32_t threads) {
   QueryLayout l{};
   l.maxm = p.shards * p.L * p.reservoir;  // <= 65535 (checked at build)
   l.nbk = p.shards * p.L;
@@ -1393,7 +1348,7 @@ QueryLayout make_query_layout(const slash_params& p) {
   l.off_ctrl = o;  o = al(o + 16u * 4u);
   l.nchunkmax = l.nbk * ((p.reservoir + 31u) / 32u);
   l.off_cbk = o;   o = al(o + l.nchunkmax * 4u);
-  l.off_cells = o; o = al(o + kRegIds * 1024u * 8u);  // 4 x 16-bit cells per register occurrence
+  l.off_cells = o; o = al(o + kRegIds * threads * 8u);  // 4 x 16-bit cells per register occurrence
   l.bytes = o;
   return l;
 }
@@ -1409,40 +1364,9 @@ uint32_t default_query_threads(const slash_params& p) {
 int run_hash(slash_index* ix, const uint64_t* offs, const uint32_t* cols, uint32_t n, uint64_t id0,
              uint32_t* bkt, uint64_t ldb, uint32_t* codes, bool count, cudaStream_t st) {
   if (n == 0) return SLASH_OK;
-  const ShardMap sm = shard_map(ix);
-  const dim3 grid((n + kHashRows - 1) / kHashRows);
   Launch lg(ix, count ? "k_hash_insert" : "k_hash", st);
-  const uint32_t nb = ix->geo.nb, K = ix->p.K;
-  const uint32_t C = nb % 32u == 0u ? nb / 32u : 0u;
-  const size_t rsmem = sizeof(uint32_t) * ((size_t)kHashWarps * (((nb + 33u) + 3u) & ~3u) +
-                                           (size_t)ix->p.L * kHashRows);
-#define SLASH_HREG(CC, KK)                                                                              \
-  if (C == CC && K == KK) {                                                                          \
-    if (count)                                                                                       \
-      k_hash_reg<CC, KK, true><<<grid, kHashWarps * 32, rsmem, st>>>(ix->geo, sm, offs, cols, n, id0, \
-                                                                   bkt, ldb, codes, ix->cnt, ix->err); \
-    else                                                                                             \
-      k_hash_reg<CC, KK, false><<<grid, kHashWarps * 32, rsmem, st>>>(ix->geo, sm, offs, cols, n, id0, \
-                                                                    bkt, ldb, codes, nullptr, ix->err); \
-    SLASH_CK(cudaGetLastError());                                                                    \
-    return SLASH_OK;                                                                                 \
-  }
-  SLASH_HREG(12, 6)
-  SLASH_HREG(12, 4)
-  SLASH_HREG(8, 8)
-  SLASH_HREG(8, 4)
-  SLASH_HREG(4, 4)
-  SLASH_HREG(16, 8)
-#undef SLASH_HREG
-  const size_t smem = hash_smem(ix);
-  if (count)
-    k_hash<true><<<grid, kHashWarps * 32, smem, st>>>(ix->geo, sm, offs, cols, n, id0, bkt, ldb, codes,
-                                                      ix->cnt, ix->err);
-  else
-    k_hash<false><<<grid, kHashWarps * 32, smem, st>>>(ix->geo, sm, offs, cols, n, id0, bkt, ldb, codes,
-                                                       nullptr, ix->err);
-  SLASH_CK(cudaGetLastError());
-  return SLASH_OK;
+  return launch_hash(ix->geo, shard_map(ix), offs, cols, n, id0, bkt, ldb, codes, count ? ix->cnt : nullptr,
+                     ix->err, st);
 }
 
 // One chunk of Algorithm 1: addresses + counts, staging plan, filtered
@@ -1551,6 +1475,7 @@ const char* slash_strerror(int code) {
     case SLASH_EBUSY: return "admission refused";
     case SLASH_ETIMEOUT: return "bounded device wait timed out";
     case SLASH_EDATA: return "invalid input data seen on the device";
+    case SLASH_EIO: return "checkpoint file error";
     default: return "unknown error";
   }
 }
@@ -1571,14 +1496,7 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
   g.dim = p->dim; g.K = p->K; g.L = p->L; g.nb = p->K * p->L; g.nw = (g.nb + 31) / 32;
   g.B = p->log2_buckets; g.R = p->reservoir; g.d = p->cm_rows; g.w = p->cm_width; g.S = p->shards;
   g.capacity = p->capacity;
-  uint64_t s = p->seed;
-  g.a = (uint32_t)(splitmix64_next(&s) >> 32);
-  g.dirseed = (uint32_t)(splitmix64_next(&s) >> 32);
-  for (uint32_t t = 0; t < p->L; ++t) g.st[t] = (uint32_t)(splitmix64_next(&s) >> 32);
-  for (uint32_t t = 0; t < p->L; ++t) g.sp[t] = (uint32_t)(splitmix64_next(&s) >> 32);
-  for (uint32_t r = 0; r < p->cm_rows; ++r) g.sc[r] = (uint32_t)(splitmix64_next(&s) >> 32);
-  for (uint32_t j = 0; j < g.nb; ++j)
-    if (mix32(j ^ g.dirseed) & 1u) g.dirbits[j >> 5] |= 1u << (j & 31u);
+  derive_seeds(g, p->seed, p->cm_rows);
   ix->nk = ((uint64_t)p->shards * p->L) << p->log2_buckets;
   if (const char* env = std::getenv("SLASH_FILTER_SIGMA")) {
     const double v = std::atof(env);
@@ -1597,10 +1515,12 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
     const uint32_t rb = 32u - p->log2_buckets;
     ix->geo.rbits = (rb < 32u && (double)(1ull << rb) > 1.5 * mu + 1.0) ? rb : 0u;
   }
-  ix->qdef.threads = default_query_threads(*p);
   {
-    const QueryLayout l = make_query_layout(*p);
+    const QueryLayout l = make_query_layout(*p, 256u);  // the smallest CTA must fit
     if (l.bytes > ix->smem_optin || hash_smem(ix) > ix->smem_optin) { delete ix; return SLASH_EINVAL; }
+    uint32_t t = default_query_threads(*p);
+    while (t > 256u && make_query_layout(*p, t).bytes > ix->smem_optin) t >>= 1;
+    ix->qdef.threads = t;
   }
   const uint64_t nblk = (ix->nk + kScanTile - 1) / kScanTile;
   cudaError_t e = cudaSuccess;
@@ -1632,13 +1552,7 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
   cudaFuncSetAttribute(k_query_fused<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_query_fused<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_merge_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ix->smem_optin);
-  cudaFuncSetAttribute(k_hash<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ix->smem_optin);
-#define SLASH_HATTR(CC, KK)                                                                              \
-  cudaFuncSetAttribute(k_hash_reg<CC, KK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);    \
-  cudaFuncSetAttribute(k_hash_reg<CC, KK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
-  SLASH_HATTR(12, 6) SLASH_HATTR(12, 4) SLASH_HATTR(8, 8) SLASH_HATTR(8, 4) SLASH_HATTR(4, 4) SLASH_HATTR(16, 8)
-#undef SLASH_HATTR
-  cudaFuncSetAttribute(k_hash<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ix->smem_optin);
+  init_hash_kernels(so);
   *out = ix;
   return SLASH_OK;
 }
@@ -1758,7 +1672,8 @@ int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
   if (n_queries == 0) return SLASH_OK;
   if (!d_offs || !d_cols || !d_ids_out || !d_scores_out) return SLASH_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  const QueryLayout lay = make_query_layout(ix->p);
+  const QueryLayout lay = make_query_layout(ix->p, thr);
+  if (lay.bytes > ix->smem_optin) return SLASH_EINVAL;
   const void* fn = nullptr;
   if (o.mode == SLASH_QUERY_PLAIN)
     fn = thr == 256 ? (const void*)k_query<256> : thr == 512 ? (const void*)k_query<512> : (const void*)k_query<1024>;
@@ -1903,6 +1818,47 @@ int slash_reset(slash_index* ix, void* cuda_stream) {
 
 uint64_t slash_size(const slash_index* ix) { return ix ? ix->next_id : 0; }
 
+static_assert(sizeof(slash_params) == sizeof(uint32_t) * 12, "checkpoint header holds 12 parameter words");
+
+int slash_save(slash_index* ix, const char* path) {
+  if (!ix || !path) return SLASH_EINVAL;
+  CkptHeader hdr{};
+  hdr.kind = kCkptReservoir;
+  std::memcpy(hdr.params, &ix->p, sizeof(slash_params));
+  hdr.next_id = ix->next_id;
+  const DevSpan spans[2] = {{ix->fill, sizeof(uint32_t) * ix->nk},
+                            {ix->slots, sizeof(uint32_t) * ix->nk * ix->p.reservoir}};
+  return ckpt_save(path, hdr, spans, 2);
+}
+
+int slash_get_params(const slash_index* ix, slash_params* out) {
+  if (!ix || !out) return SLASH_EINVAL;
+  *out = ix->p;
+  return SLASH_OK;
+}
+
+int slash_load(const char* path, void* cuda_stream, slash_index** out) {
+  if (!path || !out) return SLASH_EINVAL;
+  *out = nullptr;
+  CkptHeader hdr{};
+  FILE* f = nullptr;
+  int rc = ckpt_open(path, kCkptReservoir, &hdr, &f);
+  if (rc) return rc;
+  slash_params p{};
+  std::memcpy(&p, hdr.params, sizeof p);
+  if (!params_ok(&p) || hdr.next_id > p.capacity) { std::fclose(f); return SLASH_EINVAL; }
+  slash_index* ix = nullptr;
+  rc = slash_build_index(&p, cuda_stream, &ix);
+  if (rc) { std::fclose(f); return rc; }
+  const DevSpan spans[2] = {{ix->fill, sizeof(uint32_t) * ix->nk},
+                            {ix->slots, sizeof(uint32_t) * ix->nk * p.reservoir}};
+  rc = ckpt_load(f, hdr, spans, 2);
+  if (rc) { slash_free(ix); return rc; }
+  ix->next_id = hdr.next_id;
+  *out = ix;
+  return SLASH_OK;
+}
+
 int slash_profile(slash_index* ix, int enable) {
   if (!ix) return SLASH_EINVAL;
   SLASH_CK(cudaDeviceSynchronize());
@@ -2026,7 +1982,8 @@ extern "C" int slash_query_static(slash_index* ix, const uint64_t* d_offs, const
   int rc = static_scratch(cur, &qbkt);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  const QueryLayout lay = make_query_layout(ix->p);
+  const QueryLayout lay = make_query_layout(ix->p, 512u);
+  if (lay.bytes > ix->smem_optin) return SLASH_EINVAL;
   int bps = 0;
   SLASH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_query<512>, 512, lay.bytes));
   if (bps < 1) return SLASH_EINVAL;

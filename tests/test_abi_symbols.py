@@ -6,18 +6,22 @@ import re
 import subprocess
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "slash.h")
+INCLUDE = os.path.join(ROOT, "include")
 
 
 def _declared():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(slash_[a-z_0-9]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(INCLUDE)):
+        if h.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(INCLUDE, h)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(slash_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_four_calls():
     names = _declared()
-    for n in ("slash_build_index", "slash_insert", "slash_query", "slash_free"):
+    for n in ("slash_build_index", "slash_insert", "slash_query", "slash_free",
+              "slash_tk_build", "slash_tk_insert", "slash_tk_query", "slash_tk_free"):
         assert n in names
 
 
@@ -51,3 +55,18 @@ def test_build_index_rejects_bad_params_without_touching_the_gpu():
         rc = s._lib.slash_build_index(ctypes.byref(p.c()), None, ctypes.byref(h))
         assert rc == s.SLASH_EINVAL, b
         assert h.value is None
+
+
+def test_checkpoint_file_errors_without_gpu(tmp_path):
+    """slash_load checks the file before it touches a device."""
+    from paper_2008_03260_b300 import build
+    lib = ctypes.CDLL(build.build())
+    out = ctypes.c_void_p()
+    missing = str(tmp_path / "missing.ix").encode()
+    assert lib.slash_load(missing, None, ctypes.byref(out)) == -8       # SLASH_EIO
+    assert lib.slash_tk_load(missing, None, ctypes.byref(out)) == -8
+    junk = tmp_path / "junk.ix"
+    junk.write_bytes(b"NOTSLASH" + b"\0" * 200)
+    assert lib.slash_load(str(junk).encode(), None, ctypes.byref(out)) == -1   # SLASH_EINVAL
+    assert lib.slash_tk_load(str(junk).encode(), None, ctypes.byref(out)) == -1
+    assert out.value is None

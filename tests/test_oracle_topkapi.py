@@ -90,3 +90,19 @@ def test_sketch_index_shape_and_recall():
     ids, sc = ix.query(qo, qc, 10)
     assert np.mean([src[i] in ids[i] for i in range(300)]) > 0.85
     assert np.all(sc[:, 0] >= 1)
+
+
+def test_threshold_filters_by_score():
+    g = datagen.Generator()
+    n = 3000
+    offs, cols = g.rows(0, 0, n)
+    ix = oracle.TkIndex(K=2, L=16, log2_buckets=8, rows=2, cells=16, capacity=n)
+    ix.insert(offs, cols)
+    qo, qc, _ = g.queries(0, 1, 100, n, p_perturb=0.1)
+    ids0, sc0 = ix.query(qo, qc, 20)
+    ids2, sc2 = ix.query(qo, qc, 20, threshold=2)
+    for i in range(100):
+        keep = [(a, b) for a, b in zip(ids0[i], sc0[i]) if a >= 0 and b > 2]
+        got = [(a, b) for a, b in zip(ids2[i], sc2[i]) if a >= 0]
+        assert got == keep
+        assert np.all(ids2[i][len(got):] == -1) and np.all(sc2[i][len(got):] == 0)
