@@ -53,6 +53,8 @@ def _load():
             lib.or_minhash.restype = u32
             lib.or_minhash.argtypes = [vp, u64, u32]
             lib.or_doph.argtypes = [vp, u64, u32, u32, u32, vp, vp]
+            lib.or_doph_opt.argtypes = [vp, u64, u32, u32, u32, u32, vp, vp]
+            lib.or_seeds_init.argtypes = [u64, u32, u32, u32, vp]
             lib.or_table_address.restype = u32
             lib.or_table_address.argtypes = [vp, u32, u32, u32, u32]
             lib.or_mix31.restype = u32
@@ -61,11 +63,11 @@ def _load():
             lib.or_priority.argtypes = [u32, u32]
             lib.or_cm_cell.restype = u32
             lib.or_cm_cell.argtypes = [u32, u32, u32]
-            lib.or_hash_rows.argtypes = [u32, u32, u32, vp, vp, vp, u64, vp, vp]
+            lib.or_hash_rows.argtypes = [u32, u32, u32, u32, vp, vp, vp, u64, vp, vp]
             lib.or_new.restype = vp
-            lib.or_new.argtypes = [u32, u32, u32, u32, u32, u32, u32, u64, u64]
+            lib.or_new.argtypes = [u32, u32, u32, u32, u32, u32, u32, u64, u64, u32]
             lib.or_new_partial.restype = vp
-            lib.or_new_partial.argtypes = [u32, u32, u32, u32, u32, u32, u32, u64, u64, vp, vp, u64]
+            lib.or_new_partial.argtypes = [u32, u32, u32, u32, u32, u32, u32, u64, u64, vp, vp, u64, u32]
             lib.or_free.argtypes = [vp]
             lib.or_seeds.restype = ctypes.POINTER(u32)
             lib.or_seeds.argtypes = [vp]
@@ -87,7 +89,7 @@ def _load():
             lib.or_tk_update.argtypes = [ctypes.POINTER(u32), ctypes.POINTER(u32), u32]
             lib.or_tk_merge_cell.argtypes = [ctypes.POINTER(u32), ctypes.POINTER(u32), u32, u32]
             lib.or_tk_new.restype = vp
-            lib.or_tk_new.argtypes = [u32, u32, u32, u32, u32, u32, u64, u64]
+            lib.or_tk_new.argtypes = [u32, u32, u32, u32, u32, u32, u64, u64, u32]
             lib.or_tk_free.argtypes = [vp]
             lib.or_tk_insert.restype = i32
             lib.or_tk_insert.argtypes = [vp, vp, vp, u64, ctypes.POINTER(u64)]
@@ -142,6 +144,22 @@ def doph(cols, nb: int, a: int, dirseed: int) -> tuple[np.ndarray, np.ndarray]:
     return codes, mask.astype(bool)
 
 
+def doph_opt(cols, nb: int, a: int, od: int, dirseed: int) -> tuple[np.ndarray, np.ndarray]:
+    """DOPH with optimal densification: codes[nb] and the non-empty mask[nb]."""
+    c = _u32(cols)
+    codes = np.empty(nb, dtype=np.uint32)
+    mask = np.empty(nb, dtype=np.uint8)
+    _load().or_doph_opt(_p(c), c.size, nb, a, od, dirseed, _p(codes), _p(mask))
+    return codes, mask.astype(bool)
+
+
+def seeds_init(seed: int, L: int, d: int, densify: int = 0) -> np.ndarray:
+    """The index's seed words: derive_seeds' words, od, the densification mode."""
+    out = np.empty(2 + 2 * L + d + 2, dtype=np.uint32)
+    _load().or_seeds_init(seed, L, d, densify, _p(out))
+    return out
+
+
 def table_address(codes, t: int, K: int, B: int, st_t: int) -> int:
     c = _u32(codes)
     return int(_load().or_table_address(_p(c), t, K, B, st_t))
@@ -159,14 +177,15 @@ def cm_cell(id_: int, sc_r: int, w: int) -> int:
     return int(_load().or_cm_cell(id_, sc_r, w))
 
 
-def hash_rows(K: int, L: int, B: int, seed: int, d: int, offs, cols, want_codes: bool = True):
+def hash_rows(K: int, L: int, B: int, seed: int, d: int, offs, cols, want_codes: bool = True,
+              densify: int = 0):
     """Codes [n][K*L] (or None) and table addresses [n][L] for CSR rows."""
     offs, cols = _u64(offs), _u32(cols)
     n = offs.size - 1
-    s = derive_seeds(seed, L, d)["raw"]
+    s = seeds_init(seed, L, d, densify)
     codes = np.empty((n, K * L), dtype=np.uint32) if want_codes else None
     bk = np.empty((n, L), dtype=np.uint32)
-    _load().or_hash_rows(K, L, B, _p(s), _p(offs), _p(cols), n, _p(codes), _p(bk))
+    _load().or_hash_rows(K, L, B, d, _p(s), _p(offs), _p(cols), n, _p(codes), _p(bk))
     return codes, bk
 
 
@@ -176,17 +195,18 @@ class Index:
     listed buckets (bounded memory for full-size sampled checks)."""
 
     def __init__(self, *, K: int, L: int, log2_buckets: int, reservoir: int, cm_rows: int,
-                 cm_width: int, shards: int = 1, seed: int = 0, capacity: int, partial=None):
+                 cm_width: int, shards: int = 1, seed: int = 0, capacity: int, partial=None,
+                 densify: int = 0):
         self._lib = _load()
         self.K, self.L, self.B, self.R = K, L, log2_buckets, reservoir
         self.d, self.w, self.S, self.capacity = cm_rows, cm_width, shards, capacity
         if partial is None:
             self._h = self._lib.or_new(K, L, log2_buckets, reservoir, cm_rows, cm_width, shards,
-                                       seed, capacity)
+                                       seed, capacity, densify)
         else:
             rt, rb = _u32(partial[0]), _u32(partial[1])
             self._h = self._lib.or_new_partial(K, L, log2_buckets, reservoir, cm_rows, cm_width,
-                                               shards, seed, capacity, _p(rt), _p(rb), rt.size)
+                                               shards, seed, capacity, _p(rt), _p(rb), rt.size, densify)
         if not self._h:
             raise MemoryError("oracle index allocation failed")
         self.partial = partial is not None
@@ -279,10 +299,10 @@ class TkIndex:
     """Oracle index whose buckets are TopKAPI sketches of W rows x C cells."""
 
     def __init__(self, *, K: int, L: int, log2_buckets: int, rows: int, cells: int, shards: int = 1,
-                 seed: int = 0, capacity: int):
+                 seed: int = 0, capacity: int, densify: int = 0):
         self._lib = _load()
         self.K, self.L, self.B, self.W, self.C, self.S = K, L, log2_buckets, rows, cells, shards
-        self._h = self._lib.or_tk_new(K, L, log2_buckets, rows, cells, shards, seed, capacity)
+        self._h = self._lib.or_tk_new(K, L, log2_buckets, rows, cells, shards, seed, capacity, densify)
         if not self._h:
             raise MemoryError("oracle sketch allocation failed")
 

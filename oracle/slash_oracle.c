@@ -78,6 +78,16 @@ void or_derive_seeds(uint64_t seed, uint32_t L, uint32_t d, uint32_t *out) {
   for (uint32_t i = 0; i < n; ++i) out[i] = (uint32_t)(or_splitmix64_next(&s) >> 32);
 }
 
+/* out = the or_derive_seeds words, then od (the next SplitMix64 word: the
+ * probe seed of optimal densification) and the densification mode:
+ * 2 + 2L + d + 2 words in all. */
+void or_seeds_init(uint64_t seed, uint32_t L, uint32_t d, uint32_t densify, uint32_t *out) {
+  uint64_t s = seed;
+  uint32_t n = 2 + 2 * L + d;
+  for (uint32_t i = 0; i <= n; ++i) out[i] = (uint32_t)(or_splitmix64_next(&s) >> 32);
+  out[n + 1] = densify;
+}
+
 /* MinHash of a binary vector under the seeded hash: min over its features (Sec. 2.2).
  * Returns OR_EMPTY for an empty vector. */
 uint32_t or_minhash(const uint32_t *cols, uint64_t nnz, uint32_t a) {
@@ -121,6 +131,44 @@ void or_doph(const uint32_t *cols, uint64_t nnz, uint32_t nb, uint32_t a, uint32
   free(full);
 }
 
+/* Densified one-permutation hashing with optimal densification (Shrivastava,
+ * ICML 2017 -- the densified variant Sec. 6 says SLASH implements): the bins
+ * are filled as in or_doph; an empty bin j then probes the bins
+ *   p_a(j) = (mix32(mix32(j ^ od) + a) * nb) >> 32,  a = 1, 2, ...
+ * and copies the value of the first non-empty one.  The probe sequence depends
+ * on j and the seed only, never on the row.  After OR_OPT_PROBES(nb) probes
+ * without success the bin takes the side rule of or_doph instead (dirseed). */
+#define OR_OPT_PROBES(nb) (32u * (nb))
+
+void or_doph_opt(const uint32_t *cols, uint64_t nnz, uint32_t nb, uint32_t a, uint32_t od, uint32_t dirseed,
+                 uint32_t *codes, uint8_t *nonempty) {
+  uint8_t *full = (uint8_t *)malloc(nb);
+  uint32_t *side = (uint32_t *)malloc(sizeof(uint32_t) * nb);
+  or_doph(cols, nnz, nb, a, dirseed, side, full);  /* bins + the side rule's codes */
+  int any = 0;
+  for (uint32_t j = 0; j < nb; ++j) any |= full[j];
+  for (uint32_t j = 0; j < nb; ++j) {
+    if (full[j] || !any) { codes[j] = side[j]; continue; }
+    uint32_t base = or_mix32(j ^ od), found = 0;
+    for (uint32_t t = 1; t <= OR_OPT_PROBES(nb) && !found; ++t) {
+      uint32_t p = (uint32_t)(((uint64_t)or_mix32(base + t) * nb) >> 32);
+      if (full[p]) { codes[j] = side[p]; found = 1; }  /* a non-empty bin keeps its own value */
+    }
+    if (!found) codes[j] = side[j];
+  }
+  if (nonempty) memcpy(nonempty, full, nb);
+  free(full);
+  free(side);
+}
+
+/* The index's DOPH: seeds as written by or_seeds_init for L tables, d rows. */
+static void or_doph_seeded(const uint32_t *cols, uint64_t nnz, uint32_t nb, const uint32_t *seeds, uint32_t L,
+                           uint32_t d, uint32_t *codes) {
+  uint32_t od = seeds[2 + 2 * L + d], densify = seeds[2 + 2 * L + d + 1];
+  if (densify) or_doph_opt(cols, nnz, nb, seeds[0], od, seeds[1], codes, NULL);
+  else or_doph(cols, nnz, nb, seeds[0], seeds[1], codes, NULL);
+}
+
 /* H_t: the K codes of table t -> one of 2^B addresses (Sec. 2.3). */
 uint32_t or_table_address(const uint32_t *codes, uint32_t t, uint32_t K, uint32_t B, uint32_t st_t) {
   uint32_t acc = st_t;
@@ -145,13 +193,13 @@ uint32_t or_priority(uint32_t id, uint32_t sp_t) { return or_mix31(id ^ sp_t); }
 uint32_t or_cm_cell(uint32_t id, uint32_t sc_r, uint32_t w) { return or_mix32(id ^ sc_r) & (w - 1); }
 
 /* per-row DOPH codes (optional, [n][K*L]) and table addresses ([n][L]) */
-void or_hash_rows(uint32_t K, uint32_t L, uint32_t B, const uint32_t *seeds, const uint64_t *offs,
+void or_hash_rows(uint32_t K, uint32_t L, uint32_t B, uint32_t d, const uint32_t *seeds, const uint64_t *offs,
                   const uint32_t *cols, uint64_t n, uint32_t *codes_out, uint32_t *buckets_out) {
   uint32_t nb = K * L;
   const uint32_t *st = seeds + 2;
   uint32_t *codes = (uint32_t *)malloc(sizeof(uint32_t) * nb);
   for (uint64_t i = 0; i < n; ++i) {
-    or_doph(cols + (offs[i] - offs[0]), offs[i + 1] - offs[i], nb, seeds[0], seeds[1], codes, NULL);
+    or_doph_seeded(cols + (offs[i] - offs[0]), offs[i + 1] - offs[i], nb, seeds, L, d, codes);
     if (codes_out) memcpy(codes_out + i * nb, codes, sizeof(uint32_t) * nb);
     for (uint32_t t = 0; t < L; ++t) buckets_out[i * L + t] = or_table_address(codes, t, K, B, st[t]);
   }
@@ -163,7 +211,7 @@ void or_hash_rows(uint32_t K, uint32_t L, uint32_t B, const uint32_t *seeds, con
 typedef struct {
   uint32_t K, L, B, R, d, w, S;
   uint64_t capacity, next_id;
-  uint32_t *seeds;      /* 2 + 2L + d */
+  uint32_t *seeds;      /* or_seeds_init: 2 + 2L + d + 2 */
   /* per shard s: bucket (t, b) lives at storage row map[t*2^B + b] (dense: identity) */
   int64_t *map;         /* NULL = dense */
   uint64_t nstore;      /* materialised buckets per shard */
@@ -178,12 +226,12 @@ static uint64_t or_loc(const or_index *ix, uint32_t t, uint32_t b) {
 
 /* dense index (all L * 2^B buckets per shard; calloc keeps untouched pages free) */
 void *or_new(uint32_t K, uint32_t L, uint32_t B, uint32_t R, uint32_t d, uint32_t w, uint32_t S,
-             uint64_t seed, uint64_t capacity) {
+             uint64_t seed, uint64_t capacity, uint32_t densify) {
   or_index *ix = (or_index *)calloc(1, sizeof(or_index));
   ix->K = K; ix->L = L; ix->B = B; ix->R = R; ix->d = d; ix->w = w; ix->S = S;
   ix->capacity = capacity;
-  ix->seeds = (uint32_t *)malloc(sizeof(uint32_t) * (2 + 2 * L + d));
-  or_derive_seeds(seed, L, d, ix->seeds);
+  ix->seeds = (uint32_t *)malloc(sizeof(uint32_t) * (2 + 2 * L + d + 2));
+  or_seeds_init(seed, L, d, densify, ix->seeds);
   ix->nstore = (uint64_t)L << B;
   ix->slots = (uint32_t *)calloc(ix->nstore * S * R, sizeof(uint32_t));
   ix->fill = (uint32_t *)calloc(ix->nstore * S, sizeof(uint32_t));
@@ -195,12 +243,12 @@ void *or_new(uint32_t K, uint32_t L, uint32_t B, uint32_t R, uint32_t d, uint32_
  * buckets are dropped and queries must only touch listed buckets */
 void *or_new_partial(uint32_t K, uint32_t L, uint32_t B, uint32_t R, uint32_t d, uint32_t w, uint32_t S,
                      uint64_t seed, uint64_t capacity, const uint32_t *req_t, const uint32_t *req_b,
-                     uint64_t nreq) {
+                     uint64_t nreq, uint32_t densify) {
   or_index *ix = (or_index *)calloc(1, sizeof(or_index));
   ix->K = K; ix->L = L; ix->B = B; ix->R = R; ix->d = d; ix->w = w; ix->S = S;
   ix->capacity = capacity;
-  ix->seeds = (uint32_t *)malloc(sizeof(uint32_t) * (2 + 2 * L + d));
-  or_derive_seeds(seed, L, d, ix->seeds);
+  ix->seeds = (uint32_t *)malloc(sizeof(uint32_t) * (2 + 2 * L + d + 2));
+  or_seeds_init(seed, L, d, densify, ix->seeds);
   uint64_t nkeys = (uint64_t)L << B;
   ix->map = (int64_t *)malloc(sizeof(int64_t) * nkeys);
   for (uint64_t k = 0; k < nkeys; ++k) ix->map[k] = -1;
@@ -251,7 +299,7 @@ int or_insert(void *p, const uint64_t *offs, const uint32_t *cols, uint64_t n, u
   for (uint64_t i = 0; i < n; ++i) {
     uint64_t id = ix->next_id++;
     uint32_t s = or_shard_of(ix, id);
-    or_doph(cols + (offs[i] - offs[0]), offs[i + 1] - offs[i], nb, ix->seeds[0], ix->seeds[1], codes, NULL);
+    or_doph_seeded(cols + (offs[i] - offs[0]), offs[i + 1] - offs[i], nb, ix->seeds, ix->L, ix->d, codes);
     for (uint32_t t = 0; t < ix->L; ++t) {
       uint32_t b = or_table_address(codes, t, ix->K, ix->B, st[t]);
       if (ix->map && ix->map[((uint64_t)t << ix->B) + b] < 0) continue;
@@ -282,8 +330,8 @@ static void *or_pinsert_run(void *a) {
   for (uint64_t i = j->b; i < j->e; ++i) {
     uint64_t id = j->id0 + i;
     uint32_t s = or_shard_of(ix, id);
-    or_doph(j->cols + (j->offs[i] - j->offs[0]), j->offs[i + 1] - j->offs[i], nb, ix->seeds[0],
-            ix->seeds[1], codes, NULL);
+    or_doph_seeded(j->cols + (j->offs[i] - j->offs[0]), j->offs[i + 1] - j->offs[i], nb, ix->seeds, ix->L,
+                   ix->d, codes);
     for (uint32_t t = 0; t < ix->L; ++t) {
       uint32_t b = or_table_address(codes, t, ix->K, ix->B, st[t]);
       if (ix->map[((uint64_t)t << ix->B) + b] < 0) continue;
@@ -392,7 +440,7 @@ int or_query_one(const void *p, const uint32_t *cols, uint64_t nnz, uint32_t k, 
   uint32_t *codes = (uint32_t *)malloc(sizeof(uint32_t) * nb);
   uint32_t *addr = (uint32_t *)malloc(sizeof(uint32_t) * L);
   /* Algorithm 2, hashing: the query's address in every table */
-  or_doph(cols, nnz, nb, ix->seeds[0], ix->seeds[1], codes, NULL);
+  or_doph_seeded(cols, nnz, nb, ix->seeds, ix->L, ix->d, codes);
   for (uint32_t t = 0; t < L; ++t) {
     addr[t] = or_table_address(codes, t, K, ix->B, st[t]);
     if (ix->map && ix->map[((uint64_t)t << ix->B) + addr[t]] < 0) { free(codes); free(addr); return -1; }
@@ -488,7 +536,7 @@ uint64_t or_next_id(const void *p) { return ((const or_index *)p)->next_id; }
 typedef struct {
   uint32_t K, L, B, W, C, S;
   uint64_t capacity, next_id;
-  uint32_t *seeds;       /* 2 + 2L + W */
+  uint32_t *seeds;       /* or_seeds_init: 2 + 2L + W + 2 */
   uint32_t *hh, *cnt;    /* [S][L][2^B][W][C] */
 } or_tk;
 
@@ -507,11 +555,11 @@ void or_tk_merge_cell(uint32_t *hh, uint32_t *cnt, uint32_t bh, uint32_t bc) {
 }
 
 void *or_tk_new(uint32_t K, uint32_t L, uint32_t B, uint32_t W, uint32_t C, uint32_t S, uint64_t seed,
-                uint64_t capacity) {
+                uint64_t capacity, uint32_t densify) {
   or_tk *ix = (or_tk *)calloc(1, sizeof(or_tk));
   ix->K = K; ix->L = L; ix->B = B; ix->W = W; ix->C = C; ix->S = S; ix->capacity = capacity;
-  ix->seeds = (uint32_t *)malloc(sizeof(uint32_t) * (2 + 2 * L + W));
-  or_derive_seeds(seed, L, W, ix->seeds);
+  ix->seeds = (uint32_t *)malloc(sizeof(uint32_t) * (2 + 2 * L + W + 2));
+  or_seeds_init(seed, L, W, densify, ix->seeds);
   uint64_t n = ((uint64_t)S * L << B) * W * C;
   ix->hh = (uint32_t *)calloc(n, sizeof(uint32_t));
   ix->cnt = (uint32_t *)calloc(n, sizeof(uint32_t));
@@ -536,7 +584,7 @@ int or_tk_insert(void *p, const uint64_t *offs, const uint32_t *cols, uint64_t n
   for (uint64_t i = 0; i < n; ++i) {
     uint64_t id = ix->next_id++;
     uint32_t s = (uint32_t)(((unsigned __int128)id * ix->S) / ix->capacity);
-    or_doph(cols + (offs[i] - offs[0]), offs[i + 1] - offs[i], nb, ix->seeds[0], ix->seeds[1], codes, NULL);
+    or_doph_seeded(cols + (offs[i] - offs[0]), offs[i + 1] - offs[i], nb, ix->seeds, ix->L, ix->W, codes);
     for (uint32_t t = 0; t < ix->L; ++t) {
       uint32_t b = or_table_address(codes, t, ix->K, ix->B, st[t]);
       uint64_t base = ((((uint64_t)s * ix->L + t) << ix->B) + b) * ix->W * ix->C;
@@ -571,7 +619,7 @@ int or_tk_query(const void *p, const uint64_t *offs, const uint32_t *cols, uint6
   uint32_t *mh = (uint32_t *)malloc(sizeof(uint32_t) * WC), *mc = (uint32_t *)malloc(sizeof(uint32_t) * WC);
   or_cand *cand = (or_cand *)malloc(sizeof(or_cand) * (WC + 1));
   for (uint64_t q = 0; q < nq; ++q) {
-    or_doph(cols + (offs[q] - offs[0]), offs[q + 1] - offs[q], nb, ix->seeds[0], ix->seeds[1], codes, NULL);
+    or_doph_seeded(cols + (offs[q] - offs[0]), offs[q + 1] - offs[q], nb, ix->seeds, ix->L, ix->W, codes);
     for (uint32_t c = 0; c < WC; ++c) { mh[c] = OR_EMPTY; mc[c] = 0; }
     for (uint32_t s = 0; s < ix->S; ++s)
       for (uint32_t t = 0; t < ix->L; ++t) {
