@@ -18,8 +18,8 @@ per row, power-law feature popularity), reduced to what one device holds:
              32 cells (512 B per bucket, the size of an R=128 reservoir;
              ~8.6 GB), top-10
   sweep      quality sweep of Sec. 6 (K = 4; L = 16, 24, 32): 1M rows, 2^16
-             buckets, R=32 or TopKAPI 4x8 (same bytes), 10k planted queries
-             (20% resampled), S@1 and S@64
+             buckets, R=32 (side-rule or optimal densification) or TopKAPI
+             4x8 (same bytes), 10k planted queries (20% resampled), S@1, S@64
 """
 from __future__ import annotations
 

@@ -81,7 +81,20 @@ typedef struct {
   uint32_t shards;        /* S: on-device partitions (1 = single index)            */
   uint64_t seed;          /* the shared random seed                                */
   uint64_t capacity;      /* max ids ever inserted (1..2^31-1; ids are int32)      */
+  uint32_t densify;       /* DOPH densification: SLASH_DENSIFY_SIDE or _OPTIMAL    */
+  uint32_t reserved;      /* must be 0                                             */
 } slash_params;
+
+/* Densification rules for the empty DOPH bins (Sec. 2.2).  SIDE: the nearest
+ * non-empty bin on a fixed per-bin side (left or right), circularly.  OPTIMAL:
+ * optimal densification (Shrivastava, ICML 2017; the densified variant Sec. 6
+ * says SLASH implements): empty bin j copies the first non-empty bin of the
+ * probe sequence umulhi(mix32(mix32(j ^ od) + a), K*L), a = 1, 2, ..., with od
+ * the seed word drawn after the count-min (or sketch-row) seeds; after
+ * 32*K*L probes without a non-empty bin the SIDE rule decides.  Lower-variance
+ * codes for sparse rows, at roughly K*L / (non-empty bins) probes per empty bin. */
+#define SLASH_DENSIFY_SIDE    0u
+#define SLASH_DENSIFY_OPTIMAL 1u
 
 /* Allocate and clear an index on the current CUDA device: buckets
  * uint32 [S][L][2^B][R] (SLASH_EMPTY) and fill counts uint32 [S][L][2^B] (0).

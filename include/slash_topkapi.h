@@ -53,7 +53,7 @@ typedef struct {
   uint32_t rows;          /* W: sketch rows (1..SLASH_TK_MAX_ROWS)                     */
   uint32_t cells;         /* C: cells per row, a power of two; W*C <= SLASH_TK_MAX_CELLS */
   uint32_t shards;        /* S: on-device partitions (1 = single index)                */
-  uint32_t reserved;      /* must be 0                                                 */
+  uint32_t densify;       /* SLASH_DENSIFY_SIDE or SLASH_DENSIFY_OPTIMAL (slash.h)     */
   uint64_t seed;          /* the shared random seed                                    */
   uint64_t capacity;      /* max ids ever inserted (1..2^31-1; ids are int32)          */
 } slash_tk_params;

@@ -35,6 +35,8 @@ SLASH_EBUSY = -5
 SLASH_ETIMEOUT = -6
 SLASH_EDATA = -7
 SLASH_EIO = -8
+SLASH_DENSIFY_SIDE = 0
+SLASH_DENSIFY_OPTIMAL = 1
 SLASH_EMPTY = 0xFFFFFFFF
 SLASH_MAX_TOPK = 256
 
@@ -62,13 +64,13 @@ class slash_params(ctypes.Structure):
                 ("log2_buckets", ctypes.c_uint32), ("reservoir", ctypes.c_uint32),
                 ("cm_rows", ctypes.c_uint32), ("cm_width", ctypes.c_uint32),
                 ("shards", ctypes.c_uint32), ("seed", ctypes.c_uint64),
-                ("capacity", ctypes.c_uint64)]
+                ("capacity", ctypes.c_uint64), ("densify", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class slash_tk_params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_uint32), ("K", ctypes.c_uint32), ("L", ctypes.c_uint32),
                 ("log2_buckets", ctypes.c_uint32), ("rows", ctypes.c_uint32), ("cells", ctypes.c_uint32),
-                ("shards", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("shards", ctypes.c_uint32), ("densify", ctypes.c_uint32), ("seed", ctypes.c_uint64),
                 ("capacity", ctypes.c_uint64)]
 
 
@@ -162,10 +164,12 @@ class Params:
     shards: int = 1
     seed: int = 0
     capacity: int = 100_000
+    densify: int = 0  # SLASH_DENSIFY_SIDE (0) or SLASH_DENSIFY_OPTIMAL (1)
 
     def c(self) -> slash_params:
         return slash_params(self.dim, self.K, self.L, self.log2_buckets, self.reservoir,
-                            self.cm_rows, self.cm_width, self.shards, self.seed, self.capacity)
+                            self.cm_rows, self.cm_width, self.shards, self.seed, self.capacity,
+                            self.densify, 0)
 
     @property
     def index_bytes(self) -> int:
@@ -344,7 +348,7 @@ def slash_load(path: str, stream=None) -> int:
 def slash_get_params(ix: int) -> Params:
     cp = slash_params()
     _check(_lib.slash_get_params(ix, ctypes.byref(cp)), "slash_get_params")
-    return Params(**{f: getattr(cp, f) for f, _ in slash_params._fields_})
+    return Params(**{f: getattr(cp, f) for f, _ in slash_params._fields_ if f != "reserved"})
 
 
 class Index:
@@ -434,10 +438,11 @@ class TkParams:
     shards: int = 1
     seed: int = 0
     capacity: int = 100_000
+    densify: int = 0  # SLASH_DENSIFY_SIDE (0) or SLASH_DENSIFY_OPTIMAL (1)
 
     def c(self) -> slash_tk_params:
         return slash_tk_params(self.dim, self.K, self.L, self.log2_buckets, self.rows, self.cells,
-                               self.shards, 0, self.seed, self.capacity)
+                               self.shards, self.densify, self.seed, self.capacity)
 
     @property
     def index_bytes(self) -> int:
@@ -506,7 +511,7 @@ def slash_tk_load(path: str, stream=None) -> int:
 def slash_tk_get_params(ix: int) -> TkParams:
     cp = slash_tk_params()
     _check(_lib.slash_tk_get_params(ix, ctypes.byref(cp)), "slash_tk_get_params")
-    return TkParams(**{f: getattr(cp, f) for f, _ in slash_tk_params._fields_ if f != "reserved"})
+    return TkParams(**{f: getattr(cp, f) for f, _ in slash_tk_params._fields_})
 
 
 class TkIndex:

@@ -1047,9 +1047,14 @@ __device__ void query_core(const Geo& g, const QueryLayout& lay, unsigned char* 
   __syncthreads();
 }
 
+// Resident CTAs the register budget must allow: three 256-thread CTAs per SM
+// (at most 85 registers a thread), one CTA otherwise.
+template <int kThreads>
+constexpr int kQueryMinBlocks = kThreads <= 256 ? 3 : 1;
+
 // Plain path: one CTA per query (grid-stride); addresses from k_hash, qbkt[t*ldq + q].
 template <int kThreads>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, kQueryMinBlocks<kThreads>)
 k_query(const __grid_constant__ Geo g, const QueryLayout lay, const uint32_t* __restrict__ qbkt, uint64_t ldq,
         uint32_t nq, uint32_t k, const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill,
         int32_t* __restrict__ ids_out, uint32_t* __restrict__ scores_out) {
@@ -1069,7 +1074,7 @@ k_query(const __grid_constant__ Geo g, const QueryLayout lay, const uint32_t* __
 // hashed (DOPH, densification, L addresses) by the whole CTA in smem and then
 // answered by query_core -- no intermediate HBM traffic, one launch per batch.
 template <int kThreads>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, kQueryMinBlocks<kThreads>)
 k_query_fused(const __grid_constant__ Geo g, const QueryLayout lay, const uint64_t* __restrict__ offs,
               const uint32_t* __restrict__ cols, uint32_t nq, uint32_t k, const uint32_t* __restrict__ slots,
               const uint32_t* __restrict__ fill, int32_t* __restrict__ ids_out,
@@ -1148,7 +1153,8 @@ int launch_hash(const Geo& g, const ShardMap& sm, const uint64_t* offs, const ui
   const dim3 grid((n + kHashRows - 1) / kHashRows);
   const bool count = cnt != nullptr;
   const uint32_t nb = g.nb, K = g.K;
-  const uint32_t C = nb % 32u == 0u ? nb / 32u : 0u;
+  // register-chunk kernels hold the side rule only
+  const uint32_t C = nb % 32u == 0u && !g.densify ? nb / 32u : 0u;
   const size_t rsmem = sizeof(uint32_t) * ((size_t)kHashWarps * (((nb + 33u) + 3u) & ~3u) +
                                            (size_t)g.L * kHashRows);
 #define SLASH_HREG(CC, KK)                                                                                  \
@@ -1457,6 +1463,7 @@ bool params_ok(const slash_params* p) {
   const uint64_t nk = ((uint64_t)p->shards * p->L) << p->log2_buckets;
   if (nk >= (1ull << 32)) return false;                                    // bucket keys are uint32
   if ((uint64_t)p->shards * p->L * p->reservoir > 0xFFFFull) return false;  // 16-bit sketch counters
+  if (p->densify > SLASH_DENSIFY_OPTIMAL || p->reserved != 0) return false;
   return true;
 }
 
@@ -1497,6 +1504,7 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
   g.B = p->log2_buckets; g.R = p->reservoir; g.d = p->cm_rows; g.w = p->cm_width; g.S = p->shards;
   g.capacity = p->capacity;
   derive_seeds(g, p->seed, p->cm_rows);
+  g.densify = p->densify;
   ix->nk = ((uint64_t)p->shards * p->L) << p->log2_buckets;
   if (const char* env = std::getenv("SLASH_FILTER_SIGMA")) {
     const double v = std::atof(env);
@@ -1818,7 +1826,7 @@ int slash_reset(slash_index* ix, void* cuda_stream) {
 
 uint64_t slash_size(const slash_index* ix) { return ix ? ix->next_id : 0; }
 
-static_assert(sizeof(slash_params) == sizeof(uint32_t) * 12, "checkpoint header holds 12 parameter words");
+static_assert(sizeof(slash_params) <= sizeof(CkptHeader::params), "checkpoint header holds the parameters");
 
 int slash_save(slash_index* ix, const char* path) {
   if (!ix || !path) return SLASH_EINVAL;

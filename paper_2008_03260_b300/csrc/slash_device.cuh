@@ -17,6 +17,7 @@ constexpr uint32_t kGold32 = 0x9E3779B1u;   // odd multiplier of the K-code comb
 constexpr uint32_t kMaxShards = 64;
 constexpr uint32_t kErrCol = 1u;            // a feature id >= dim was skipped
 constexpr uint32_t kErrOffs = 2u;           // a row with d_offs[i+1] < d_offs[i] was read as empty
+constexpr uint32_t kOptProbes = 32u;        // optimal densification: probes per empty bin, times nb
 
 // MurmurHash3 32-bit finaliser (Appleby): a bijection of uint32.
 __host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
@@ -52,6 +53,8 @@ __device__ __forceinline__ uint32_t cm_cell(uint32_t id, uint32_t sc_r, uint32_t
 struct Geo {
   uint32_t dim, K, L, nb, nw, B, R, d, w, S;
   uint32_t rbits;                        // insert addresses carry the pair's rank in 32-B low bits (0: off)
+  uint32_t densify;                      // 0: side rule (Sec. 2.2), 1: optimal densification
+  uint32_t od;                           // optimal densification's probe seed
   uint64_t capacity;
   uint32_t a, dirseed;
   uint32_t st[SLASH_MAX_L];              // table seeds
@@ -139,16 +142,41 @@ __device__ __forceinline__ void doph_densify(const Geo& g, uint32_t* m, const ui
     if (rn == kNone) rn = ro;
     if (ln == kNone) ln = lo2;
   }
-  // branch-free: an empty bin reads the nearest non-empty bin on its side; a
-  // non-empty bin rewrites its own value.  Only non-empty bins are read, and
-  // their values never change, so the update is safe in place.
+  // bins left to the side rule: every empty bin, or with optimal densification
+  // only those whose probe sequence found no non-empty bin
+  uint32_t todo = cnt == 32u ? ~cb : (~cb & ((1u << cnt) - 1u));
+  if (g.densify) {
+    // optimal densification (Shrivastava, ICML 2017): empty bin j probes bins
+    // umulhi(mix32(mix32(j ^ od) + a), nb) for a = 1, 2, ... and copies the
+    // first non-empty one (at most kOptProbes * nb probes)
+    uint32_t left = todo;
+    todo = 0u;
+    while (left) {
+      const uint32_t p = (uint32_t)(__ffs(left) - 1);
+      left &= left - 1u;
+      const uint32_t j = lo + p, base = mix32(j ^ g.od), lim = kOptProbes * g.nb;
+      bool found = false;
+      for (uint32_t a = 1; a <= lim; ++a) {
+        const uint32_t q = __umulhi(mix32(base + a), g.nb);
+        if ((mask[q >> 5] >> (q & 31u)) & 1u) {
+          m[j] = m[q];
+          found = true;
+          break;
+        }
+      }
+      if (!found) todo |= 1u << p;
+    }
+  }
+  // side rule: an empty bin reads the nearest non-empty bin on its side.  Only
+  // non-empty bins are read, and their values never change, so every update
+  // here and above is safe in place.
   for (uint32_t p = 0; p < cnt; ++p) {
+    if (!((todo >> p) & 1u)) continue;
     const uint32_t above = cb & ((0xFFFFFFFEu << p));            // bits > p (p < 32)
     const uint32_t below = cb & ((1u << p) - 1u);                // bits < p
     const uint32_t kr = above ? lo + (uint32_t)(__ffs(above) - 1) : rn;
     const uint32_t kl = below ? lo + 31u - (uint32_t)__clz(below) : ln;
-    const uint32_t k = ((cb >> p) & 1u) ? lo + p : (((db >> p) & 1u) ? kr : kl);
-    m[lo + p] = m[k];
+    m[lo + p] = m[((db >> p) & 1u) ? kr : kl];
   }
   __syncwarp();
 }
@@ -183,7 +211,7 @@ inline uint64_t splitmix64_next(uint64_t* s) {
 
 // Sec. 4 "Initialization": every hash function comes from one shared seed.
 // Sub-seeds are the upper halves of successive SplitMix64 words, drawn in
-// the order a, dirseed, st[L], sp[L], sc[rows]; g.L and g.nb must be set.
+// the order a, dirseed, st[L], sp[L], sc[rows], od; g.L and g.nb must be set.
 inline void derive_seeds(Geo& g, uint64_t seed, uint32_t rows) {
   uint64_t s = seed;
   g.a = (uint32_t)(splitmix64_next(&s) >> 32);
@@ -191,6 +219,7 @@ inline void derive_seeds(Geo& g, uint64_t seed, uint32_t rows) {
   for (uint32_t t = 0; t < g.L; ++t) g.st[t] = (uint32_t)(splitmix64_next(&s) >> 32);
   for (uint32_t t = 0; t < g.L; ++t) g.sp[t] = (uint32_t)(splitmix64_next(&s) >> 32);
   for (uint32_t r = 0; r < rows; ++r) g.sc[r] = (uint32_t)(splitmix64_next(&s) >> 32);
+  g.od = (uint32_t)(splitmix64_next(&s) >> 32);
   for (uint32_t w = 0; w < SLASH_MAX_NB / 32; ++w) g.dirbits[w] = 0u;
   for (uint32_t j = 0; j < g.nb; ++j)
     if (mix32(j ^ g.dirseed) & 1u) g.dirbits[j >> 5] |= 1u << (j & 31u);

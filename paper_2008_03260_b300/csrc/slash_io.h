@@ -25,7 +25,7 @@ struct CkptHeader {
   char magic[8];
   uint32_t kind;
   uint32_t header_bytes;   // sizeof(CkptHeader), for a later format to grow
-  uint32_t params[12];     // the kind's parameter struct, as raw words
+  uint32_t params[16];     // the kind's parameter struct, as raw words (zero-padded)
   uint64_t next_id;
   uint64_t payload_bytes;  // sum of the arrays' sizes
   uint64_t checksum;

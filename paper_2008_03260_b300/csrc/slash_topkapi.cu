@@ -23,7 +23,8 @@
 //   k_tk_query   warp per query: DOPH + addresses, then the ordered merge of
 //                the S*L sketches (shard-major, then table) with the merged
 //                sketch in registers (lane owns cells lane + 32 i), then the
-//                distinct heavy hitters ranked by (count desc, id asc)
+//                distinct heavy hitters ranked by (count desc, id asc) with
+//                two warp bitonic sorts of the cells in registers
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -89,6 +90,41 @@ k_tk_apply(const __grid_constant__ Geo g, const TkGeo tg, const __grid_constant_
   }
 }
 
+// Bitonic sort of the warp's 32*N keys, ascending; element i*32 + lane is
+// key[i] of that lane.  Strides below 32 exchange through shuffles, larger
+// ones between a lane's own registers.
+template <int N>
+__device__ __forceinline__ void warp_sort_u64(uint64_t (&key)[N], uint32_t lane) {
+  constexpr uint32_t n = 32u * N;
+#pragma unroll
+  for (uint32_t k = 2; k <= n; k <<= 1) {
+#pragma unroll
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32u) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const int p = i ^ (int)(j >> 5);
+          if (p > i) {
+            const bool up = ((32u * i) & k) == 0u;  // k >= 64: the lane bits do not matter
+            const uint64_t a = key[i], b = key[p];
+            const bool sw = up ? (a > b) : (a < b);
+            key[i] = sw ? b : a;
+            key[p] = sw ? a : b;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const uint32_t e = 32u * i + lane;
+          const uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, key[i], j);
+          const bool take_min = ((e & j) == 0u) == ((e & k) == 0u);
+          key[i] = take_min ? (o < key[i] ? o : key[i]) : (o > key[i] ? o : key[i]);
+        }
+      }
+    }
+  }
+}
+
 // One Appendix 2 merge of the cell (h, c) with a bucket cell of word v
 // (0 = empty, else id + 1 with count 1).
 __device__ __forceinline__ void tk_merge1(uint32_t& h, uint32_t& c, uint32_t v) {
@@ -110,10 +146,8 @@ k_tk_query(const __grid_constant__ Geo g, const TkGeo tg, const uint64_t* __rest
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   uint32_t* addr = tsm + warp * tg.per_warp;
   uint32_t* work = addr + tg.lpad;
-  uint32_t* m = work;                 // DOPH codes ...
+  uint32_t* m = work;  // DOPH codes
   uint32_t* mask = work + g.nb;
-  uint32_t* hs = work;                // ... then the merged sketch's heavy hitters
-  uint32_t* cs = work + NPL * 32;     //     and counts
   const uint32_t SL = g.S * g.L;
   constexpr int U = NPL >= 8 ? 2 : 16 / NPL;  // sketches loaded ahead of the merge
   for (uint32_t q = blockIdx.x * kTkWarps + warp; q < nq; q += gridDim.x * kTkWarps) {
@@ -147,50 +181,34 @@ k_tk_query(const __grid_constant__ Geo g, const TkGeo tg, const uint64_t* __rest
 #pragma unroll
         for (int i = 0; i < NPL; ++i) tk_merge1(h[i], c[i], v[j][i]);
     }
-    // distinct heavy hitters above the threshold, each at its largest count
+    // distinct heavy hitters above the threshold, each at its largest count:
+    // sort the cells by (id asc, count desc), drop each id's later cells, then
+    // sort the survivors by (count desc, id asc); empty cells sort last
+    uint64_t key[NPL];
 #pragma unroll
-    for (int i = 0; i < NPL; ++i) {
-      hs[lane + 32u * i] = h[i];
-      cs[lane + 32u * i] = c[i] > threshold ? c[i] : 0u;
-    }
-    __syncwarp();
-    bool keep[NPL];
+    for (int i = 0; i < NPL; ++i)
+      key[i] = c[i] > threshold ? ((uint64_t)h[i] << 32) | (0xFFFFFFFFu - c[i]) : ~0ull;
+    warp_sort_u64<NPL>(key, lane);
+    uint64_t carry = ~0ull;  // last element of the previous register
     uint32_t nkeep = 0;
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
-      const uint32_t me = lane + 32u * i, ci = cs[me], hi = hs[me];
-      bool kp = ci != 0u;
-      if (kp) {
-        for (uint32_t j = 0; j < NPL * 32u; ++j) {
-          const uint32_t cj = cs[j];
-          // another cell of the same id with a larger count, or the same count and a lower index
-          if (cj != 0u && hs[j] == hi && (cj > ci || (cj == ci && j < me))) { kp = false; break; }
-        }
-      }
-      keep[i] = kp;
-      nkeep += kp;
+      uint64_t prev = __shfl_up_sync(0xFFFFFFFFu, key[i], 1);
+      if (lane == 0) prev = carry;
+      carry = __shfl_sync(0xFFFFFFFFu, key[i], 31);
+      const bool live = key[i] != ~0ull && (prev == ~0ull || (prev >> 32) != (key[i] >> 32));
+      key[i] = live ? (key[i] << 32) | (key[i] >> 32) : ~0ull;
+      nkeep += __popc(__ballot_sync(0xFFFFFFFFu, live));
     }
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < NPL; ++i)
-      if (!keep[i]) cs[lane + 32u * i] = 0u;
-    __syncwarp();
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nkeep += __shfl_xor_sync(0xFFFFFFFFu, nkeep, o);
+    warp_sort_u64<NPL>(key, lane);
     int32_t* io = ids_out + (uint64_t)q * k;
     uint32_t* so = scores_out + (uint64_t)q * k;
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
-      if (!keep[i]) continue;
-      const uint32_t me = lane + 32u * i, ci = cs[me], hi = hs[me];
-      uint32_t rank = 0;
-      for (uint32_t j = 0; j < NPL * 32u && rank < k; ++j) {
-        const uint32_t cj = cs[j];
-        rank += cj != 0u && (cj > ci || (cj == ci && hs[j] < hi));
-      }
-      if (rank < k) {
-        io[rank] = (int32_t)hi;
-        so[rank] = ci;
+      const uint32_t e = 32u * i + lane;
+      if (e < k && key[i] != ~0ull) {
+        io[e] = (int32_t)(uint32_t)key[i];
+        so[e] = 0xFFFFFFFFu - (uint32_t)(key[i] >> 32);
       }
     }
     for (uint32_t j = min(nkeep, k) + lane; j < k; j += 32) {
@@ -237,7 +255,7 @@ namespace {
   } while (0)
 
 bool tk_params_ok(const slash_tk_params* p) {
-  if (!p || p->reserved != 0) return false;
+  if (!p || p->densify > SLASH_DENSIFY_OPTIMAL) return false;
   if (p->dim == 0 || p->K == 0 || p->L == 0 || p->L > SLASH_MAX_L) return false;
   if ((uint64_t)p->K * p->L > SLASH_MAX_NB) return false;
   if (p->log2_buckets < 1 || p->log2_buckets > 30) return false;
@@ -284,12 +302,12 @@ int slash_tk_build(const slash_tk_params* p, void* cuda_stream, slash_tk_index**
   g.B = p->log2_buckets; g.R = 0; g.d = p->rows; g.w = p->cells; g.S = p->shards;
   g.rbits = 0; g.capacity = p->capacity;
   derive_seeds(g, p->seed, p->rows);  // the W sketch-row seeds take the count-min rows' place
+  g.densify = p->densify;
   TkGeo& tg = ix->tg;
   tg.W = p->rows; tg.C = p->cells; tg.cmask = p->cells - 1u; tg.WC = p->rows * p->cells;
   tg.lpad = (p->L + 3u) & ~3u;
   const uint32_t hash_words = (g.nb + g.nw + 3u) & ~3u;
-  const uint32_t merge_words = 2u * 32u * (uint32_t)cells_per_lane(tg.WC);
-  tg.per_warp = tg.lpad + std::max(hash_words, merge_words);
+  tg.per_warp = tg.lpad + hash_words;
   if (tk_smem(ix) > ix->smem_optin) { delete ix; return SLASH_EINVAL; }
   ix->ncells = (((uint64_t)p->shards * p->L) << p->log2_buckets) * tg.WC;
   cudaError_t e = cudaMalloc(&ix->cells, sizeof(uint32_t) * ix->ncells);
@@ -424,7 +442,7 @@ uint64_t slash_tk_size(const slash_tk_index* ix) { return ix ? ix->next_id : 0; 
 
 uint64_t slash_tk_launches(const slash_tk_index* ix) { return ix ? ix->launches : 0; }
 
-static_assert(sizeof(slash_tk_params) == sizeof(uint32_t) * 12, "checkpoint header holds 12 parameter words");
+static_assert(sizeof(slash_tk_params) <= sizeof(CkptHeader::params), "checkpoint header holds the parameters");
 
 int slash_tk_save(slash_tk_index* ix, const char* path) {
   if (!ix || !path) return SLASH_EINVAL;
