@@ -86,6 +86,13 @@ int slash_tk_query(slash_tk_index *ix, const uint64_t *d_offs, const uint32_t *d
  * Synchronises.  Errors: SLASH_EINVAL, SLASH_ECUDA. */
 int slash_tk_export(slash_tk_index *ix, uint32_t *h_cells);
 
+/* Test support -- copy selected sketches to host memory: for i < n, sketch
+ * (h_shard[i], h_table[i], h_bucket[i]) -> h_cells[i][W][C] (cell words as in
+ * slash_tk_export).  Synchronises.  Errors: SLASH_EINVAL (index out of range),
+ * SLASH_ECUDA. */
+int slash_tk_debug_buckets(slash_tk_index *ix, const uint32_t *h_shard, const uint32_t *h_table,
+                           const uint32_t *h_bucket, uint32_t n, uint32_t *h_cells);
+
 /* Wait for `cuda_stream`, then report and clear the sticky device error word
  * (as slash_sync). */
 int slash_tk_sync(slash_tk_index *ix, void *cuda_stream);

@@ -94,6 +94,12 @@ def _load():
             lib.or_tk_insert.restype = i32
             lib.or_tk_insert.argtypes = [vp, vp, vp, u64, ctypes.POINTER(u64)]
             lib.or_tk_export.argtypes = [vp, vp]
+            lib.or_tk_new_partial.restype = vp
+            lib.or_tk_new_partial.argtypes = [u32, u32, u32, u32, u32, u32, u64, u64, u32, vp, vp, u64]
+            lib.or_tk_insert_parallel.restype = i32
+            lib.or_tk_insert_parallel.argtypes = [vp, vp, vp, u64, ctypes.POINTER(u64), i32]
+            lib.or_tk_bucket.restype = i32
+            lib.or_tk_bucket.argtypes = [vp, u32, u32, u32, vp]
             lib.or_tk_query.restype = i32
             lib.or_tk_query.argtypes = [vp, vp, vp, u64, u32, u32, vp, vp]
             _lib = lib
@@ -299,24 +305,42 @@ class TkIndex:
     """Oracle index whose buckets are TopKAPI sketches of W rows x C cells."""
 
     def __init__(self, *, K: int, L: int, log2_buckets: int, rows: int, cells: int, shards: int = 1,
-                 seed: int = 0, capacity: int, densify: int = 0):
+                 seed: int = 0, capacity: int, densify: int = 0, partial=None):
         self._lib = _load()
         self.K, self.L, self.B, self.W, self.C, self.S = K, L, log2_buckets, rows, cells, shards
-        self._h = self._lib.or_tk_new(K, L, log2_buckets, rows, cells, shards, seed, capacity, densify)
+        if partial is None:
+            self._h = self._lib.or_tk_new(K, L, log2_buckets, rows, cells, shards, seed, capacity, densify)
+        else:
+            rt, rb = _u32(partial[0]), _u32(partial[1])
+            self._h = self._lib.or_tk_new_partial(K, L, log2_buckets, rows, cells, shards, seed, capacity,
+                                                  densify, _p(rt), _p(rb), rt.size)
         if not self._h:
             raise MemoryError("oracle sketch allocation failed")
+        self.partial = partial is not None
 
     def __del__(self):
         h, self._h = getattr(self, "_h", None), None
         if h:
             self._lib.or_tk_free(h)
 
-    def insert(self, offs, cols) -> int:
+    def insert(self, offs, cols, threads: int = 1) -> int:
         offs, cols = _u64(offs), _u32(cols)
         first = ctypes.c_uint64()
-        if self._lib.or_tk_insert(self._h, _p(offs), _p(cols), offs.size - 1, ctypes.byref(first)):
+        if threads > 1:
+            rc = self._lib.or_tk_insert_parallel(self._h, _p(offs), _p(cols), offs.size - 1, ctypes.byref(first),
+                                                 threads)
+        else:
+            rc = self._lib.or_tk_insert(self._h, _p(offs), _p(cols), offs.size - 1, ctypes.byref(first))
+        if rc:
             raise ValueError("oracle insert failed: capacity exceeded")
         return int(first.value)
+
+    def bucket(self, t: int, b: int, s: int = 0) -> np.ndarray:
+        """cells [W][C][2] of sketch (s, t, b) = (heavy hitter or EMPTY, count)."""
+        out = np.empty((self.W, self.C, 2), dtype=np.uint32)
+        if self._lib.or_tk_bucket(self._h, s, t, b, _p(out)):
+            raise KeyError((s, t, b))
+        return out
 
     def export(self) -> np.ndarray:
         """cells [S][L][2^B][W][C][2] = (heavy hitter or EMPTY, count)."""
@@ -330,5 +354,6 @@ class TkIndex:
         nq = offs.size - 1
         ids = np.empty((nq, k), dtype=np.int32)
         scores = np.empty((nq, k), dtype=np.uint32)
-        self._lib.or_tk_query(self._h, _p(offs), _p(cols), nq, k, threshold, _p(ids), _p(scores))
+        if self._lib.or_tk_query(self._h, _p(offs), _p(cols), nq, k, threshold, _p(ids), _p(scores)):
+            raise KeyError("a query's sketch is not kept by this partial index")
         return ids, scores

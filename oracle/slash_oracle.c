@@ -537,8 +537,18 @@ typedef struct {
   uint32_t K, L, B, W, C, S;
   uint64_t capacity, next_id;
   uint32_t *seeds;       /* or_seeds_init: 2 + 2L + W + 2 */
-  uint32_t *hh, *cnt;    /* [S][L][2^B][W][C] */
+  /* per shard s: sketch (t, b) lives at storage row map[t*2^B + b] (dense: identity) */
+  int64_t *map;          /* NULL = dense */
+  uint64_t nstore;       /* materialised sketches per shard */
+  uint32_t *hh, *cnt;    /* [S][nstore][W][C] */
 } or_tk;
+
+/* storage row of sketch (s, t, b), or -1 when a partial index does not keep it */
+static int64_t or_tk_loc(const or_tk *ix, uint32_t s, uint32_t t, uint32_t b) {
+  uint64_t key = ((uint64_t)t << ix->B) + b;
+  int64_t r = ix->map ? ix->map[key] : (int64_t)key;
+  return r < 0 ? -1 : (int64_t)((uint64_t)s * ix->nstore + (uint64_t)r);
+}
 
 void or_tk_update(uint32_t *hh, uint32_t *cnt, uint32_t x) {
   if (*cnt > 0 && *hh == x) { *cnt += 1; return; }
@@ -560,17 +570,40 @@ void *or_tk_new(uint32_t K, uint32_t L, uint32_t B, uint32_t W, uint32_t C, uint
   ix->K = K; ix->L = L; ix->B = B; ix->W = W; ix->C = C; ix->S = S; ix->capacity = capacity;
   ix->seeds = (uint32_t *)malloc(sizeof(uint32_t) * (2 + 2 * L + W + 2));
   or_seeds_init(seed, L, W, densify, ix->seeds);
-  uint64_t n = ((uint64_t)S * L << B) * W * C;
+  ix->nstore = (uint64_t)L << B;
+  uint64_t n = (uint64_t)S * ix->nstore * W * C;
   ix->hh = (uint32_t *)calloc(n, sizeof(uint32_t));
   ix->cnt = (uint32_t *)calloc(n, sizeof(uint32_t));
   if (!ix->hh || !ix->cnt) { free(ix->hh); free(ix->cnt); free(ix->seeds); free(ix); return NULL; }
   return ix;
 }
 
+/* partial sketch index: only the listed (t, b) sketches (of every shard) are kept */
+void *or_tk_new_partial(uint32_t K, uint32_t L, uint32_t B, uint32_t W, uint32_t C, uint32_t S, uint64_t seed,
+                        uint64_t capacity, uint32_t densify, const uint32_t *req_t, const uint32_t *req_b,
+                        uint64_t nreq) {
+  or_tk *ix = (or_tk *)calloc(1, sizeof(or_tk));
+  ix->K = K; ix->L = L; ix->B = B; ix->W = W; ix->C = C; ix->S = S; ix->capacity = capacity;
+  ix->seeds = (uint32_t *)malloc(sizeof(uint32_t) * (2 + 2 * L + W + 2));
+  or_seeds_init(seed, L, W, densify, ix->seeds);
+  uint64_t nkeys = (uint64_t)L << B;
+  ix->map = (int64_t *)malloc(sizeof(int64_t) * nkeys);
+  for (uint64_t k = 0; k < nkeys; ++k) ix->map[k] = -1;
+  uint64_t n = 0;
+  for (uint64_t i = 0; i < nreq; ++i) {
+    uint64_t key = ((uint64_t)req_t[i] << B) + req_b[i];
+    if (ix->map[key] < 0) ix->map[key] = (int64_t)n++;
+  }
+  ix->nstore = n;
+  ix->hh = (uint32_t *)calloc((uint64_t)S * n * W * C + 1, sizeof(uint32_t));
+  ix->cnt = (uint32_t *)calloc((uint64_t)S * n * W * C + 1, sizeof(uint32_t));
+  return ix;
+}
+
 void or_tk_free(void *p) {
   or_tk *ix = (or_tk *)p;
   if (!ix) return;
-  free(ix->seeds); free(ix->hh); free(ix->cnt); free(ix);
+  free(ix->seeds); free(ix->map); free(ix->hh); free(ix->cnt); free(ix);
 }
 
 /* Algorithm 1 with sketches: each row's id goes into one sketch per table. */
@@ -587,7 +620,9 @@ int or_tk_insert(void *p, const uint64_t *offs, const uint32_t *cols, uint64_t n
     or_doph_seeded(cols + (offs[i] - offs[0]), offs[i + 1] - offs[i], nb, ix->seeds, ix->L, ix->W, codes);
     for (uint32_t t = 0; t < ix->L; ++t) {
       uint32_t b = or_table_address(codes, t, ix->K, ix->B, st[t]);
-      uint64_t base = ((((uint64_t)s * ix->L + t) << ix->B) + b) * ix->W * ix->C;
+      int64_t loc = or_tk_loc(ix, s, t, b);
+      if (loc < 0) continue;  /* a partial index does not keep this sketch */
+      uint64_t base = (uint64_t)loc * ix->W * ix->C;
       for (uint32_t r = 0; r < ix->W; ++r) {
         uint64_t c = base + (uint64_t)r * ix->C + (or_mix32((uint32_t)id ^ tk[r]) & (ix->C - 1));
         or_tk_update(ix->hh + c, ix->cnt + c, (uint32_t)id);
@@ -598,10 +633,84 @@ int or_tk_insert(void *p, const uint64_t *offs, const uint32_t *cols, uint64_t n
   return 0;
 }
 
+/* or_tk_insert with the rows' table addresses computed by `threads` threads
+ * (a row's hash depends on that row alone); the cell updates then run on one
+ * thread in ascending id order, exactly as in or_tk_insert. */
+typedef struct {
+  const or_tk *ix; const uint64_t *offs; const uint32_t *cols; uint64_t b, e; uint32_t *addr;
+} or_tk_hjob;
+
+static void *or_tk_hash_run(void *a) {
+  or_tk_hjob *j = (or_tk_hjob *)a;
+  const or_tk *ix = j->ix;
+  uint32_t nb = ix->K * ix->L;
+  uint32_t *codes = (uint32_t *)malloc(sizeof(uint32_t) * nb);
+  for (uint64_t i = j->b; i < j->e; ++i) {
+    or_doph_seeded(j->cols + (j->offs[i] - j->offs[0]), j->offs[i + 1] - j->offs[i], nb, ix->seeds, ix->L, ix->W,
+                   codes);
+    for (uint32_t t = 0; t < ix->L; ++t)
+      j->addr[(i - j->b) * ix->L + t] = or_table_address(codes, t, ix->K, ix->B, ix->seeds[2 + t]);
+  }
+  free(codes);
+  return NULL;
+}
+
+int or_tk_insert_parallel(void *p, const uint64_t *offs, const uint32_t *cols, uint64_t n, uint64_t *first_id,
+                          int threads) {
+  or_tk *ix = (or_tk *)p;
+  if (ix->next_id + n > ix->capacity) return -1;
+  if (threads < 1) threads = 1;
+  const uint32_t *tk = ix->seeds + 2 + 2 * ix->L;
+  const uint64_t block = 1u << 20;
+  uint32_t *addr = (uint32_t *)malloc(sizeof(uint32_t) * block * ix->L);
+  or_tk_hjob *job = (or_tk_hjob *)calloc(threads, sizeof(or_tk_hjob));
+  pthread_t *tid = (pthread_t *)calloc(threads, sizeof(pthread_t));
+  *first_id = ix->next_id;
+  for (uint64_t r0 = 0; r0 < n; r0 += block) {
+    uint64_t m = n - r0 < block ? n - r0 : block;
+    for (int t = 0; t < threads; ++t) {
+      job[t].ix = ix; job[t].offs = offs; job[t].cols = cols;
+      job[t].b = r0 + m * (uint64_t)t / threads; job[t].e = r0 + m * (uint64_t)(t + 1) / threads;
+      job[t].addr = addr + (job[t].b - r0) * ix->L;
+      pthread_create(&tid[t], NULL, or_tk_hash_run, &job[t]);
+    }
+    for (int t = 0; t < threads; ++t) pthread_join(tid[t], NULL);
+    for (uint64_t i = 0; i < m; ++i) {
+      uint64_t id = ix->next_id + r0 + i;
+      uint32_t s = (uint32_t)(((unsigned __int128)id * ix->S) / ix->capacity);
+      for (uint32_t t = 0; t < ix->L; ++t) {
+        int64_t loc = or_tk_loc(ix, s, t, addr[i * ix->L + t]);
+        if (loc < 0) continue;
+        uint64_t base = (uint64_t)loc * ix->W * ix->C;
+        for (uint32_t r = 0; r < ix->W; ++r) {
+          uint64_t c = base + (uint64_t)r * ix->C + (or_mix32((uint32_t)id ^ tk[r]) & (ix->C - 1));
+          or_tk_update(ix->hh + c, ix->cnt + c, (uint32_t)id);
+        }
+      }
+    }
+  }
+  ix->next_id += n;
+  free(addr); free(job); free(tid);
+  return 0;
+}
+
+/* cells of sketch (s, t, b): out[W*C][2] = (heavy hitter or 0xFFFFFFFF, count); -1 if not kept */
+int or_tk_bucket(const void *p, uint32_t s, uint32_t t, uint32_t b, uint32_t *out) {
+  const or_tk *ix = (const or_tk *)p;
+  int64_t loc = or_tk_loc(ix, s, t, b);
+  if (loc < 0) return -1;
+  uint64_t base = (uint64_t)loc * ix->W * ix->C;
+  for (uint32_t c = 0; c < ix->W * ix->C; ++c) {
+    out[2 * c] = ix->cnt[base + c] ? ix->hh[base + c] : OR_EMPTY;
+    out[2 * c + 1] = ix->cnt[base + c];
+  }
+  return 0;
+}
+
 /* cells [S][L][2^B][W][C][2] = (heavy hitter or 0xFFFFFFFF when empty, count) */
 void or_tk_export(const void *p, uint32_t *out) {
   const or_tk *ix = (const or_tk *)p;
-  uint64_t n = ((uint64_t)ix->S * ix->L << ix->B) * ix->W * ix->C;
+  uint64_t n = (uint64_t)ix->S * ix->nstore * ix->W * ix->C;  /* dense: nstore = L * 2^B */
   for (uint64_t c = 0; c < n; ++c) {
     out[2 * c] = ix->cnt[c] ? ix->hh[c] : OR_EMPTY;
     out[2 * c + 1] = ix->cnt[c];
@@ -621,12 +730,16 @@ int or_tk_query(const void *p, const uint64_t *offs, const uint32_t *cols, uint6
   for (uint64_t q = 0; q < nq; ++q) {
     or_doph_seeded(cols + (offs[q] - offs[0]), offs[q + 1] - offs[q], nb, ix->seeds, ix->L, ix->W, codes);
     for (uint32_t c = 0; c < WC; ++c) { mh[c] = OR_EMPTY; mc[c] = 0; }
+    int missing = 0;
     for (uint32_t s = 0; s < ix->S; ++s)
       for (uint32_t t = 0; t < ix->L; ++t) {
         uint32_t b = or_table_address(codes, t, ix->K, ix->B, st[t]);
-        uint64_t base = ((((uint64_t)s * ix->L + t) << ix->B) + b) * WC;
+        int64_t loc = or_tk_loc(ix, s, t, b);
+        if (loc < 0) { missing = 1; continue; }
+        uint64_t base = (uint64_t)loc * WC;
         for (uint32_t c = 0; c < WC; ++c) or_tk_merge_cell(mh + c, mc + c, ix->hh[base + c], ix->cnt[base + c]);
       }
+    if (missing) { free(codes); free(mh); free(mc); free(cand); return -1; }
     /* distinct heavy hitters, each with its largest count; Appendix 2 reports
      * those whose count exceeds the threshold */
     uint32_t nc = 0;

@@ -110,6 +110,7 @@ def _load() -> ctypes.CDLL:
         "slash_tk_size": (u64, [vp]),
         "slash_tk_launches": (u64, [vp]),
         "slash_tk_free": (i32, [vp]),
+        "slash_tk_debug_buckets": (i32, [vp, vp, vp, vp, u32, vp]),
         "slash_save": (i32, [vp, ctypes.c_char_p]),
         "slash_load": (i32, [ctypes.c_char_p, vp, P(vp)]),
         "slash_get_params": (i32, [vp, P(slash_params)]),
@@ -541,6 +542,17 @@ class TkIndex:
 
     def export(self):
         return slash_tk_export(self.h, self.p)
+
+    def buckets(self, shard, table, bucket):
+        """Cell words [n][W][C] of the listed sketches."""
+        import numpy as np
+        s_ = np.ascontiguousarray(shard, dtype=np.uint32)
+        t_ = np.ascontiguousarray(table, dtype=np.uint32)
+        b_ = np.ascontiguousarray(bucket, dtype=np.uint32)
+        out = np.empty((s_.size, self.p.rows, self.p.cells), dtype=np.uint32)
+        _check(_lib.slash_tk_debug_buckets(self.h, s_.ctypes.data, t_.ctypes.data, b_.ctypes.data, s_.size,
+                                           out.ctypes.data), "slash_tk_debug_buckets")
+        return out
 
     def sync(self, stream=None) -> None:
         _check(int(_lib.slash_tk_sync(self.h, _stream(stream))), "slash_tk_sync")

@@ -66,6 +66,10 @@ namespace {
 constexpr int kHashWarps = 8;
 constexpr int kRowsPerWarp = 4;
 constexpr int kHashRows = kHashWarps * kRowsPerWarp;  // rows per CTA
+// The CTA's address tile is [L][kTileStride]: a lane writes its tables' entries
+// of one row, i.e. a column of the tile; the odd stride puts them in different
+// shared-memory banks (a stride of kHashRows = 32 would put all 32 in one).
+constexpr int kTileStride = kHashRows + 1;
 
 // Rows [blockIdx.x*32, +32): addresses -> bkt[t*ldb + row] (table-major),
 // optional codes [n][nb], optional per-bucket counts (insert).
@@ -80,7 +84,7 @@ k_hash(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
   const uint32_t per_warp = (g.nb + g.nw + 3u) & ~3u;  // 16-byte aligned per warp
   uint32_t* m = smem + warp * per_warp;
   uint32_t* mask = m + g.nb;
-  uint32_t* tile = smem + kHashWarps * per_warp;  // [L][kHashRows]
+  uint32_t* tile = smem + kHashWarps * per_warp;  // [L][kTileStride]
   const uint64_t row0 = (uint64_t)blockIdx.x * kHashRows;
   for (uint32_t k = 0; k < kRowsPerWarp; ++k) {
     const uint32_t lr = warp * kRowsPerWarp + k;
@@ -102,7 +106,7 @@ k_hash(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
         const uint32_t rank = atomicAdd(&cnt[(((uint64_t)s * g.L + t) << g.B) | b], 1u);
         if (g.rbits) out = (b << g.rbits) | min(rank, (1u << g.rbits) - 1u);
       }
-      tile[t * kHashRows + lr] = out;
+      tile[t * kTileStride + lr] = out;
     }
     if (codes)
       for (uint32_t j = lane; j < g.nb; j += 32) codes[r * g.nb + j] = m[j];
@@ -112,7 +116,7 @@ k_hash(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
   for (uint32_t idx = threadIdx.x; idx < g.L * kHashRows; idx += blockDim.x) {
     const uint32_t t = idx / kHashRows, lr = idx - t * kHashRows;
     const uint64_t r = row0 + lr;
-    if (r < n) bkt[t * ldb + r] = tile[idx];
+    if (r < n) bkt[t * ldb + r] = tile[t * kTileStride + lr];
   }
 }
 
@@ -123,7 +127,7 @@ k_hash(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
 // hit 32 different banks.  Non-empty bins are recognised by value; the one
 // feature whose hash is 0xFFFFFFFF (it lands in bin nb-1) is flagged apart.
 template <int C, int K, bool kCount>
-__global__ void __launch_bounds__(kHashWarps * 32)
+__global__ void __launch_bounds__(kHashWarps * 32, 5)  // five CTAs per SM: 51 registers
 k_hash_reg(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
            const uint64_t* __restrict__ offs, const uint32_t* __restrict__ cols, uint32_t n, uint64_t id0,
            uint32_t* __restrict__ bkt, uint64_t ldb, uint32_t* __restrict__ codes,
@@ -133,7 +137,7 @@ k_hash_reg(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   uint32_t* m = smem + warp * ROW;        // padded bin minima; m[ROW-1] = flag word
   uint32_t* flag = m + ROW - 1u;
-  uint32_t* tile = smem + kHashWarps * ROW;  // [L][kHashRows]
+  uint32_t* tile = smem + kHashWarps * ROW;  // [L][kTileStride]
   const uint64_t row0 = (uint64_t)blockIdx.x * kHashRows;
   for (uint32_t kk = 0; kk < kRowsPerWarp; ++kk) {
     const uint32_t lr = warp * kRowsPerWarp + kk;
@@ -223,7 +227,7 @@ k_hash_reg(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
         const uint32_t rank = atomicAdd(&cnt[(((uint64_t)s * g.L + t) << g.B) | b], 1u);
         if (g.rbits) out = (b << g.rbits) | min(rank, (1u << g.rbits) - 1u);
       }
-      tile[t * kHashRows + lr] = out;
+      tile[t * kTileStride + lr] = out;
     }
     if (codes) {
 #pragma unroll
@@ -235,7 +239,7 @@ k_hash_reg(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
   for (uint32_t idx = threadIdx.x; idx < g.L * kHashRows; idx += blockDim.x) {
     const uint32_t t = idx / kHashRows, lr = idx - t * kHashRows;
     const uint64_t r = row0 + lr;
-    if (r < n) bkt[t * ldb + r] = tile[idx];
+    if (r < n) bkt[t * ldb + r] = tile[t * kTileStride + lr];
   }
 }
 
@@ -366,13 +370,18 @@ k_plan(const __grid_constant__ Geo g, uint64_t nk, const uint32_t* __restrict__ 
 
 // ----------------------------------------------------------------------------- insert: scatter
 constexpr int kScatterThreads = 256;
-constexpr int kScatterPerThread = 4;
-constexpr uint32_t kScatterPiece = 1u << 21;  // rows per piece
+constexpr int kScatterPerThread = 8;
+// Rows per piece.  A piece walks one table at a time; with the whole chunk in
+// one piece a bucket's staged ids arrive in rank order across the chunk and
+// each bucket keeps one partly written line in L2 (one table: 2^B lines), so
+// the staging stores leave L2 as whole lines (measured at 2^18 buckets: 2M-row
+// pieces 34.7 ms, 4M 29.0 ms, 64M 22.3 ms per 50M rows).
+constexpr uint32_t kScatterPiece = 1u << 26;
 
 // Grid (x: rows within a piece, y: table, z: piece): blocks run roughly in
-// that order, so the records and the stage region touched at any moment are
-// one table's (a few MB): they stay in L2.  Ids below their bucket's
-// threshold take a slot of its staging range.
+// that order, so the records touched at any moment are one table's (16 B per
+// bucket) and stay in L2, as do the open staging lines of that table's
+// buckets.  Ids below their bucket's threshold take a slot of its staging range.
 __global__ void __launch_bounds__(kScatterThreads)
 k_scatter(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
           const uint32_t* __restrict__ bkt, uint64_t ldb, uint32_t n, uint64_t id0, uint4* __restrict__ meta,
@@ -1132,7 +1141,7 @@ namespace slash {
 
 size_t hash_smem_bytes(const Geo& g) {
   const size_t per_warp = (g.nb + g.nw + 3u) & ~3u;
-  return sizeof(uint32_t) * ((size_t)kHashWarps * per_warp + (size_t)g.L * kHashRows);
+  return sizeof(uint32_t) * ((size_t)kHashWarps * per_warp + (size_t)g.L * kTileStride);
 }
 
 void init_hash_kernels(int smem_optin) {
@@ -1156,7 +1165,7 @@ int launch_hash(const Geo& g, const ShardMap& sm, const uint64_t* offs, const ui
   // register-chunk kernels hold the side rule only
   const uint32_t C = nb % 32u == 0u && !g.densify ? nb / 32u : 0u;
   const size_t rsmem = sizeof(uint32_t) * ((size_t)kHashWarps * (((nb + 33u) + 3u) & ~3u) +
-                                           (size_t)g.L * kHashRows);
+                                           (size_t)g.L * kTileStride);
 #define SLASH_HREG(CC, KK)                                                                                  \
   if (C == CC && K == KK) {                                                                              \
     if (count)                                                                                           \

@@ -419,6 +419,24 @@ int slash_tk_export(slash_tk_index* ix, uint32_t* h_cells) {
   return SLASH_OK;
 }
 
+int slash_tk_debug_buckets(slash_tk_index* ix, const uint32_t* h_shard, const uint32_t* h_table,
+                           const uint32_t* h_bucket, uint32_t n, uint32_t* h_cells) {
+  if (!ix) return SLASH_EINVAL;
+  if (n == 0) return SLASH_OK;
+  if (!h_shard || !h_table || !h_bucket || !h_cells) return SLASH_EINVAL;
+  for (uint32_t i = 0; i < n; ++i)
+    if (h_shard[i] >= ix->p.shards || h_table[i] >= ix->p.L || h_bucket[i] >= (1u << ix->p.log2_buckets))
+      return SLASH_EINVAL;
+  SLASH_TK_CK(cudaDeviceSynchronize());
+  const uint32_t wc = ix->tg.WC;
+  for (uint32_t i = 0; i < n; ++i) {
+    const uint64_t key = (((uint64_t)h_shard[i] * ix->p.L + h_table[i]) << ix->p.log2_buckets) | h_bucket[i];
+    SLASH_TK_CK(cudaMemcpy(h_cells + (uint64_t)i * wc, ix->cells + key * wc, sizeof(uint32_t) * wc,
+                           cudaMemcpyDeviceToHost));
+  }
+  return SLASH_OK;
+}
+
 int slash_tk_sync(slash_tk_index* ix, void* cuda_stream) {
   if (!ix) return SLASH_EINVAL;
   SLASH_TK_CK(cudaStreamSynchronize((cudaStream_t)cuda_stream));

@@ -46,3 +46,39 @@ def test_criteo_full_size_sampled_parity():
     want_ids, want_sc = oix.query(qo, qc, w.topk)
     assert np.array_equal(gids, want_ids)
     assert np.array_equal(gsc, want_sc)
+
+
+def test_topkapi_full_size_sampled_parity():
+    """The `topkapi` workload (50M rows, 4x32 sketches, 2^18 per table) as the
+    benchmark runs it: the sketches of 200 queries plus 2000 random ones, and
+    the 200 queries' answers, against an oracle that keeps only those sketches
+    (its cell updates run in id order over all 50M rows)."""
+    import paper_2008_03260_b300 as s
+    from datagen.workloads import TOPKAPI as tw
+    W, C = tw.extra["tk_rows"], tw.extra["tk_cells"]
+    g = datagen.Generator()
+    offs, cols = g.rows(tw.seed, 0, tw.n_rows)
+    qo, qc, _ = g.queries(tw.seed, tw.qseed, 200, tw.n_rows, **tw.query_kwargs())
+    p = s.TkParams(dim=tw.dim, K=tw.K, L=tw.L, log2_buckets=tw.log2_buckets, rows=W, cells=C,
+                   seed=tw.seed, capacity=tw.n_rows)
+    with s.TkIndex(p) as ix:
+        ix.insert(_dev(offs), _dev(cols))
+        ids, sc = ix.query(_dev(qo), _dev(qc), tw.topk)
+        ix.sync()
+        _, qbk = oracle.hash_rows(tw.K, tw.L, tw.log2_buckets, tw.seed, W, qo, qc, want_codes=False)
+        rng = np.random.default_rng(6)
+        rt = np.concatenate([np.tile(np.arange(tw.L), len(qo) - 1), rng.integers(0, tw.L, 2000)]).astype(np.uint32)
+        rb = np.concatenate([qbk.ravel(), rng.integers(0, 1 << tw.log2_buckets, 2000)]).astype(np.uint32)
+        gcells = ix.buckets(np.zeros_like(rt), rt, rb)
+        gids, gsc = ids.cpu().numpy(), sc.cpu().numpy().view(np.uint32)
+    oix = oracle.TkIndex(K=tw.K, L=tw.L, log2_buckets=tw.log2_buckets, rows=W, cells=C, seed=tw.seed,
+                         capacity=tw.n_rows, partial=(rt, rb))
+    oix.insert(offs, cols, threads=datagen.default_threads())
+    for i in range(len(rt)):
+        cells = oix.bucket(int(rt[i]), int(rb[i]))
+        want = np.where(cells[..., 1] > 0, cells[..., 0] + 1, 0).astype(np.uint32)
+        assert np.array_equal(gcells[i], want), (int(rt[i]), int(rb[i]))
+    assert (gcells > 0).mean() > 0.5  # the sample's sketches are mostly occupied
+    want_ids, want_sc = oix.query(qo, qc, tw.topk)
+    assert np.array_equal(gids, want_ids)
+    assert np.array_equal(gsc, want_sc)

@@ -106,3 +106,28 @@ def test_threshold_filters_by_score():
         got = [(a, b) for a, b in zip(ids2[i], sc2[i]) if a >= 0]
         assert got == keep
         assert np.all(ids2[i][len(got):] == -1) and np.all(sc2[i][len(got):] == 0)
+
+
+def test_partial_parallel_insert_matches_dense():
+    """The partial index with the parallel hash keeps exactly the dense
+    index's cells for the listed sketches, and answers queries over them."""
+    g = datagen.Generator()
+    n = 5000
+    offs, cols = g.rows(2, 0, n)
+    qo, qc, _ = g.queries(2, 3, 40, n)
+    dense = oracle.TkIndex(K=3, L=8, log2_buckets=7, rows=2, cells=8, shards=2, seed=4, capacity=n)
+    dense.insert(offs, cols)
+    _, qbk = oracle.hash_rows(3, 8, 7, 4, 2, qo, qc, want_codes=False)
+    rt = np.concatenate([np.tile(np.arange(8), 40), np.arange(8)]).astype(np.uint32)
+    rb = np.concatenate([qbk.ravel(), np.arange(8)]).astype(np.uint32)
+    part = oracle.TkIndex(K=3, L=8, log2_buckets=7, rows=2, cells=8, shards=2, seed=4, capacity=n,
+                          partial=(rt, rb))
+    part.insert(offs[:2001], cols, threads=3)
+    part.insert(offs[2000:] - offs[2000], cols[int(offs[2000]):], threads=2)
+    full = dense.export()
+    for t, b in zip(rt, rb):
+        for s in range(2):
+            assert np.array_equal(part.bucket(int(t), int(b), s), full[s, t, b])
+    a, b_ = dense.query(qo, qc, 5)
+    c, d = part.query(qo, qc, 5)
+    assert np.array_equal(a, c) and np.array_equal(b_, d)
