@@ -209,14 +209,15 @@ def config_of(w, args) -> dict:
 
 
 # ----------------------------------------------------------------------------- GPU arm
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of work,
-# from ncu captures of the unchanged kernels on the 2M-row criteo-shaped case
-# (see profiles/); a full launch's traffic is this times its units (rows or
-# (row, table) pairs), since each unit's reads and writes are its own.
-TRAFFIC_PER_UNIT = {
-    "k_hash_insert": (807.018496e6 / 2_000_000, "rows", "profiles/k_hash_reg_criteo-2Mrows.md"),
-    "k_scatter": (905.274624e6 / (2_000_000 * 64), "pairs", "profiles/k_scatter_criteo-2Mrows.md"),
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# unchanged kernels, measured by ncu (one-pass metrics) on this full-size
+# workload: 50M rows, 64 tables, 2^18 buckets (see profiles/).
+TRAFFIC_PER_LAUNCH = {
+    "k_hash_insert": (9701348608 + 13646447104, "profiles/dram_criteo-50Mrows.md"),
+    "k_scatter": (18967860480 + 13676890880, "profiles/dram_criteo-50Mrows.md"),
+    "k_merge_small": (8093892608 + 8968221440, "profiles/dram_criteo-50Mrows.md"),
 }
+TRAFFIC_SHAPE = {"rows": 50_000_000, "L": 64, "log2_buckets": 18, "reservoir": 128}
 
 ALGO_BYTES_DOC = {
     "k_hash_insert": "8 + 4*nnz (CSR read) + 4*L (addresses written) per row",
@@ -405,11 +406,10 @@ def main():
         bytes_per_launch = algo[dom] / launches_per_step
         ach = bytes_per_launch / (kern[dom]["ms_per_launch"] / 1e3) / 1e9
         traffic, tsrc = None, None
-        if dom in TRAFFIC_PER_UNIT:
-            per, unit, src = TRAFFIC_PER_UNIT[dom]
-            units = rows if unit == "rows" else rows * L
-            traffic = per * units / launches_per_step
-            tsrc = f"{src}: ncu DRAM bytes of a 2M-row capture, scaled by {unit}"
+        shape = {"rows": rows, "L": L, "log2_buckets": w.log2_buckets, "reservoir": w.reservoir}
+        if dom in TRAFFIC_PER_LAUNCH and shape == TRAFFIC_SHAPE and launches_per_step == 1:
+            traffic, src = TRAFFIC_PER_LAUNCH[dom]
+            tsrc = f"{src}: ncu DRAM bytes of this kernel on this workload (one-pass metrics)"
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / pk["hbm_gbs"], "traffic": traffic, "traffic_source": tsrc,
                 "peak_source": pk["source"],

@@ -86,6 +86,7 @@ k_hash(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
   uint32_t* mask = m + g.nb;
   uint32_t* tile = smem + kHashWarps * per_warp;  // [L][kTileStride]
   const uint64_t row0 = (uint64_t)blockIdx.x * kHashRows;
+  const uint64_t keep = kCount ? l2_evict_last_policy() : 0ull;  // the bucket counts stay in L2
   for (uint32_t k = 0; k < kRowsPerWarp; ++k) {
     const uint32_t lr = warp * kRowsPerWarp + k;
     const uint64_t r = row0 + lr;
@@ -103,7 +104,7 @@ k_hash(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
       uint32_t out = b;
       if (kCount) {
         // the count's old value is this pair's rank in its bucket: kept in the low bits
-        const uint32_t rank = atomicAdd(&cnt[(((uint64_t)s * g.L + t) << g.B) | b], 1u);
+        const uint32_t rank = atomic_add_keep(&cnt[(((uint64_t)s * g.L + t) << g.B) | b], 1u, keep);
         if (g.rbits) out = (b << g.rbits) | min(rank, (1u << g.rbits) - 1u);
       }
       tile[t * kTileStride + lr] = out;
@@ -116,7 +117,7 @@ k_hash(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
   for (uint32_t idx = threadIdx.x; idx < g.L * kHashRows; idx += blockDim.x) {
     const uint32_t t = idx / kHashRows, lr = idx - t * kHashRows;
     const uint64_t r = row0 + lr;
-    if (r < n) bkt[t * ldb + r] = tile[t * kTileStride + lr];
+    if (r < n) __stcs(&bkt[t * ldb + r], tile[t * kTileStride + lr]);
   }
 }
 
@@ -139,6 +140,7 @@ k_hash_reg(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
   uint32_t* flag = m + ROW - 1u;
   uint32_t* tile = smem + kHashWarps * ROW;  // [L][kTileStride]
   const uint64_t row0 = (uint64_t)blockIdx.x * kHashRows;
+  const uint64_t keep = kCount ? l2_evict_last_policy() : 0ull;  // the bucket counts stay in L2
   for (uint32_t kk = 0; kk < kRowsPerWarp; ++kk) {
     const uint32_t lr = warp * kRowsPerWarp + kk;
     const uint64_t r = row0 + lr;
@@ -155,7 +157,7 @@ k_hash_reg(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
     __syncwarp();
     bool bad = false;
     for (uint64_t i = b0 + lane; i < b1; i += 32) {
-      const uint32_t f = __ldg(cols + i);
+      const uint32_t f = __ldcs(cols + i);
       if (f >= g.dim) { bad = true; continue; }
       const uint32_t h = mix32(f ^ g.a);
       const uint32_t bin = __umulhi(h, NB);
@@ -224,7 +226,7 @@ k_hash_reg(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
       uint32_t out = b;
       if (kCount) {
         // the count's old value is this pair's rank in its bucket: kept in the low bits
-        const uint32_t rank = atomicAdd(&cnt[(((uint64_t)s * g.L + t) << g.B) | b], 1u);
+        const uint32_t rank = atomic_add_keep(&cnt[(((uint64_t)s * g.L + t) << g.B) | b], 1u, keep);
         if (g.rbits) out = (b << g.rbits) | min(rank, (1u << g.rbits) - 1u);
       }
       tile[t * kTileStride + lr] = out;
@@ -239,7 +241,7 @@ k_hash_reg(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
   for (uint32_t idx = threadIdx.x; idx < g.L * kHashRows; idx += blockDim.x) {
     const uint32_t t = idx / kHashRows, lr = idx - t * kHashRows;
     const uint64_t r = row0 + lr;
-    if (r < n) bkt[t * ldb + r] = tile[t * kTileStride + lr];
+    if (r < n) __stcs(&bkt[t * ldb + r], tile[t * kTileStride + lr]);
   }
 }
 
@@ -395,7 +397,7 @@ k_scatter(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
   for (int k = 0; k < kScatterPerThread; ++k) {
     const uint64_t i = base + (uint64_t)k * kScatterThreads;
     if (i >= pend) break;
-    const uint32_t v = bkt[t * ldb + i];
+    const uint32_t v = __ldcs(&bkt[t * ldb + i]);
     const uint32_t b = g.rbits ? v >> g.rbits : v;
     const uint64_t id = id0 + i;
     const uint32_t s = shard_of(sm, g.S, id);

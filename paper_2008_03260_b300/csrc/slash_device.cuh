@@ -49,6 +49,29 @@ __device__ __forceinline__ uint32_t cm_cell(uint32_t id, uint32_t sc_r, uint32_t
   return mix32(id ^ sc_r) & wmask;
 }
 
+// L2 residency hints.  Counters and sketch cells that a kernel updates many
+// times are tagged evict-last; the kernels read their one-pass inputs and write
+// their one-pass outputs with evict-first loads and stores (__ldcs / __stcs),
+// so that this streaming traffic does not push the counters out of L2.
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+// atomicAdd(p, v) whose line L2 keeps as long as it can; returns the old value.
+__device__ __forceinline__ uint32_t atomic_add_keep(uint32_t* p, uint32_t v, uint64_t pol) {
+  uint32_t old;
+  asm volatile("atom.global.add.L2::cache_hint.u32 %0, [%1], %2, %3;"
+               : "=r"(old) : "l"(p), "r"(v), "l"(pol) : "memory");
+  return old;
+}
+
+// atomicMax(p, v) without a result, on a line L2 keeps as long as it can.
+__device__ __forceinline__ void red_max_keep(uint32_t* p, uint32_t v, uint64_t pol) {
+  asm volatile("red.global.max.L2::cache_hint.u32 [%0], %1, %2;" :: "l"(p), "r"(v), "l"(pol) : "memory");
+}
+
 // Index geometry and seeds, passed by value to every kernel (constant bank).
 struct Geo {
   uint32_t dim, K, L, nb, nw, B, R, d, w, S;

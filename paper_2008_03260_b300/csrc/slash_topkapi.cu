@@ -19,7 +19,7 @@
 // Kernels:
 //   k_tk_apply   thread per (pass, row): if the row's address in the pass's
 //                table lies in the pass's bucket range, W atomic maxima
-//                (red.global.max) on the sketch's cells
+//                (red.global.max, evict-last) on the sketch's cells
 //   k_tk_query   warp per query: DOPH + addresses, then the ordered merge of
 //                the S*L sketches (shard-major, then table) with the merged
 //                sketch in registers (lane owns cells lane + 32 i), then the
@@ -75,18 +75,19 @@ k_tk_apply(const __grid_constant__ Geo g, const TkGeo tg, const __grid_constant_
   const uint32_t t = pass >> log2q, q = pass & ((1u << log2q) - 1u);
   const uint32_t shift = g.B - log2q;  // bucket range = top log2q bits of the address
   const uint32_t* col = bkt + (uint64_t)t * ldb;
+  const uint64_t keep = l2_evict_last_policy();  // the pass's sketches stay in L2
 #pragma unroll 4
   for (uint32_t i = 0; i < kApplyRowsPerThread; ++i) {
     const uint32_t r = rb * kApplyRows + i * kApplyThreads + threadIdx.x;
     if (r >= n) break;
-    const uint32_t b = __ldg(col + r);
+    const uint32_t b = __ldcs(col + r);
     if ((b >> shift) != q) continue;
     const uint64_t id = id0 + r;
     const uint32_t s = g.S > 1 ? shard_of(sm, g.S, id) : 0u;
     uint32_t* sk = cells + (((((uint64_t)s * g.L + t) << g.B) | b) * tg.WC);
     const uint32_t word = (uint32_t)id + 1u;
     for (uint32_t rr = 0; rr < tg.W; ++rr)
-      atomicMax(sk + rr * tg.C + (mix32((uint32_t)id ^ g.sc[rr]) & tg.cmask), word);
+      red_max_keep(sk + rr * tg.C + (mix32((uint32_t)id ^ g.sc[rr]) & tg.cmask), word, keep);
   }
 }
 
