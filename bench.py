@@ -218,6 +218,9 @@ TRAFFIC_PER_LAUNCH = {
     "k_merge_small": (8093892608 + 8968221440, "profiles/dram_criteo-50Mrows.md"),
 }
 TRAFFIC_SHAPE = {"rows": 50_000_000, "L": 64, "log2_buckets": 18, "reservoir": 128}
+# Warp instructions per row of the insert hash (smsp__inst_executed.sum of a
+# 2M-row ncu capture / 2M; the count per row does not depend on the table size).
+HASH_WARP_INST_PER_ROW = (1101909036 / 2_000_000, "profiles/k_hash_reg_criteo-2Mrows.md")
 
 ALGO_BYTES_DOC = {
     "k_hash_insert": "8 + 4*nnz (CSR read) + 4*L (addresses written) per row",
@@ -336,6 +339,7 @@ def main():
         evs = [step() for _ in range(args.steps)]
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+    clock_info = clk.summary()
     prof, launches1 = ix.profile_read()
     ix.profile(False)
     rc = slash.slash_sync(ix.h)
@@ -414,6 +418,15 @@ def main():
                 "frac": ach / pk["hbm_gbs"], "traffic": traffic, "traffic_source": tsrc,
                 "peak_source": pk["source"],
                 "algorithmic_bytes_per_launch": bytes_per_launch, "bytes_def": ALGO_BYTES_DOC.get(dom)}
+    if roof is not None and dom == "k_hash_insert":
+        # the kernel is issue-bound: its instruction rate against the SMs' issue peak
+        # (4 schedulers x 1 warp instruction per clock per SM, at the sampled SM clock)
+        per_row, src = HASH_WARP_INST_PER_ROW
+        mhz = clock_info.get("sm_mhz") or 2032.0
+        peak = torch.cuda.get_device_properties(local).multi_processor_count * 4 * mhz * 1e6
+        ach = per_row * rows / (kern[dom]["ms_per_launch"] / 1e3)
+        roof["issue"] = {"achieved_warp_inst_per_s": ach, "peak_warp_inst_per_s": peak, "frac": ach / peak,
+                         "warp_inst_per_row": per_row, "source": src, "sm_mhz": mhz}
     path_ins_bytes = 8 * rows + 4 * nnz + 12 * L * rows   # per-row figure of the insert path
     path_q_bytes = algo["k_query_fused"]
     out = {
@@ -436,7 +449,7 @@ def main():
         "roofline": roof,
         "kernels": kern,
         "gpu_launches": int(launches1 - launches0),
-        "clocks": clk.summary(),
+        "clocks": clock_info,
         "wall_s": wall,
     }
     if e2e:

@@ -9,17 +9,15 @@
 // largest -- id that reached it, so insertion is one order-free atomic
 // maximum per (row, table, sketch row), whatever the launch order.
 //
-// Insert: the rows' table addresses come from the hash kernels of the
-// reservoir index (launch_hash, table-major [L][n]); then k_tk_apply walks
-// the (table, bucket-range) passes in order, so that the sketches one pass
-// updates (at most ~64 MB) stay in L2 while its atomics land.  Without the
-// passes each row's L*W atomics hit random lines of the whole sketch array
-// and nearly every one misses L2.
+// Insert: the rows' table addresses (with each pair's rank in its bucket)
+// come from the hash kernels of the reservoir index; the pairs are staged by
+// sketch, and a warp per touched sketch takes each cell's maximum in shared
+// memory, so each sketch is read and written once per chunk.
 //
 // Kernels:
-//   k_tk_apply   thread per (pass, row): if the row's address in the pass's
-//                table lies in the pass's bucket range, W atomic maxima
-//                (red.global.max, evict-last) on the sketch's cells
+//   k_tk_scan_*  staging offsets of the sketches (exclusive scan of counts)
+//   k_tk_scatter thread per (row, table): the id to its sketch's staging range
+//   k_tk_merge   warp per touched sketch: cell-wise maximum, one write back
 //   k_tk_query   warp per query: DOPH + addresses, then the ordered merge of
 //                the S*L sketches (shard-major, then table) with the merged
 //                sketch in registers (lane owns cells lane + 32 i), then the
@@ -29,7 +27,6 @@
 
 #include <algorithm>
 #include <cstdint>
-#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -60,34 +57,160 @@ __device__ __forceinline__ void csr_range(const uint64_t* __restrict__ offs, uin
   }
 }
 
-constexpr uint32_t kApplyThreads = 256;
-constexpr uint32_t kApplyRowsPerThread = 8;
-constexpr uint32_t kApplyRows = kApplyThreads * kApplyRowsPerThread;  // rows per CTA and pass
+// ----------------------------------------------------------------------------- insert
+// Per chunk of rows: (1) the shared hash kernel writes the addresses [L][n]
+// with each pair's rank in its bucket in the low bits and counts the pairs per
+// bucket; (2) a scan turns the staged counts min(count, kRankCap) into offsets;
+// (3) k_tk_scatter stages every pair at offset + rank, table by table (pairs
+// whose rank field saturated -- very heavy buckets -- apply their atomic
+// maxima directly); (4) k_tk_merge gives each touched sketch to a warp, which
+// takes each cell's maximum of old word and staged ids in shared memory and
+// writes the sketch back once.  Result: the same cells as one atomic maximum
+// per (row, table, sketch row), with each sketch read and written once.
+constexpr uint32_t kScanThreads = 256;
+constexpr uint32_t kScanItems = 16;
+constexpr uint32_t kScanTile = kScanThreads * kScanItems;
+constexpr uint32_t kStageThreads = 256;
+constexpr uint32_t kStagePerThread = 8;
+constexpr uint32_t kMergeWarpsTk = 8;
 
-// Algorithm 1 with sketch buckets, after the addresses bkt[t*ldb + r] are in
-// place.  CTA x handles pass x / nrb (table t = pass / Q, bucket range
-// pass % Q of 2^B / Q buckets) and rows [(x % nrb) * kApplyRows, +kApplyRows).
-__global__ void __launch_bounds__(kApplyThreads)
-k_tk_apply(const __grid_constant__ Geo g, const TkGeo tg, const __grid_constant__ ShardMap sm,
-           const uint32_t* __restrict__ bkt, uint64_t ldb, uint32_t n, uint64_t id0, uint32_t nrb,
-           uint32_t log2q, uint32_t* __restrict__ cells) {
-  const uint32_t pass = blockIdx.x / nrb, rb = blockIdx.x - pass * nrb;
-  const uint32_t t = pass >> log2q, q = pass & ((1u << log2q) - 1u);
-  const uint32_t shift = g.B - log2q;  // bucket range = top log2q bits of the address
-  const uint32_t* col = bkt + (uint64_t)t * ldb;
-  const uint64_t keep = l2_evict_last_policy();  // the pass's sketches stay in L2
-#pragma unroll 4
-  for (uint32_t i = 0; i < kApplyRowsPerThread; ++i) {
-    const uint32_t r = rb * kApplyRows + i * kApplyThreads + threadIdx.x;
-    if (r >= n) break;
-    const uint32_t b = __ldcs(col + r);
-    if ((b >> shift) != q) continue;
-    const uint64_t id = id0 + r;
+__device__ __forceinline__ uint32_t staged_count(uint32_t c, uint32_t rcap) { return c < rcap ? c : rcap; }
+
+// blocksum[blk] = sum of the staged counts of tile blk
+__global__ void __launch_bounds__(kScanThreads)
+k_tk_scan_reduce(const uint32_t* __restrict__ cnt, uint64_t nk, uint32_t rcap, uint32_t* __restrict__ blocksum) {
+  __shared__ uint32_t wsum[kScanThreads / 32];
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
+  uint32_t v = 0;
+  for (uint32_t i = threadIdx.x; i < kScanTile; i += kScanThreads)
+    if (base + i < nk) v += staged_count(cnt[base + i], rcap);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  if ((threadIdx.x & 31u) == 0) wsum[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (uint32_t w = 0; w < kScanThreads / 32; ++w) t += wsum[w];
+    blocksum[blockIdx.x] = t;
+  }
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan_u32(uint32_t v, uint32_t lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane >= (uint32_t)o) v += u;
+  }
+  return v;
+}
+
+// exclusive scan of v over the CTA; returns the CTA total through *tot
+__device__ __forceinline__ uint32_t cta_excl_scan_u32(uint32_t v, uint32_t* wsum, uint32_t* tot) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t inc = warp_incl_scan_u32(v, lane);
+  if (lane == 31u) wsum[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t x = lane < nw ? wsum[lane] : 0u;
+    const uint32_t xi = warp_incl_scan_u32(x, lane);
+    if (lane < nw) wsum[lane] = xi - x;
+    if (lane == nw - 1u) wsum[32] = xi;
+  }
+  __syncthreads();
+  const uint32_t r = wsum[warp] + inc - v;
+  *tot = wsum[32];
+  __syncthreads();
+  return r;
+}
+
+// single CTA: blocksum -> exclusive offsets of the tiles
+__global__ void __launch_bounds__(1024) k_tk_scan_blocks(uint32_t* __restrict__ blocksum, uint32_t nblk) {
+  __shared__ uint32_t wsum[33];
+  uint32_t carry = 0;
+  for (uint32_t b0 = 0; b0 < nblk; b0 += blockDim.x) {
+    const uint32_t i = b0 + threadIdx.x;
+    const uint32_t v = i < nblk ? blocksum[i] : 0u;
+    uint32_t tot;
+    const uint32_t ex = cta_excl_scan_u32(v, wsum, &tot);
+    if (i < nblk) blocksum[i] = carry + ex;
+    carry += tot;
+  }
+}
+
+// off[key] = exclusive prefix of the staged counts
+__global__ void __launch_bounds__(kScanThreads)
+k_tk_scan_apply(const uint32_t* __restrict__ cnt, uint64_t nk, uint32_t rcap, const uint32_t* __restrict__ blocksum,
+                uint32_t* __restrict__ off) {
+  __shared__ uint32_t wsum[33];
+  const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems], sum = 0;
+#pragma unroll
+  for (uint32_t i = 0; i < kScanItems; ++i) {
+    v[i] = base + i < nk ? staged_count(cnt[base + i], rcap) : 0u;
+    sum += v[i];
+  }
+  uint32_t tot;
+  uint32_t run = blocksum[blockIdx.x] + cta_excl_scan_u32(sum, wsum, &tot);
+#pragma unroll
+  for (uint32_t i = 0; i < kScanItems; ++i) {
+    if (base + i < nk) off[base + i] = run;
+    run += v[i];
+  }
+}
+
+// Grid (x: rows, y: table): blocks run table by table, so a table's offsets and
+// its buckets' open staging lines stay in L2 (as in the reservoir index).
+__global__ void __launch_bounds__(kStageThreads)
+k_tk_scatter(const __grid_constant__ Geo g, const TkGeo tg, const __grid_constant__ ShardMap sm,
+             const uint32_t* __restrict__ bkt, uint64_t ldb, uint32_t n, uint64_t id0,
+             const uint32_t* __restrict__ off, uint32_t* __restrict__ stage, uint32_t* __restrict__ cells) {
+  const uint32_t t = blockIdx.y;
+  const uint32_t rmask = (1u << g.rbits) - 1u;  // a saturated rank field equals rmask
+  const uint64_t base = (uint64_t)blockIdx.x * (kStageThreads * kStagePerThread) + threadIdx.x;
+#pragma unroll
+  for (uint32_t k = 0; k < kStagePerThread; ++k) {
+    const uint64_t i = base + (uint64_t)k * kStageThreads;
+    if (i >= n) break;
+    const uint32_t v = __ldcs(&bkt[t * ldb + i]);
+    const uint32_t b = v >> g.rbits, rank = v & rmask;
+    const uint64_t id = id0 + i;
     const uint32_t s = g.S > 1 ? shard_of(sm, g.S, id) : 0u;
-    uint32_t* sk = cells + (((((uint64_t)s * g.L + t) << g.B) | b) * tg.WC);
-    const uint32_t word = (uint32_t)id + 1u;
-    for (uint32_t rr = 0; rr < tg.W; ++rr)
-      red_max_keep(sk + rr * tg.C + (mix32((uint32_t)id ^ g.sc[rr]) & tg.cmask), word, keep);
+    const uint64_t key = (((uint64_t)s * g.L + t) << g.B) | b;
+    if (rank < rmask) {
+      stage[(uint64_t)off[key] + rank] = (uint32_t)id;
+    } else {  // very heavy bucket: this pair updates the sketch directly
+      uint32_t* sk = cells + key * tg.WC;
+      for (uint32_t rr = 0; rr < tg.W; ++rr)
+        atomicMax(sk + rr * tg.C + (mix32((uint32_t)id ^ g.sc[rr]) & tg.cmask), (uint32_t)id + 1u);
+    }
+  }
+}
+
+// Warp per touched sketch: cell = max(cell, id + 1 of every staged id hashed
+// to it).  Clears the bucket's count for the next chunk.
+__global__ void __launch_bounds__(kMergeWarpsTk * 32)
+k_tk_merge(const __grid_constant__ Geo g, const TkGeo tg, uint64_t nk, uint32_t* __restrict__ cnt,
+           const uint32_t* __restrict__ off, const uint32_t* __restrict__ stage, uint32_t* __restrict__ cells) {
+  extern __shared__ uint32_t msk[];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  uint32_t* sw = msk + warp * tg.WC;
+  const uint32_t rcap = (1u << g.rbits) - 1u;
+  const uint64_t nwarps = (uint64_t)gridDim.x * kMergeWarpsTk;
+  for (uint64_t key = (uint64_t)blockIdx.x * kMergeWarpsTk + warp; key < nk; key += nwarps) {
+    const uint32_t c = cnt[key];
+    if (c == 0u) continue;
+    const uint32_t ns = staged_count(c, rcap), o = off[key];
+    uint32_t* sk = cells + key * tg.WC;
+    for (uint32_t j = lane; j < tg.WC; j += 32) sw[j] = sk[j];
+    __syncwarp();
+    for (uint32_t j = lane; j < ns; j += 32) {
+      const uint32_t id = __ldcs(&stage[(uint64_t)o + j]);
+      for (uint32_t rr = 0; rr < tg.W; ++rr) atomicMax(&sw[rr * tg.C + (mix32(id ^ g.sc[rr]) & tg.cmask)], id + 1u);
+    }
+    __syncwarp();
+    for (uint32_t j = lane; j < tg.WC; j += 32) sk[j] = sw[j];
+    if (lane == 0) cnt[key] = 0u;
+    __syncwarp();
   }
 }
 
@@ -240,8 +363,12 @@ struct slash_tk_index {
   uint32_t* cells = nullptr;
   uint32_t* err = nullptr;
   uint64_t launches = 0;
-  uint32_t log2q = 0;        // bucket ranges per table in an insert pass (2^log2q)
-  uint32_t* bkt = nullptr;   // insert workspace: addresses [L][ws_rows]
+  uint64_t nk = 0;               // S * L * 2^B sketches
+  uint32_t* cnt = nullptr;       // [nk] pairs per sketch in the current chunk, zero between chunks
+  uint32_t* off = nullptr;       // [nk] staging offsets
+  uint32_t* blocksum = nullptr;  // [ceil(nk / kScanTile)]
+  uint32_t* bkt = nullptr;       // insert workspace: addresses (+ ranks) [L][ws_rows]
+  uint32_t* stage = nullptr;     // insert workspace: staged ids [L * ws_rows]
   uint64_t ws_rows = 0;
 };
 
@@ -301,7 +428,8 @@ int slash_tk_build(const slash_tk_params* p, void* cuda_stream, slash_tk_index**
   Geo& g = ix->geo;
   g.dim = p->dim; g.K = p->K; g.L = p->L; g.nb = p->K * p->L; g.nw = (g.nb + 31) / 32;
   g.B = p->log2_buckets; g.R = 0; g.d = p->rows; g.w = p->cells; g.S = p->shards;
-  g.rbits = 0; g.capacity = p->capacity;
+  g.rbits = 32u - p->log2_buckets;  // insert addresses carry the pair's rank in their low bits
+  g.capacity = p->capacity;
   derive_seeds(g, p->seed, p->rows);  // the W sketch-row seeds take the count-min rows' place
   g.densify = p->densify;
   TkGeo& tg = ix->tg;
@@ -310,9 +438,15 @@ int slash_tk_build(const slash_tk_params* p, void* cuda_stream, slash_tk_index**
   const uint32_t hash_words = (g.nb + g.nw + 3u) & ~3u;
   tg.per_warp = tg.lpad + hash_words;
   if (tk_smem(ix) > ix->smem_optin) { delete ix; return SLASH_EINVAL; }
-  ix->ncells = (((uint64_t)p->shards * p->L) << p->log2_buckets) * tg.WC;
+  ix->nk = ((uint64_t)p->shards * p->L) << p->log2_buckets;
+  ix->ncells = ix->nk * tg.WC;
+  const uint64_t nblk = (ix->nk + kScanTile - 1) / kScanTile;
   cudaError_t e = cudaMalloc(&ix->cells, sizeof(uint32_t) * ix->ncells);
   if (e == cudaSuccess) e = cudaMalloc(&ix->err, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&ix->cnt, sizeof(uint32_t) * ix->nk);
+  if (e == cudaSuccess) e = cudaMalloc(&ix->off, sizeof(uint32_t) * ix->nk);
+  if (e == cudaSuccess) e = cudaMalloc(&ix->blocksum, sizeof(uint32_t) * nblk);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ix->cnt, 0, sizeof(uint32_t) * ix->nk, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ix->cells, 0, sizeof(uint32_t) * ix->ncells, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ix->err, 0, sizeof(uint32_t), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -322,19 +456,10 @@ int slash_tk_build(const slash_tk_params* p, void* cuda_stream, slash_tk_index**
     slash_tk_free(ix);
     return rc;
   }
-  {
-    // passes small enough for L2: the sketches of one (table, range) pass <= 64 MB
-    uint64_t mb = 64;
-    if (const char* env = std::getenv("SLASH_TK_PASS_MB")) {
-      const long long v = std::atoll(env);
-      if (v > 0) mb = (uint64_t)v;
-    }
-    const uint64_t per_table = ((uint64_t)p->shards << p->log2_buckets) * tg.WC * sizeof(uint32_t);
-    while (ix->log2q < p->log2_buckets && (per_table >> ix->log2q) > (mb << 20)) ++ix->log2q;
-  }
   const int so = (int)ix->smem_optin;
   init_hash_kernels(so);
   if (hash_smem_bytes(g) > ix->smem_optin) { slash_tk_free(ix); return SLASH_EINVAL; }
+  cudaFuncSetAttribute(k_tk_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_tk_query<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_tk_query<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_tk_query<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
@@ -356,30 +481,45 @@ int slash_tk_insert(slash_tk_index* ix, const uint64_t* d_offs, const uint32_t* 
   if (ix->next_id + n_rows > ix->p.capacity) return SLASH_EFULL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const ShardMap sm = make_shard_map(ix->p.shards, ix->p.capacity);
-  // rows per chunk: addresses take 4*L bytes a row; budget 16 GiB of workspace
-  const uint64_t chunk = std::min<uint64_t>(n_rows, std::max<uint64_t>(kApplyRows, (16ull << 30) / (4ull * ix->p.L)));
+  // rows per chunk: addresses and staged ids take 8*L bytes a row (budget 32 GiB),
+  // and a chunk's (row, table) pairs must have uint32 staging offsets
+  const uint64_t L = ix->p.L;
+  const uint64_t chunk = std::min<uint64_t>(n_rows, std::min<uint64_t>(0xFFFFFFFFull / L, (32ull << 30) / (8ull * L)));
   if (chunk > ix->ws_rows) {
-    uint32_t* b = nullptr;
-    if (cudaMalloc(&b, sizeof(uint32_t) * ix->p.L * chunk) != cudaSuccess) {
+    uint32_t *b = nullptr, *sg = nullptr;
+    cudaError_t e = cudaMalloc(&b, sizeof(uint32_t) * L * chunk);
+    if (e == cudaSuccess) e = cudaMalloc(&sg, sizeof(uint32_t) * L * chunk);
+    if (e != cudaSuccess) {
       cudaGetLastError();
+      cudaFree(b);
       return SLASH_ENOMEM;
     }
-    cudaFree(ix->bkt);  // (stream-ordered after earlier work: cudaFree synchronises)
+    cudaFree(ix->bkt);  // (cudaFree waits for the work still using them)
+    cudaFree(ix->stage);
     ix->bkt = b;
+    ix->stage = sg;
     ix->ws_rows = chunk;
   }
+  const uint32_t rcap = (1u << ix->geo.rbits) - 1u;
+  const uint32_t nblk = (uint32_t)((ix->nk + kScanTile - 1) / kScanTile);
+  const uint32_t mgrid = (uint32_t)std::min<uint64_t>((ix->nk + kMergeWarpsTk - 1) / kMergeWarpsTk,
+                                                      (uint64_t)std::max(ix->num_sms, 1) * 16);
+  const size_t msmem = sizeof(uint32_t) * kMergeWarpsTk * ix->tg.WC;
   const uint64_t first = ix->next_id;
   for (uint64_t r0 = 0; r0 < n_rows; r0 += chunk) {
     const uint32_t n = (uint32_t)std::min<uint64_t>(chunk, n_rows - r0);
-    int rc = launch_hash(ix->geo, sm, d_offs + r0, d_cols, n, first + r0, ix->bkt, n, nullptr, nullptr, ix->err, st);
+    int rc = launch_hash(ix->geo, sm, d_offs + r0, d_cols, n, first + r0, ix->bkt, n, nullptr, ix->cnt, ix->err, st);
     ++ix->launches;
     if (rc) return rc;
-    const uint32_t nrb = (n + kApplyRows - 1) / kApplyRows;
-    const uint64_t blocks = (uint64_t)nrb * ix->p.L << ix->log2q;
-    if (blocks >= (1ull << 31)) return SLASH_EINVAL;
-    k_tk_apply<<<(uint32_t)blocks, kApplyThreads, 0, st>>>(ix->geo, ix->tg, sm, ix->bkt, n, n, first + r0, nrb,
-                                                          ix->log2q, ix->cells);
-    ++ix->launches;
+    k_tk_scan_reduce<<<nblk, kScanThreads, 0, st>>>(ix->cnt, ix->nk, rcap, ix->blocksum);
+    k_tk_scan_blocks<<<1, 1024, 0, st>>>(ix->blocksum, nblk);
+    k_tk_scan_apply<<<nblk, kScanThreads, 0, st>>>(ix->cnt, ix->nk, rcap, ix->blocksum, ix->off);
+    const dim3 sgrid((n + kStageThreads * kStagePerThread - 1) / (kStageThreads * kStagePerThread), ix->p.L);
+    k_tk_scatter<<<sgrid, kStageThreads, 0, st>>>(ix->geo, ix->tg, sm, ix->bkt, n, n, first + r0, ix->off,
+                                                  ix->stage, ix->cells);
+    k_tk_merge<<<mgrid, kMergeWarpsTk * 32, msmem, st>>>(ix->geo, ix->tg, ix->nk, ix->cnt, ix->off, ix->stage,
+                                                         ix->cells);
+    ix->launches += 5;
     SLASH_TK_CK(cudaGetLastError());
   }
   if (first_id_out) *first_id_out = first;
@@ -506,6 +646,10 @@ int slash_tk_free(slash_tk_index* ix) {
   int rc = SLASH_OK;
   if (ix->cells && cudaFree(ix->cells) != cudaSuccess) rc = SLASH_ECUDA;
   if (ix->bkt && cudaFree(ix->bkt) != cudaSuccess) rc = SLASH_ECUDA;
+  if (ix->stage && cudaFree(ix->stage) != cudaSuccess) rc = SLASH_ECUDA;
+  if (ix->cnt && cudaFree(ix->cnt) != cudaSuccess) rc = SLASH_ECUDA;
+  if (ix->off && cudaFree(ix->off) != cudaSuccess) rc = SLASH_ECUDA;
+  if (ix->blocksum && cudaFree(ix->blocksum) != cudaSuccess) rc = SLASH_ECUDA;
   if (ix->err && cudaFree(ix->err) != cudaSuccess) rc = SLASH_ECUDA;
   delete ix;
   return rc;
