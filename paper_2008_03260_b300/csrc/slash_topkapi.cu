@@ -60,13 +60,12 @@ __device__ __forceinline__ void csr_range(const uint64_t* __restrict__ offs, uin
 // ----------------------------------------------------------------------------- insert
 // Per chunk of rows: (1) the shared hash kernel writes the addresses [L][n]
 // with each pair's rank in its bucket in the low bits and counts the pairs per
-// bucket; (2) a scan turns the staged counts min(count, kRankCap) into offsets;
-// (3) k_tk_scatter stages every pair at offset + rank, table by table (pairs
-// whose rank field saturated -- very heavy buckets -- apply their atomic
-// maxima directly); (4) k_tk_merge gives each touched sketch to a warp, which
-// takes each cell's maximum of old word and staged ids in shared memory and
-// writes the sketch back once.  Result: the same cells as one atomic maximum
-// per (row, table, sketch row), with each sketch read and written once.
+// bucket; (2) a scan turns the counts into staging offsets; (3) k_tk_scatter
+// stages every pair at offset + rank, table by table; (4) k_tk_merge gives each
+// touched sketch to a warp, which takes each cell's maximum of old word and
+// staged ids in shared memory and writes the sketch back once (k_tk_merge_big
+// splits very large sketches over many warps).  Result: the same cells as one
+// atomic maximum per (row, table, sketch row).
 constexpr uint32_t kScanThreads = 256;
 constexpr uint32_t kScanItems = 16;
 constexpr uint32_t kScanTile = kScanThreads * kScanItems;
@@ -74,16 +73,14 @@ constexpr uint32_t kStageThreads = 256;
 constexpr uint32_t kStagePerThread = 8;
 constexpr uint32_t kMergeWarpsTk = 8;
 
-__device__ __forceinline__ uint32_t staged_count(uint32_t c, uint32_t rcap) { return c < rcap ? c : rcap; }
-
-// blocksum[blk] = sum of the staged counts of tile blk
+// blocksum[blk] = sum of the counts of tile blk
 __global__ void __launch_bounds__(kScanThreads)
-k_tk_scan_reduce(const uint32_t* __restrict__ cnt, uint64_t nk, uint32_t rcap, uint32_t* __restrict__ blocksum) {
+k_tk_scan_reduce(const uint32_t* __restrict__ cnt, uint64_t nk, uint32_t* __restrict__ blocksum) {
   __shared__ uint32_t wsum[kScanThreads / 32];
   const uint64_t base = (uint64_t)blockIdx.x * kScanTile;
   uint32_t v = 0;
   for (uint32_t i = threadIdx.x; i < kScanTile; i += kScanThreads)
-    if (base + i < nk) v += staged_count(cnt[base + i], rcap);
+    if (base + i < nk) v += cnt[base + i];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
   if ((threadIdx.x & 31u) == 0) wsum[threadIdx.x >> 5] = v;
@@ -137,16 +134,16 @@ __global__ void __launch_bounds__(1024) k_tk_scan_blocks(uint32_t* __restrict__ 
   }
 }
 
-// off[key] = exclusive prefix of the staged counts
+// off[key] = exclusive prefix of the counts
 __global__ void __launch_bounds__(kScanThreads)
-k_tk_scan_apply(const uint32_t* __restrict__ cnt, uint64_t nk, uint32_t rcap, const uint32_t* __restrict__ blocksum,
+k_tk_scan_apply(const uint32_t* __restrict__ cnt, uint64_t nk, const uint32_t* __restrict__ blocksum,
                 uint32_t* __restrict__ off) {
   __shared__ uint32_t wsum[33];
   const uint64_t base = (uint64_t)blockIdx.x * kScanTile + (uint64_t)threadIdx.x * kScanItems;
   uint32_t v[kScanItems], sum = 0;
 #pragma unroll
   for (uint32_t i = 0; i < kScanItems; ++i) {
-    v[i] = base + i < nk ? staged_count(cnt[base + i], rcap) : 0u;
+    v[i] = base + i < nk ? cnt[base + i] : 0u;
     sum += v[i];
   }
   uint32_t tot;
@@ -159,57 +156,112 @@ k_tk_scan_apply(const uint32_t* __restrict__ cnt, uint64_t nk, uint32_t rcap, co
 }
 
 // Grid (x: rows, y: table): blocks run table by table, so a table's offsets and
-// its buckets' open staging lines stay in L2 (as in the reservoir index).
+// its buckets' open staging lines stay in L2 (as in the reservoir index).  A
+// pair stages at offset + rank; a pair whose rank field saturated (ranks >=
+// rmask: heavy buckets only) takes a slot past rmask from the bucket's cursor,
+// one atomic per group of lanes that share the bucket.
 __global__ void __launch_bounds__(kStageThreads)
-k_tk_scatter(const __grid_constant__ Geo g, const TkGeo tg, const __grid_constant__ ShardMap sm,
-             const uint32_t* __restrict__ bkt, uint64_t ldb, uint32_t n, uint64_t id0,
-             const uint32_t* __restrict__ off, uint32_t* __restrict__ stage, uint32_t* __restrict__ cells) {
-  const uint32_t t = blockIdx.y;
+k_tk_scatter(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm, const uint32_t* __restrict__ bkt,
+             uint64_t ldb, uint32_t n, uint64_t id0, const uint32_t* __restrict__ off, uint32_t* __restrict__ cur,
+             uint32_t* __restrict__ stage) {
+  const uint32_t t = blockIdx.y, lane = threadIdx.x & 31u;
   const uint32_t rmask = (1u << g.rbits) - 1u;  // a saturated rank field equals rmask
   const uint64_t base = (uint64_t)blockIdx.x * (kStageThreads * kStagePerThread) + threadIdx.x;
 #pragma unroll
   for (uint32_t k = 0; k < kStagePerThread; ++k) {
     const uint64_t i = base + (uint64_t)k * kStageThreads;
-    if (i >= n) break;
-    const uint32_t v = __ldcs(&bkt[t * ldb + i]);
+    const bool valid = i < n;  // (no early exit: the warp stays converged for the cursor step)
+    const uint32_t v = valid ? __ldcs(&bkt[t * ldb + i]) : 0u;
     const uint32_t b = v >> g.rbits, rank = v & rmask;
     const uint64_t id = id0 + i;
-    const uint32_t s = g.S > 1 ? shard_of(sm, g.S, id) : 0u;
+    const uint32_t s = (valid && g.S > 1) ? shard_of(sm, g.S, id) : 0u;
     const uint64_t key = (((uint64_t)s * g.L + t) << g.B) | b;
-    if (rank < rmask) {
-      stage[(uint64_t)off[key] + rank] = (uint32_t)id;
-    } else {  // very heavy bucket: this pair updates the sketch directly
-      uint32_t* sk = cells + key * tg.WC;
-      for (uint32_t rr = 0; rr < tg.W; ++rr)
-        atomicMax(sk + rr * tg.C + (mix32((uint32_t)id ^ g.sc[rr]) & tg.cmask), (uint32_t)id + 1u);
+    const bool over = valid && rank == rmask;
+    uint32_t slot = rank;
+    if (__ballot_sync(0xFFFFFFFFu, over)) {
+      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, over ? (uint32_t)key : 0xFFFFFFFFu);
+      const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
+      uint32_t first = 0u;
+      if (over && lane == leader) first = atomicAdd(&cur[key], (uint32_t)__popc(peers));
+      first = __shfl_sync(0xFFFFFFFFu, first, leader);
+      if (over) slot = rmask + first + (uint32_t)__popc(peers & ((1u << lane) - 1u));
     }
+    if (valid) stage[(uint64_t)off[key] + slot] = (uint32_t)id;
   }
 }
 
-// Warp per touched sketch: cell = max(cell, id + 1 of every staged id hashed
-// to it).  Clears the bucket's count for the next chunk.
+// Warp per touched sketch with at most kMergeCap staged ids: cell = max(cell,
+// id + 1 of every staged id hashed to it), one read and one write of the
+// sketch.  A larger sketch is cut into slices of kMergeCap staged ids, each a
+// task (key, first staged index, length) in `big` for k_tk_merge_big.  Clears
+// the bucket's count and cursor for the next chunk.
+constexpr uint32_t kMergeCap = 4096;
+
 __global__ void __launch_bounds__(kMergeWarpsTk * 32)
 k_tk_merge(const __grid_constant__ Geo g, const TkGeo tg, uint64_t nk, uint32_t* __restrict__ cnt,
-           const uint32_t* __restrict__ off, const uint32_t* __restrict__ stage, uint32_t* __restrict__ cells) {
+           uint32_t* __restrict__ cur, const uint32_t* __restrict__ off, const uint32_t* __restrict__ stage,
+           uint32_t* __restrict__ cells, uint32_t* __restrict__ big, uint32_t* __restrict__ nbig) {
   extern __shared__ uint32_t msk[];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   uint32_t* sw = msk + warp * tg.WC;
-  const uint32_t rcap = (1u << g.rbits) - 1u;
+  const uint32_t rmask = (1u << g.rbits) - 1u;
   const uint64_t nwarps = (uint64_t)gridDim.x * kMergeWarpsTk;
   for (uint64_t key = (uint64_t)blockIdx.x * kMergeWarpsTk + warp; key < nk; key += nwarps) {
     const uint32_t c = cnt[key];
     if (c == 0u) continue;
-    const uint32_t ns = staged_count(c, rcap), o = off[key];
+    const uint32_t o = off[key];
+    if (lane == 0) {
+      cnt[key] = 0u;
+      if (c > rmask) cur[key] = 0u;
+    }
+    if (c > kMergeCap) {
+      const uint32_t nsl = (c + kMergeCap - 1u) / kMergeCap;
+      uint32_t first = 0u;
+      if (lane == 0) first = atomicAdd(nbig, nsl);
+      first = __shfl_sync(0xFFFFFFFFu, first, 0);
+      for (uint32_t sl = lane; sl < nsl; sl += 32) {
+        big[3 * (first + sl)] = (uint32_t)key;
+        big[3 * (first + sl) + 1] = o + sl * kMergeCap;
+        big[3 * (first + sl) + 2] = min(kMergeCap, c - sl * kMergeCap);
+      }
+      continue;
+    }
     uint32_t* sk = cells + key * tg.WC;
     for (uint32_t j = lane; j < tg.WC; j += 32) sw[j] = sk[j];
     __syncwarp();
-    for (uint32_t j = lane; j < ns; j += 32) {
+    for (uint32_t j = lane; j < c; j += 32) {
       const uint32_t id = __ldcs(&stage[(uint64_t)o + j]);
       for (uint32_t rr = 0; rr < tg.W; ++rr) atomicMax(&sw[rr * tg.C + (mix32(id ^ g.sc[rr]) & tg.cmask)], id + 1u);
     }
     __syncwarp();
     for (uint32_t j = lane; j < tg.WC; j += 32) sk[j] = sw[j];
-    if (lane == 0) cnt[key] = 0u;
+    __syncwarp();
+  }
+}
+
+// The slices of the large sketches, one per warp at a time: a warp takes its
+// slice's cell maxima in shared memory and applies the non-empty ones with
+// atomic maxima (a sketch's slices land in any order).
+__global__ void __launch_bounds__(kMergeWarpsTk * 32)
+k_tk_merge_big(const __grid_constant__ Geo g, const TkGeo tg, const uint32_t* __restrict__ big,
+               const uint32_t* __restrict__ nbig, const uint32_t* __restrict__ stage, uint32_t* __restrict__ cells) {
+  extern __shared__ uint32_t msk[];
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  uint32_t* sw = msk + warp * tg.WC;
+  const uint32_t nw = gridDim.x * kMergeWarpsTk, ntask = *nbig;
+  for (uint32_t task = blockIdx.x * kMergeWarpsTk + warp; task < ntask; task += nw) {
+    const uint64_t key = big[3 * task];
+    const uint32_t lo = big[3 * task + 1], len = big[3 * task + 2];
+    for (uint32_t j = lane; j < tg.WC; j += 32) sw[j] = 0u;
+    __syncwarp();
+    for (uint32_t j = lane; j < len; j += 32) {
+      const uint32_t id = __ldcs(&stage[(uint64_t)lo + j]);
+      for (uint32_t rr = 0; rr < tg.W; ++rr) atomicMax(&sw[rr * tg.C + (mix32(id ^ g.sc[rr]) & tg.cmask)], id + 1u);
+    }
+    __syncwarp();
+    uint32_t* sk = cells + key * tg.WC;
+    for (uint32_t j = lane; j < tg.WC; j += 32)
+      if (sw[j]) atomicMax(sk + j, sw[j]);
     __syncwarp();
   }
 }
@@ -367,8 +419,11 @@ struct slash_tk_index {
   uint32_t* cnt = nullptr;       // [nk] pairs per sketch in the current chunk, zero between chunks
   uint32_t* off = nullptr;       // [nk] staging offsets
   uint32_t* blocksum = nullptr;  // [ceil(nk / kScanTile)]
+  uint32_t* cur = nullptr;       // [nk] staging cursors past the rank field's range (heavy buckets), zero between chunks
+  uint32_t* nbig = nullptr;      // [1] tasks in `big`
   uint32_t* bkt = nullptr;       // insert workspace: addresses (+ ranks) [L][ws_rows]
   uint32_t* stage = nullptr;     // insert workspace: staged ids [L * ws_rows]
+  uint32_t* big = nullptr;       // insert workspace: slices (key, first staged index, length) of large sketches
   uint64_t ws_rows = 0;
 };
 
@@ -446,7 +501,10 @@ int slash_tk_build(const slash_tk_params* p, void* cuda_stream, slash_tk_index**
   if (e == cudaSuccess) e = cudaMalloc(&ix->cnt, sizeof(uint32_t) * ix->nk);
   if (e == cudaSuccess) e = cudaMalloc(&ix->off, sizeof(uint32_t) * ix->nk);
   if (e == cudaSuccess) e = cudaMalloc(&ix->blocksum, sizeof(uint32_t) * nblk);
+  if (e == cudaSuccess) e = cudaMalloc(&ix->cur, sizeof(uint32_t) * ix->nk);
+  if (e == cudaSuccess) e = cudaMalloc(&ix->nbig, sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemsetAsync(ix->cnt, 0, sizeof(uint32_t) * ix->nk, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ix->cur, 0, sizeof(uint32_t) * ix->nk, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ix->cells, 0, sizeof(uint32_t) * ix->ncells, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(ix->err, 0, sizeof(uint32_t), st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -460,6 +518,7 @@ int slash_tk_build(const slash_tk_params* p, void* cuda_stream, slash_tk_index**
   init_hash_kernels(so);
   if (hash_smem_bytes(g) > ix->smem_optin) { slash_tk_free(ix); return SLASH_EINVAL; }
   cudaFuncSetAttribute(k_tk_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_tk_merge_big, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_tk_query<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_tk_query<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_tk_query<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
@@ -486,21 +545,26 @@ int slash_tk_insert(slash_tk_index* ix, const uint64_t* d_offs, const uint32_t* 
   const uint64_t L = ix->p.L;
   const uint64_t chunk = std::min<uint64_t>(n_rows, std::min<uint64_t>(0xFFFFFFFFull / L, (32ull << 30) / (8ull * L)));
   if (chunk > ix->ws_rows) {
-    uint32_t *b = nullptr, *sg = nullptr;
+    uint32_t *b = nullptr, *sg = nullptr, *bg = nullptr;
     cudaError_t e = cudaMalloc(&b, sizeof(uint32_t) * L * chunk);
     if (e == cudaSuccess) e = cudaMalloc(&sg, sizeof(uint32_t) * L * chunk);
+    // slices of the sketches with more than kMergeCap of the chunk's pairs: each is at
+    // least half full but the last, so at most 2 * pairs / kMergeCap of them
+    if (e == cudaSuccess) e = cudaMalloc(&bg, sizeof(uint32_t) * 3 * (2 * L * chunk / kMergeCap + 1));
     if (e != cudaSuccess) {
       cudaGetLastError();
       cudaFree(b);
+      cudaFree(sg);
       return SLASH_ENOMEM;
     }
     cudaFree(ix->bkt);  // (cudaFree waits for the work still using them)
     cudaFree(ix->stage);
+    cudaFree(ix->big);
     ix->bkt = b;
     ix->stage = sg;
+    ix->big = bg;
     ix->ws_rows = chunk;
   }
-  const uint32_t rcap = (1u << ix->geo.rbits) - 1u;
   const uint32_t nblk = (uint32_t)((ix->nk + kScanTile - 1) / kScanTile);
   const uint32_t mgrid = (uint32_t)std::min<uint64_t>((ix->nk + kMergeWarpsTk - 1) / kMergeWarpsTk,
                                                       (uint64_t)std::max(ix->num_sms, 1) * 16);
@@ -511,15 +575,18 @@ int slash_tk_insert(slash_tk_index* ix, const uint64_t* d_offs, const uint32_t* 
     int rc = launch_hash(ix->geo, sm, d_offs + r0, d_cols, n, first + r0, ix->bkt, n, nullptr, ix->cnt, ix->err, st);
     ++ix->launches;
     if (rc) return rc;
-    k_tk_scan_reduce<<<nblk, kScanThreads, 0, st>>>(ix->cnt, ix->nk, rcap, ix->blocksum);
+    k_tk_scan_reduce<<<nblk, kScanThreads, 0, st>>>(ix->cnt, ix->nk, ix->blocksum);
     k_tk_scan_blocks<<<1, 1024, 0, st>>>(ix->blocksum, nblk);
-    k_tk_scan_apply<<<nblk, kScanThreads, 0, st>>>(ix->cnt, ix->nk, rcap, ix->blocksum, ix->off);
+    k_tk_scan_apply<<<nblk, kScanThreads, 0, st>>>(ix->cnt, ix->nk, ix->blocksum, ix->off);
     const dim3 sgrid((n + kStageThreads * kStagePerThread - 1) / (kStageThreads * kStagePerThread), ix->p.L);
-    k_tk_scatter<<<sgrid, kStageThreads, 0, st>>>(ix->geo, ix->tg, sm, ix->bkt, n, n, first + r0, ix->off,
-                                                  ix->stage, ix->cells);
-    k_tk_merge<<<mgrid, kMergeWarpsTk * 32, msmem, st>>>(ix->geo, ix->tg, ix->nk, ix->cnt, ix->off, ix->stage,
-                                                         ix->cells);
-    ix->launches += 5;
+    k_tk_scatter<<<sgrid, kStageThreads, 0, st>>>(ix->geo, sm, ix->bkt, n, n, first + r0, ix->off, ix->cur,
+                                                  ix->stage);
+    SLASH_TK_CK(cudaMemsetAsync(ix->nbig, 0, sizeof(uint32_t), st));
+    k_tk_merge<<<mgrid, kMergeWarpsTk * 32, msmem, st>>>(ix->geo, ix->tg, ix->nk, ix->cnt, ix->cur, ix->off,
+                                                         ix->stage, ix->cells, ix->big, ix->nbig);
+    k_tk_merge_big<<<(uint32_t)std::max(ix->num_sms, 1) * 4, kMergeWarpsTk * 32, msmem, st>>>(
+        ix->geo, ix->tg, ix->big, ix->nbig, ix->stage, ix->cells);
+    ix->launches += 6;
     SLASH_TK_CK(cudaGetLastError());
   }
   if (first_id_out) *first_id_out = first;
@@ -650,6 +717,9 @@ int slash_tk_free(slash_tk_index* ix) {
   if (ix->cnt && cudaFree(ix->cnt) != cudaSuccess) rc = SLASH_ECUDA;
   if (ix->off && cudaFree(ix->off) != cudaSuccess) rc = SLASH_ECUDA;
   if (ix->blocksum && cudaFree(ix->blocksum) != cudaSuccess) rc = SLASH_ECUDA;
+  if (ix->cur && cudaFree(ix->cur) != cudaSuccess) rc = SLASH_ECUDA;
+  if (ix->nbig && cudaFree(ix->nbig) != cudaSuccess) rc = SLASH_ECUDA;
+  if (ix->big && cudaFree(ix->big) != cudaSuccess) rc = SLASH_ECUDA;
   if (ix->err && cudaFree(ix->err) != cudaSuccess) rc = SLASH_ECUDA;
   delete ix;
   return rc;
