@@ -245,6 +245,7 @@ def main():
     ap.add_argument("--log2-buckets", type=int, default=0, help="override (small profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--schedule", default="", help="query schedule without autotuning, e.g. plain:1024")
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-max-requests", type=int, default=20_000)
     ap.add_argument("--no-e2e", action="store_true")
@@ -300,6 +301,11 @@ def main():
     ix = slash.Index(p)
     st = torch.cuda.current_stream()
 
+    sched = {}
+    if args.schedule:  # a fixed schedule (profiling runs) instead of the index default / autotuner
+        mode, thr = args.schedule.split(":")
+        sched = {"mode": mode, "threads": int(thr)}
+
     def step():
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record(st)
@@ -307,7 +313,7 @@ def main():
         ev[1].record(st)
         ix.insert(d_offs, d_cols, st)
         ev[2].record(st)
-        ix.query(d_qo, d_qc, w.topk, st, d_ids_out=d_ids, d_scores_out=d_sc)
+        ix.query(d_qo, d_qc, w.topk, st, d_ids_out=d_ids, d_scores_out=d_sc, **sched)
         ev[3].record(st)
         return ev
 
