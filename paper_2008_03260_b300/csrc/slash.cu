@@ -64,7 +64,7 @@ using namespace slash;
 namespace {
 
 constexpr int kHashWarps = 8;
-constexpr int kRowsPerWarp = 4;
+constexpr int kRowsPerWarp = 8;
 constexpr int kHashRows = kHashWarps * kRowsPerWarp;  // rows per CTA
 // The CTA's address tile is [L][kTileStride]: a lane writes its tables' entries
 // of one row, i.e. a column of the tile; the odd stride puts them in different
@@ -414,7 +414,7 @@ k_scatter(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
 }
 
 // ----------------------------------------------------------------------------- insert: merge
-constexpr int kMergeWarps = 8;
+constexpr int kMergeWarps = 16;
 constexpr uint32_t kSmallMax = 1024;  // most candidates a warp merges in smem (buffer size is per index)
 constexpr uint32_t kInvMul2 = 0x7ED1B41Du;  // 0xC2B2AE35^-1 mod 2^31
 constexpr uint32_t kInvMul1 = 0x25CB9243u;  // 0x85EBCA6B^-1 mod 2^31
