@@ -213,14 +213,14 @@ def config_of(w, args) -> dict:
 # unchanged kernels, measured by ncu (one-pass metrics) on this full-size
 # workload: 50M rows, 64 tables, 2^18 buckets (see profiles/).
 TRAFFIC_PER_LAUNCH = {
-    "k_hash_insert": (9701348608 + 13646447104, "profiles/dram_criteo-50Mrows.md"),
-    "k_scatter": (18967860480 + 13676890880, "profiles/dram_criteo-50Mrows.md"),
-    "k_merge_small": (8093892608 + 8968221440, "profiles/dram_criteo-50Mrows.md"),
+    "k_hash_insert": (9654329344 + 13679100928, "profiles/dram_criteo-50Mrows.md"),
+    "k_scatter": (18967236096 + 13676748800, "profiles/dram_criteo-50Mrows.md"),
+    "k_merge_small": (7899732224 + 8946798080, "profiles/dram_criteo-50Mrows.md"),
 }
 TRAFFIC_SHAPE = {"rows": 50_000_000, "L": 64, "log2_buckets": 18, "reservoir": 128}
 # Warp instructions per row of the insert hash (smsp__inst_executed.sum of a
 # 2M-row ncu capture / 2M; the count per row does not depend on the table size).
-HASH_WARP_INST_PER_ROW = (1102909036 / 2_000_000, "profiles/k_hash_reg_criteo-2Mrows.md")
+HASH_WARP_INST_PER_ROW = (1094409036 / 2_000_000, "profiles/k_hash_reg_criteo-2Mrows.md")
 
 ALGO_BYTES_DOC = {
     "k_hash_insert": "8 + 4*nnz (CSR read) + 4*L (addresses written) per row",
