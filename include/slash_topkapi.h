@@ -20,8 +20,9 @@
  *     Ids are unique, so an arriving id never matches: every non-empty cell of
  *     a bucket holds count 1 and the LAST id that reached it, and ids arrive in
  *     ascending order -- so a cell holds the largest id hashed to it.  The
- *     library stores that id + 1 (0 = empty) and inserts with an order-free
- *     atomic maximum; the cell's state equals the sequential rule's exactly.
+ *     library stores that id + 1 (0 = empty) and takes, per cell, the maximum
+ *     over the ids hashed to it -- order-free, so any parallel schedule gives
+ *     the sequential rule's state exactly.
  *   - Merge (Appendix 2, "Merging"): same heavy hitter -> counts add; else the
  *     larger count wins with the difference; equal counts leave an empty cell.
  *     The merge depends on order: a query folds shard-major, then table order.
@@ -66,9 +67,11 @@ int slash_tk_build(const slash_tk_params *p, void *cuda_stream, slash_tk_index *
 
 /* Pre-processing (Algorithm 1): rows get ids [*first_id_out, +n_rows) in order;
  * each id is inserted into one sketch per table of shard floor(id*S/capacity).
- * One launch; results do not depend on how rows are split into calls.
+ * Results do not depend on how rows are split into calls.  Uses per-index
+ * workspace grown on demand (addresses and staged ids, 8*L bytes per row of a
+ * chunk of up to (2^32-1)/L rows), so one insert at a time per index.
  * n_rows = 0 is a no-op.  Errors: SLASH_EINVAL (NULL pointers with n_rows > 0),
- * SLASH_EFULL, SLASH_ECUDA. */
+ * SLASH_EFULL, SLASH_ENOMEM (workspace growth), SLASH_ECUDA. */
 int slash_tk_insert(slash_tk_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n_rows,
                     uint64_t *first_id_out, void *cuda_stream);
 
