@@ -211,16 +211,17 @@ def config_of(w, args) -> dict:
 # ----------------------------------------------------------------------------- GPU arm
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # unchanged kernels, measured by ncu (one-pass metrics) on this full-size
-# workload: 50M rows, 64 tables, 2^18 buckets (see profiles/).
+# workload: 50M rows, 64 tables, 2^18 buckets.
 TRAFFIC_PER_LAUNCH = {
-    "k_hash_insert": (9654329344 + 13679100928, "profiles/dram_criteo-50Mrows.md"),
-    "k_scatter": (18967236096 + 13676748800, "profiles/dram_criteo-50Mrows.md"),
-    "k_merge_small": (7899732224 + 8946798080, "profiles/dram_criteo-50Mrows.md"),
+    "k_hash_insert": (9654329344 + 13679100928, "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel, full-size criteo insert, one-pass metrics"),
+    "k_scatter": (18967236096 + 13676748800, "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel, full-size criteo insert, one-pass metrics"),
+    "k_merge_small": (7899732224 + 8946798080, "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel, full-size criteo insert, one-pass metrics"),
 }
 TRAFFIC_SHAPE = {"rows": 50_000_000, "L": 64, "log2_buckets": 18, "reservoir": 128}
 # Warp instructions per row of the insert hash (smsp__inst_executed.sum of a
 # 2M-row ncu capture / 2M; the count per row does not depend on the table size).
-HASH_WARP_INST_PER_ROW = (1094409036 / 2_000_000, "profiles/k_hash_reg_criteo-2Mrows.md")
+HASH_WARP_INST_PER_ROW = (1094409036 / 2_000_000, "ncu smsp__inst_executed.sum of k_hash_reg<12, 6, 1> on 2M "
+                                                   "criteo-shaped rows (2^14 buckets) / 2M")
 
 ALGO_BYTES_DOC = {
     "k_hash_insert": "8 + 4*nnz (CSR read) + 4*L (addresses written) per row",
@@ -419,7 +420,7 @@ def main():
         shape = {"rows": rows, "L": L, "log2_buckets": w.log2_buckets, "reservoir": w.reservoir}
         if dom in TRAFFIC_PER_LAUNCH and shape == TRAFFIC_SHAPE and launches_per_step == 1:
             traffic, src = TRAFFIC_PER_LAUNCH[dom]
-            tsrc = f"{src}: ncu DRAM bytes of this kernel on this workload (one-pass metrics)"
+            tsrc = src
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / pk["hbm_gbs"], "traffic": traffic, "traffic_source": tsrc,
                 "peak_source": pk["source"],
