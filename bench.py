@@ -160,7 +160,7 @@ def run_reference(args, w: workloads.Workload) -> None:
         return
     import oracle
     tk = "tk_rows" in w.extra
-    per_step = 30_000 if w.L >= 32 else 150_000
+    per_step = min(w.n_rows, 30_000 if w.L >= 32 else 150_000)  # a step's sample fits the index
     total = per_step * (args.steps + args.warmup)
     g = datagen.Generator(dim_bits=w.dim_bits)
     offs, cols = g.rows(w.seed, 0, total, lo=w.nnz_lo, hi=w.nnz_hi)
