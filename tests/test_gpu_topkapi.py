@@ -103,3 +103,41 @@ def test_sketch_errors():
         assert ids.numel() == 0
         with pytest.raises(s.SlashError):
             ix.query(_dev(offs), _dev(cols), 0)
+
+
+def test_heavy_sketch_paths():
+    """12,000 copies of one row land in one sketch per table: with 2^24 sketches
+    per table the rank field holds 255, so most copies take cursor slots, and
+    the sketch's 12,000 staged ids go through the sliced merge.  Checked on the
+    heavy sketches and on every sketch of 100 queries, against a partial oracle."""
+    s = _s()
+    g = datagen.Generator()
+    base_o, base_c = g.rows(9, 0, 3000)
+    rows = [base_c[int(base_o[i]):int(base_o[i + 1])] for i in range(3000)]
+    heavy = rows[0]
+    mixed = []
+    for i in range(3000):
+        mixed.append(rows[i])
+        mixed.extend([heavy] * 4)
+    offs, cols = _csr(mixed)
+    n = len(offs) - 1
+    K, L, B, W, C = 2, 2, 24, 2, 8
+    qo, qc, _ = g.queries(9, 10, 100, 3000)
+    _, qbk = oracle.hash_rows(K, L, B, 3, W, qo, qc, want_codes=False)
+    _, hbk = oracle.hash_rows(K, L, B, 3, W, offs[:2], cols[:int(offs[1])], want_codes=False)
+    rt = np.concatenate([np.tile(np.arange(L), 100), np.arange(L)]).astype(np.uint32)
+    rb = np.concatenate([qbk.ravel(), hbk.ravel()]).astype(np.uint32)
+    p = s.TkParams(K=K, L=L, log2_buckets=B, rows=W, cells=C, seed=3, capacity=n)
+    with s.TkIndex(p) as ix:
+        ix.insert(_dev(offs), _dev(cols))
+        ids, sc = ix.query(_dev(qo), _dev(qc), 10)
+        ix.sync()
+        got = ix.buckets(np.zeros_like(rt), rt, rb)
+    ox = oracle.TkIndex(K=K, L=L, log2_buckets=B, rows=W, cells=C, seed=3, capacity=n, partial=(rt, rb))
+    ox.insert(offs, cols, threads=4)
+    for i in range(len(rt)):
+        cells = ox.bucket(int(rt[i]), int(rb[i]))
+        assert np.array_equal(got[i], np.where(cells[..., 1] > 0, cells[..., 0] + 1, 0).astype(np.uint32)), i
+    eids, esc = ox.query(qo, qc, 10)
+    assert np.array_equal(ids.cpu().numpy(), eids)
+    assert np.array_equal(_host_u32(sc), esc)
