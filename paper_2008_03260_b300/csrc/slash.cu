@@ -791,6 +791,8 @@ __device__ __forceinline__ uint32_t estimate(const Geo& g, const uint32_t* cmw, 
 //     finds that id bound;
 //  4. the pool is sorted by (estimate desc, id asc) and the first k distinct
 //     keys are written (duplicates of an id share its key and are adjacent).
+constexpr uint32_t kLocalTop = 10;  // per-lane register list of the one-pass top-k (k <= 16)
+
 __device__ void query_core(const Geo& g, const QueryLayout& lay, unsigned char* qsm,
                            const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill,
                            uint32_t k, int32_t* __restrict__ ids_out, uint32_t* __restrict__ scores_out,
@@ -994,6 +996,52 @@ __device__ void query_core(const Geo& g, const QueryLayout& lay, unsigned char* 
   }
   __syncthreads();
   const uint32_t P = ctrl[C_NPOOL];  // <= occurrences <= maxm <= npool
+  if (k <= kLocalTop && P > 64u) {
+    // k <= 16: in one pass over the pool each lane of warp 0 keeps its 16
+    // smallest distinct keys, sorted, in registers; then k rounds take the
+    // warp minimum of the lanes' heads, and every lane holding that key pops it
+    // (a key is one id at its estimate: equal keys are the same id)
+    if (warp == 0) {
+      uint64_t loc[kLocalTop];
+#pragma unroll
+      for (int t = 0; t < (int)kLocalTop; ++t) loc[t] = ~0ull;
+      for (uint32_t i = lane; i < P; i += 32) {
+        const uint64_t key = pool[i];
+        if (key >= loc[kLocalTop - 1]) continue;
+        bool dup = false;
+#pragma unroll
+        for (int t = 0; t < (int)kLocalTop; ++t) dup |= loc[t] == key;
+        if (dup) continue;
+#pragma unroll
+        for (int t = (int)kLocalTop - 1; t > 0; --t) loc[t] = loc[t - 1] > key ? loc[t - 1] : (loc[t] > key ? key : loc[t]);
+        loc[0] = loc[0] > key ? key : loc[0];
+      }
+      for (uint32_t j = 0; j < k; ++j) {
+        uint64_t best = loc[0];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const uint64_t other = __shfl_xor_sync(0xFFFFFFFFu, best, o);
+          best = other < best ? other : best;
+        }
+        if (lane == 0) {
+          if (best != ~0ull) {
+            ids_out[j] = (int32_t)(uint32_t)best;
+            scores_out[j] = 0xFFFFu - (uint32_t)(best >> 32);
+          } else {
+            ids_out[j] = -1;
+            scores_out[j] = 0u;
+          }
+        }
+        if (best != ~0ull && loc[0] == best) {
+#pragma unroll
+          for (int t = 0; t < (int)kLocalTop - 1; ++t) loc[t] = loc[t + 1];
+          loc[kLocalTop - 1] = ~0ull;
+        }
+      }
+    }
+    __syncthreads();
+    return;
+  }
   if ((uint64_t)k * ((P + 31u) / 32u) <= 512u) {
     // small pool: warp 0 picks the k smallest distinct keys by repeated minimum
     // (a key equal to the last one picked is a duplicate of the same id: skipped)
