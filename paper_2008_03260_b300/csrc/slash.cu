@@ -791,7 +791,7 @@ __device__ __forceinline__ uint32_t estimate(const Geo& g, const uint32_t* cmw, 
 //     finds that id bound;
 //  4. the pool is sorted by (estimate desc, id asc) and the first k distinct
 //     keys are written (duplicates of an id share its key and are adjacent).
-constexpr uint32_t kLocalTop = 10;  // per-lane register list of the one-pass top-k (k <= 16)
+constexpr uint32_t kLocalTop = 10;  // per-lane register list of the one-pass top-k (k <= 10; more spills at 1024 threads)
 
 __device__ void query_core(const Geo& g, const QueryLayout& lay, unsigned char* qsm,
                            const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill,
@@ -997,7 +997,7 @@ __device__ void query_core(const Geo& g, const QueryLayout& lay, unsigned char* 
   __syncthreads();
   const uint32_t P = ctrl[C_NPOOL];  // <= occurrences <= maxm <= npool
   if (k <= kLocalTop && P > 64u) {
-    // k <= 16: in one pass over the pool each lane of warp 0 keeps its 16
+    // k <= kLocalTop: in one pass over the pool each lane of warp 0 keeps its kLocalTop
     // smallest distinct keys, sorted, in registers; then k rounds take the
     // warp minimum of the lanes' heads, and every lane holding that key pops it
     // (a key is one id at its estimate: equal keys are the same id)
