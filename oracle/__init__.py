@@ -102,6 +102,8 @@ def _load():
             lib.or_tk_bucket.argtypes = [vp, u32, u32, u32, vp]
             lib.or_tk_query.restype = i32
             lib.or_tk_query.argtypes = [vp, vp, vp, u64, u32, u32, vp, vp]
+            lib.or_tk_fold.argtypes = [vp, vp, u64, u32, vp, vp]
+            lib.or_tk_rank.argtypes = [vp, vp, u32, u32, u32, vp, vp]
             _lib = lib
     return _lib
 
@@ -299,6 +301,26 @@ def tk_merge(a: tuple[int, int], b: tuple[int, int]) -> tuple[int, int]:
     h, c = ctypes.c_uint32(a[0]), ctypes.c_uint32(a[1])
     _load().or_tk_merge_cell(ctypes.byref(h), ctypes.byref(c), b[0], b[1])
     return int(h.value), int(c.value)
+
+
+def tk_fold(sketches) -> tuple[np.ndarray, np.ndarray]:
+    """Appendix 2 merge of a sequence of sketches, in the given order, into an
+    empty sketch.  ``sketches``: [n][cells][2] (heavy hitter, count) pairs;
+    returns (heavy hitters, counts) of the merged cells."""
+    a = np.ascontiguousarray(sketches, dtype=np.uint32)
+    n, wc = a.shape[0], a.shape[1]
+    hh, cnt = np.ascontiguousarray(a[..., 0]), np.ascontiguousarray(a[..., 1])
+    mh, mc = np.empty(wc, np.uint32), np.empty(wc, np.uint32)
+    _load().or_tk_fold(_p(hh), _p(cnt), n, wc, _p(mh), _p(mc))
+    return mh, mc
+
+
+def tk_rank(mh, mc, k: int, threshold: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """Appendix 2 query report of one merged sketch: top-k (ids, scores)."""
+    mh, mc = _u32(mh), _u32(mc)
+    ids, scores = np.empty(k, np.int32), np.empty(k, np.uint32)
+    _load().or_tk_rank(_p(mh), _p(mc), mh.size, k, threshold, _p(ids), _p(scores))
+    return ids, scores
 
 
 class TkIndex:

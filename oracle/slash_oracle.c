@@ -717,45 +717,64 @@ void or_tk_export(const void *p, uint32_t *out) {
   }
 }
 
-/* Algorithm 2 with sketches: merge the query's S*L buckets (shard-major, then table) into one
- * sketch, report its top-k heavy hitters by (count descending, id ascending). */
+/* Appendix 2 "Merging": fold n sketches of WC cells each, in the order given
+ * (sketch i's cells at hh[i*WC ..], cnt[i*WC ..]), into an empty sketch mh/mc. */
+void or_tk_fold(const uint32_t *hh, const uint32_t *cnt, uint64_t n, uint32_t WC, uint32_t *mh, uint32_t *mc) {
+  for (uint32_t c = 0; c < WC; ++c) { mh[c] = OR_EMPTY; mc[c] = 0; }
+  for (uint64_t i = 0; i < n; ++i)
+    for (uint32_t c = 0; c < WC; ++c) or_tk_merge_cell(mh + c, mc + c, hh[i * WC + c], cnt[i * WC + c]);
+}
+
+/* Appendix 2 "Querying" on a merged sketch: the distinct heavy hitters, each
+ * scored by its largest count over the cells; those whose score exceeds the
+ * threshold are ranked (score desc, id asc); the first k are written, padded
+ * with (-1, 0). */
+void or_tk_rank(const uint32_t *mh, const uint32_t *mc, uint32_t WC, uint32_t k, uint32_t threshold,
+                int32_t *ids, uint32_t *scores) {
+  or_cand *cand = (or_cand *)malloc(sizeof(or_cand) * (WC + 1));
+  uint32_t nc = 0;
+  for (uint32_t c = 0; c < WC; ++c) {
+    if (mc[c] == 0 || mc[c] <= threshold) continue;
+    uint32_t j = 0;
+    while (j < nc && cand[j].id != mh[c]) ++j;
+    if (j == nc) { cand[nc].id = mh[c]; cand[nc].est = mc[c]; ++nc; }
+    else if (mc[c] > cand[j].est) cand[j].est = mc[c];
+  }
+  qsort(cand, nc, sizeof(or_cand), cmp_cand);
+  for (uint32_t i = 0; i < k; ++i) {
+    ids[i] = i < nc ? (int32_t)cand[i].id : -1;
+    scores[i] = i < nc ? cand[i].est : 0;
+  }
+  free(cand);
+}
+
+/* Algorithm 2 with sketches: the query's S*L sketches, shard-major then in
+ * table order, are folded into one (or_tk_fold) and ranked (or_tk_rank). */
 int or_tk_query(const void *p, const uint64_t *offs, const uint32_t *cols, uint64_t nq, uint32_t k,
                 uint32_t threshold, int32_t *ids, uint32_t *scores) {
   const or_tk *ix = (const or_tk *)p;
   uint32_t nb = ix->K * ix->L, WC = ix->W * ix->C;
+  uint64_t n = (uint64_t)ix->S * ix->L;
   const uint32_t *st = ix->seeds + 2;
   uint32_t *codes = (uint32_t *)malloc(sizeof(uint32_t) * nb);
   uint32_t *mh = (uint32_t *)malloc(sizeof(uint32_t) * WC), *mc = (uint32_t *)malloc(sizeof(uint32_t) * WC);
-  or_cand *cand = (or_cand *)malloc(sizeof(or_cand) * (WC + 1));
-  for (uint64_t q = 0; q < nq; ++q) {
+  uint32_t *sh = (uint32_t *)malloc(sizeof(uint32_t) * n * WC), *sn = (uint32_t *)malloc(sizeof(uint32_t) * n * WC);
+  int rc = 0;
+  for (uint64_t q = 0; q < nq && rc == 0; ++q) {
     or_doph_seeded(cols + (offs[q] - offs[0]), offs[q + 1] - offs[q], nb, ix->seeds, ix->L, ix->W, codes);
-    for (uint32_t c = 0; c < WC; ++c) { mh[c] = OR_EMPTY; mc[c] = 0; }
-    int missing = 0;
-    for (uint32_t s = 0; s < ix->S; ++s)
-      for (uint32_t t = 0; t < ix->L; ++t) {
+    uint64_t i = 0;
+    for (uint32_t s = 0; s < ix->S && rc == 0; ++s)
+      for (uint32_t t = 0; t < ix->L; ++t, ++i) {
         uint32_t b = or_table_address(codes, t, ix->K, ix->B, st[t]);
         int64_t loc = or_tk_loc(ix, s, t, b);
-        if (loc < 0) { missing = 1; continue; }
-        uint64_t base = (uint64_t)loc * WC;
-        for (uint32_t c = 0; c < WC; ++c) or_tk_merge_cell(mh + c, mc + c, ix->hh[base + c], ix->cnt[base + c]);
+        if (loc < 0) { rc = -1; break; }
+        memcpy(sh + i * WC, ix->hh + (uint64_t)loc * WC, sizeof(uint32_t) * WC);
+        memcpy(sn + i * WC, ix->cnt + (uint64_t)loc * WC, sizeof(uint32_t) * WC);
       }
-    if (missing) { free(codes); free(mh); free(mc); free(cand); return -1; }
-    /* distinct heavy hitters, each with its largest count; Appendix 2 reports
-     * those whose count exceeds the threshold */
-    uint32_t nc = 0;
-    for (uint32_t c = 0; c < WC; ++c) {
-      if (mc[c] == 0 || mc[c] <= threshold) continue;
-      uint32_t j = 0;
-      while (j < nc && cand[j].id != mh[c]) ++j;
-      if (j == nc) { cand[nc].id = mh[c]; cand[nc].est = mc[c]; ++nc; }
-      else if (mc[c] > cand[j].est) cand[j].est = mc[c];
-    }
-    qsort(cand, nc, sizeof(or_cand), cmp_cand);
-    for (uint32_t i = 0; i < k; ++i) {
-      ids[q * k + i] = i < nc ? (int32_t)cand[i].id : -1;
-      scores[q * k + i] = i < nc ? cand[i].est : 0;
-    }
+    if (rc) break;
+    or_tk_fold(sh, sn, n, WC, mh, mc);
+    or_tk_rank(mh, mc, WC, k, threshold, ids + q * k, scores + q * k);
   }
-  free(codes); free(mh); free(mc); free(cand);
-  return 0;
+  free(codes); free(mh); free(mc); free(sh); free(sn);
+  return rc;
 }

@@ -131,3 +131,85 @@ def test_partial_parallel_insert_matches_dense():
     a, b_ = dense.query(qo, qc, 5)
     c, d = part.query(qo, qc, 5)
     assert np.array_equal(a, c) and np.array_equal(b_, d)
+
+
+# ---------------------------------------------------------------------------- query report, worked by hand
+# Appendix 2 "Querying": the merged sketch's heavy hitters are reported with
+# their counts; an id may hold several cells (one per sketch row, or more), and
+# this build scores it by the largest of its counts.  The expected values below
+# are worked out by hand from the cells, not computed through the oracle.
+
+def test_rank_scores_an_id_by_its_largest_cell():
+    # id 7 holds two cells (counts 3 and 5), id 9 one cell (6), one cell is empty.
+    #   largest count: 9 -> 6, 7 -> 5            => [(9, 6), (7, 5), pad]
+    #   (a sum would rank 7 first with 8; the first cell would score 7 with 3)
+    mh = [7, 9, 7, EMPTY]
+    mc = [3, 6, 5, 0]
+    ids, sc = oracle.tk_rank(mh, mc, 3)
+    assert ids.tolist() == [9, 7, -1]
+    assert sc.tolist() == [6, 5, 0]
+    # the same cells in another order give the same report
+    ids, sc = oracle.tk_rank([7, 7, EMPTY, 9], [5, 3, 0, 6], 3)
+    assert ids.tolist() == [9, 7, -1] and sc.tolist() == [6, 5, 0]
+
+
+def test_rank_ties_threshold_and_padding():
+    # equal scores rank by smaller id; a score must exceed the threshold
+    mh = [4, 3, 5, 4]
+    mc = [2, 2, 1, 1]
+    ids, sc = oracle.tk_rank(mh, mc, 4)
+    assert ids.tolist() == [3, 4, 5, -1] and sc.tolist() == [2, 2, 1, 0]
+    ids, sc = oracle.tk_rank(mh, mc, 4, threshold=1)
+    assert ids.tolist() == [3, 4, -1, -1] and sc.tolist() == [2, 2, 0, 0]
+    ids, sc = oracle.tk_rank(mh, mc, 2, threshold=2)
+    assert ids.tolist() == [-1, -1] and sc.tolist() == [0, 0]
+    # an id whose largest count passes the threshold is kept with that count,
+    # even though another of its cells does not pass
+    ids, sc = oracle.tk_rank([7, 7], [1, 4], 1, threshold=3)
+    assert ids.tolist() == [7] and sc.tolist() == [4]
+    # k smaller than the number of heavy hitters: only the first k
+    ids, sc = oracle.tk_rank([1, 2, 3], [5, 9, 7], 2)
+    assert ids.tolist() == [2, 3] and sc.tolist() == [9, 7]
+
+
+def test_fold_follows_the_merge_rule_in_order():
+    x, y, z = 11, 22, 33
+    # one-cell sketches A = (x, 2), B = (y, 2), C = (z, 1)
+    A, B, C = [[x, 2]], [[y, 2]], [[z, 1]]
+    # A, B, C: (x,2) + (y,2) -> equal counts cancel -> empty; + (z,1) -> (z,1)
+    mh, mc = oracle.tk_fold([A, B, C])
+    assert (int(mh[0]), int(mc[0])) == (z, 1)
+    # A, C, B: (x,2) + (z,1) -> x keeps 1; + (y,2) -> y wins with 2-1 = 1
+    mh, mc = oracle.tk_fold([A, C, B])
+    assert (int(mh[0]), int(mc[0])) == (y, 1)
+    # same heavy hitter: counts add; an empty cell leaves the other unchanged
+    mh, mc = oracle.tk_fold([[[x, 2], [EMPTY, 0]], [[x, 3], [y, 4]], [[EMPTY, 0], [y, 1]]])
+    assert mh[0] == x and mc[0] == 5 and mh[1] == y and mc[1] == 5
+    # nothing folded: every cell empty
+    mh, mc = oracle.tk_fold(np.zeros((0, 3, 2), np.uint32))
+    assert np.all(mc == 0)
+
+
+def test_query_folds_shard_major_then_table_order():
+    """The index query equals ranking the fold of its S*L sketches taken
+    shard-major, then in table order; at least one query's answer changes when
+    the sketches are folded table-major instead (so the order is checked)."""
+    g = datagen.Generator()
+    n = 6000
+    offs, cols = g.rows(4, 0, n)
+    S, L, B, W, C = 2, 8, 3, 2, 2
+    ix = oracle.TkIndex(K=2, L=L, log2_buckets=B, rows=W, cells=C, shards=S, seed=6, capacity=n)
+    ix.insert(offs, cols)
+    qo, qc, _ = g.queries(4, 5, 60, n, p_perturb=0.2)
+    ids, sc = ix.query(qo, qc, 6)
+    _, qbk = oracle.hash_rows(2, L, B, 6, W, qo, qc, want_codes=False)
+    differs = 0
+    for q in range(60):
+        sk = {(s, t): ix.bucket(t, int(qbk[q, t]), s).reshape(W * C, 2) for s in range(S) for t in range(L)}
+        shard_major = [sk[(s, t)] for s in range(S) for t in range(L)]
+        table_major = [sk[(s, t)] for t in range(L) for s in range(S)]
+        a = oracle.tk_rank(*oracle.tk_fold(shard_major), 6)
+        assert np.array_equal(a[0], ids[q]) and np.array_equal(a[1], sc[q])
+        b = oracle.tk_rank(*oracle.tk_fold(table_major), 6)
+        differs += not (np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]))
+    assert differs > 0
