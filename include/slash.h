@@ -233,6 +233,35 @@ int slash_profile_read(slash_index *ix, uint32_t max_kernels, char *h_names, flo
 int slash_debug_hash(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n,
                      uint32_t *d_codes, uint32_t *d_buckets, void *cuda_stream);
 
+/* Measurement support (no counterpart in the paper) -- a shared-memory
+ * microbenchmark on the current device that gives the count-min update its
+ * ceiling: `ctas_per_sm` CTAs of `threads` threads per SM (256, 512 or 1024;
+ * 1..8) each run `iters` operations per thread on a shared table of `words`
+ * 32-bit words (a power of two, 32..65536) at pseudo-random addresses.  mode 0:
+ * atomicAdd at a random word (the sketch update); 1: plain load at a random word;
+ * 2: atomicAdd at a random word of the lane's own bank (no bank conflicts);
+ * 3: atomicAdd with every lane of a warp on one word.  *ms_out = the fastest of
+ * three timed launches (after a warm-up), *ops_out = operations per launch.
+ * Synchronises the device.  Errors: SLASH_EINVAL, SLASH_ENOMEM, SLASH_ECUDA. */
+int slash_probe_smem(uint32_t mode, uint32_t words, uint32_t iters, uint32_t threads, uint32_t ctas_per_sm,
+                     float *ms_out, uint64_t *ops_out);
+
+/* Test support -- the next `count` device allocations this index makes for its
+ * workspace (insert, plain-query and host-staging buffers) fail as if the device
+ * were out of memory: the call that needed them returns SLASH_ENOMEM before any
+ * work is enqueued, and the index (its buckets, fills and next id) is unchanged.
+ * count = 0 cancels.  Errors: SLASH_EINVAL (NULL). */
+int slash_debug_fail_alloc(slash_index *ix, uint32_t count);
+
+/* Test support -- while enabled, the shared-memory copy wait of the staged
+ * query engine (the one serving topk <= 10 when R is a multiple of 4) waits for
+ * 16 bytes that no copy delivers, so every such wait gives up after its 1 s
+ * limit: the kernel sets the sticky error word and returns, the next
+ * slash_sync() reports SLASH_ETIMEOUT, and the device stays usable.  Query
+ * outputs of such a call are undefined.  Errors: SLASH_EINVAL (NULL, or an
+ * index the staged engine does not serve). */
+int slash_debug_stall_copies(slash_index *ix, int enable);
+
 /* Test support -- copy the whole index to host memory: h_slots uint32
  * [S][L][2^B][R], h_fill uint32 [S][L][2^B].  Synchronises.  Either pointer
  * may be NULL.  Errors: SLASH_ECUDA. */

@@ -95,6 +95,9 @@ def _load() -> ctypes.CDLL:
         "slash_size": (u64, [vp]),
         "slash_debug_hash": (i32, [vp, vp, vp, u32, vp, vp, vp]),
         "slash_debug_export": (i32, [vp, vp, vp]),
+        "slash_debug_fail_alloc": (i32, [vp, u32]),
+        "slash_probe_smem": (i32, [u32, u32, u32, u32, u32, P(ctypes.c_float), P(u64)]),
+        "slash_debug_stall_copies": (i32, [vp, i32]),
         "slash_debug_buckets": (i32, [vp, vp, vp, vp, u32, vp, vp]),
         "slash_query_ex": (i32, [vp, vp, vp, u32, u32, vp, vp, P(slash_query_opts), vp]),
         "slash_autotune": (i32, [vp, vp, vp, u32, u32, vp, vp, vp, P(slash_query_opts), P(ctypes.c_float)]),
@@ -289,6 +292,25 @@ def slash_debug_hash(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, nb: in
                                  codes.data_ptr() if codes is not None else None, bk.data_ptr(),
                                  _stream(stream)), "slash_debug_hash")
     return codes, bk
+
+
+def slash_debug_fail_alloc(ix: int, count: int) -> None:
+    """Test support: the index's next ``count`` workspace allocations fail (SLASH_ENOMEM)."""
+    _check(_lib.slash_debug_fail_alloc(ix, count), "slash_debug_fail_alloc")
+
+
+def slash_probe_smem(mode: int, words: int = 16384, iters: int = 4096, threads: int = 512,
+                     ctas_per_sm: int = 2) -> tuple[float, int]:
+    """Shared-memory microbenchmark (see include/slash.h): (ms, operations)."""
+    ms, ops = ctypes.c_float(), ctypes.c_uint64()
+    _check(_lib.slash_probe_smem(mode, words, iters, threads, ctas_per_sm, ctypes.byref(ms), ctypes.byref(ops)),
+           "slash_probe_smem")
+    return float(ms.value), int(ops.value)
+
+
+def slash_debug_stall_copies(ix: int, enable: bool) -> None:
+    """Test support: staged query waits give up after their time limit (SLASH_ETIMEOUT)."""
+    _check(_lib.slash_debug_stall_copies(ix, 1 if enable else 0), "slash_debug_stall_copies")
 
 
 def slash_debug_export(ix: int, p: Params, fill_only: bool = False):

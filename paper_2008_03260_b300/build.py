@@ -14,7 +14,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libslash.so")
-SOURCES = [os.path.join(CSRC, "slash.cu"), os.path.join(CSRC, "slash_topkapi.cu")]
+SOURCES = [os.path.join(CSRC, "slash.cu"), os.path.join(CSRC, "slash_topkapi.cu"),
+           os.path.join(CSRC, "slash_probe.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
     os.path.join(INCLUDE, "slash.h"), os.path.join(INCLUDE, "slash_topkapi.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

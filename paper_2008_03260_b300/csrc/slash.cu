@@ -54,6 +54,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "slash.h"
 #include "slash_device.cuh"
 #include "slash_io.h"
@@ -715,7 +717,7 @@ k_merge_big(const __grid_constant__ Geo g, const uint32_t* __restrict__ list, co
 constexpr uint32_t kHistBins = 256;  // estimate histogram; the last bin holds est >= 255
 constexpr int kRegIds = 8;           // candidate occurrences a thread keeps in registers
 
-enum { C_NPOOL = 0, C_ELO, C_PFX, C_NEED, C_Q, C_N };
+enum { C_NPOOL = 0, C_ELO, C_PFX, C_NEED, C_Q, C_N };  // control words of query_core (16 reserved)
 
 // Shared-memory carve-up of one query (byte offsets), fixed per index.
 struct QueryLayout {
@@ -1177,6 +1179,482 @@ k_query_fused(const __grid_constant__ Geo g, const QueryLayout lay, const uint64
   }
 }
 
+// ----------------------------------------------------------------------------- query, staged
+// The query engine for the common case (R a multiple of 4, k <= kLocalTop, at
+// most kStagedMaxBuckets buckets per query); query_core stays the general one.
+// Per query (Algorithm 2, local and cross-partition merge):
+//   - warp 0 reads the S*L bucket keys and fills and issues one bulk copy per
+//     non-empty bucket (cp.async.bulk, completed on an mbarrier), moving its
+//     ids into a shared-memory buffer; a bucket's run is rounded up to 4 ids,
+//     which is safe because the slots past a bucket's fill hold 0xFFFFFFFF.
+//     Meanwhile the other warps clear the sketch;
+//   - every thread counts its share of the buffer into the packed sketch;
+//   - each occurrence's estimate is computed once and kept as a byte (255 =
+//     "at least 255", recomputed exactly where it matters), with a histogram;
+//   - cut-off and tie bound exactly as in query_core.  The pool holds buffer
+//     indices; by the cut-off's construction it has fewer than (2k+1)*S*L
+//     entries unless the capped bin (estimates >= 255) decides.  That query is
+//     marked (id -2 in its first output slot) and answered by k_query_redo;
+//   - warp 0 ranks the pool with per-lane register lists (k <= kLocalTop).
+// A CTA needs about 110 KB of shared memory at the criteo shape (64 KB of
+// sketch, 32 KB of ids), so two 512-thread CTAs share an SM: one CTA's
+// single-warp phases overlap the other's counting.
+constexpr uint32_t kStagedMaxBuckets = 256;     // S*L of the staged engine
+constexpr uint64_t kStagedWaitNs = 1000000000ull;   // bounded mbarrier wait: 1 s of %globaltimer
+constexpr uint64_t kStagedDrainNs = 100000000ull;   // after a timeout: 0.1 s for copies still in flight
+constexpr int32_t kRedoMark = -2;               // first output id of a query left to k_query_redo
+
+struct StagedLayout {
+  uint32_t nbk;      // buckets per query, S*L
+  uint32_t maxmult;  // most occurrences of one id, S*L
+  uint32_t idcap;    // id buffer words, >= S*L*R
+  uint32_t pcap;     // pool entries, (2k+1)*S*L for k = kLocalTop
+  uint32_t off_cm, off_ids, off_est, off_pool, off_bkey, off_boff, off_hist, off_ctrl, off_bar, bytes;
+  uint32_t extra_tx;  // test support: bytes announced on the mbarrier beyond the copies (0 in service)
+};
+
+enum { S_NPOOL = 0, S_ELO, S_PFX, S_NEED, S_Q, S_TOT, S_N };
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for the phase with the given parity to complete, for at most limit_ns
+// (and at most 2^30 polls, should the timer not advance).
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < (1u << 30); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 63u && global_ns() - t0 > limit_ns) return false;
+  }
+  return false;
+}
+// Orders this thread's earlier shared-memory accesses before later async-proxy (bulk copy) writes.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Global -> shared bulk copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned), completing `bytes` transactions on the mbarrier at `bar`.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Warp 0: read the fills of the buckets in bkey[0..nbk), lay their runs out in
+// the id buffer (bucket order, each rounded up to 4 ids), announce the bytes on
+// the mbarrier and issue the copies.  Returns the buffer's length in ids.
+__device__ __forceinline__ void staged_issue(const Geo& g, const StagedLayout& lay, unsigned char* qsm,
+                                             const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill,
+                                             uint32_t bar, uint32_t lane) {
+  constexpr int kPer = kStagedMaxBuckets / 32;
+  const uint32_t* bkey = reinterpret_cast<const uint32_t*>(qsm + lay.off_bkey);
+  uint32_t* ctrl = reinterpret_cast<uint32_t*>(qsm + lay.off_ctrl);
+  const uint32_t ids_s = smem_u32(qsm + lay.off_ids);
+  uint32_t f[kPer], key[kPer], sum = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const uint32_t i = lane * kPer + j;  // a lane's buckets are consecutive: runs stay in bucket order
+    key[j] = i < lay.nbk ? bkey[i] : 0u;
+    f[j] = i < lay.nbk ? min(__ldg(fill + key[j]), g.R) : 0u;  // a fill never exceeds R; the copy stays in bounds
+    sum += (f[j] + 3u) & ~3u;
+  }
+  uint32_t inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= (uint32_t)o) inc += u;
+  }
+  const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+  fence_proxy_async_smem();  // the buffer's earlier reads and writes come before the copies
+  if (lane == 0) {
+    ctrl[S_TOT] = total;
+    mbar_arrive_expect_tx(bar, total * 4u + lay.extra_tx);
+  }
+  __syncwarp();
+  uint32_t o = inc - sum;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const uint32_t n4 = (f[j] + 3u) & ~3u;
+    if (n4) bulk_g2s(ids_s + 4u * o, slots + (uint64_t)key[j] * g.R, 4u * n4, bar);
+    o += n4;
+  }
+}
+
+// 64-bit warp minimum
+__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t u = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    v = u < v ? u : v;
+  }
+  return v;
+}
+
+// The staged query of one CTA, after bkey[] is in place (synced) and warp 0
+// has issued the copies.  Returns false if the bounded wait gave up.
+__device__ bool staged_answer(const Geo& g, const StagedLayout& lay, unsigned char* qsm, uint32_t bar,
+                              uint32_t parity, uint32_t k, int32_t* __restrict__ ids_out,
+                              uint32_t* __restrict__ scores_out, uint32_t* __restrict__ err) {
+  uint32_t* cmw = reinterpret_cast<uint32_t*>(qsm + lay.off_cm);
+  const uint32_t* ids = reinterpret_cast<const uint32_t*>(qsm + lay.off_ids);
+  const uint4* ids4 = reinterpret_cast<const uint4*>(ids);
+  uint32_t* est4 = reinterpret_cast<uint32_t*>(qsm + lay.off_est);  // 4 byte-estimates per word
+  const uint8_t* est8 = reinterpret_cast<const uint8_t*>(est4);
+  uint32_t* pool = reinterpret_cast<uint32_t*>(qsm + lay.off_pool);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(qsm + lay.off_hist);
+  uint32_t* ctrl = reinterpret_cast<uint32_t*>(qsm + lay.off_ctrl);
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, T = blockDim.x;
+  const uint32_t wmask = g.w - 1u;
+  const bool ok = mbar_wait_bounded(bar, parity, kStagedWaitNs);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicOr(err, kErrWait);
+    mbar_wait_bounded(bar, parity, kStagedDrainNs);  // let copies still in flight land before the CTA leaves
+    return false;
+  }
+  const uint32_t n4 = ctrl[S_TOT] >> 2;
+  // -- count every occurrence into the sketch
+  for (uint32_t i = threadIdx.x; i < n4; i += T) {
+    const uint4 v = ids4[i];
+    const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (x[c] == kEmpty) continue;
+      for (uint32_t r = 0; r < g.d; ++r) cm_add(cmw, r * g.w + cm_cell(x[c], g.sc[r], wmask));
+    }
+  }
+  __syncthreads();
+  // -- estimates (bytes, 255 = at least 255) and their histogram; bins 1..3 hold
+  //    most occurrences, so they are counted by warp ballots instead of atomics
+  uint32_t c1 = 0, c2 = 0, c3 = 0;
+  for (uint32_t i0 = 0; i0 < n4; i0 += T) {
+    const uint32_t i = i0 + threadIdx.x;
+    uint32_t packed = 0;
+    uint32_t e4[4] = {0u, 0u, 0u, 0u};
+    if (i < n4) {
+      const uint4 v = ids4[i];
+      const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (x[c] == kEmpty) continue;
+        const uint32_t e = min(estimate(g, cmw, x[c]), kHistBins - 1u);
+        e4[c] = e;
+        packed |= e << (8 * c);
+      }
+      est4[i] = packed;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      c1 += __popc(__ballot_sync(0xFFFFFFFFu, e4[c] == 1u));
+      c2 += __popc(__ballot_sync(0xFFFFFFFFu, e4[c] == 2u));
+      c3 += __popc(__ballot_sync(0xFFFFFFFFu, e4[c] == 3u));
+      if (e4[c] > 3u) atomicAdd(&hist[e4[c]], 1u);
+    }
+  }
+  if (lane == 0) {
+    if (c1) atomicAdd(&hist[1], c1);
+    if (c2) atomicAdd(&hist[2], c2);
+    if (c3) atomicAdd(&hist[3], c3);
+  }
+  __syncthreads();
+  // -- cut-off: the largest bin e_lo whose bins at or above it surely hold >= k distinct ids
+  if (warp == 0) {
+    uint32_t v[8], sum = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t bin = kHistBins - 1u - (lane * 8u + i);  // lane 0 holds the top bins
+      const uint32_t div = bin == kHistBins - 1u ? lay.maxmult : max(1u, min(bin, lay.maxmult));
+      v[i] = bin == 0u ? 0u : (hist[bin] + div - 1u) / div;
+      sum += v[i];
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= (uint32_t)o) inc += u;
+    }
+    const uint32_t ex = inc - sum;
+    if (ex < k && k <= inc) {
+      uint32_t cum = ex;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        cum += v[i];
+        if (cum >= k) { ctrl[S_ELO] = kHistBins - 1u - (lane * 8u + i); break; }
+      }
+    }
+  }
+  __syncthreads();
+  const uint32_t elo = ctrl[S_ELO];
+  // -- ties in bin e_lo (not the capped bin): the (k*mu)-th smallest occurrence id bounds them
+  uint32_t idmax = 0xFFFFFFFFu;
+  const bool tie_bin = elo > 0u && elo < kHistBins - 1u;
+  const uint32_t mu = tie_bin ? min(elo, lay.maxmult) : 0u;
+  const uint32_t need0 = k * mu;
+  if (tie_bin && hist[elo] > need0) {
+    uint32_t prefix = 0, need = need0;
+    uint32_t* h2 = hist;  // the estimate histogram is no longer needed
+    for (int sh = 24; sh >= 0; sh -= 8) {
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < kHistBins; i += T) h2[i] = 0u;
+      __syncthreads();
+      for (uint32_t i = threadIdx.x; i < n4; i += T) {
+        const uint32_t ew = est4[i];
+        if (((ew & 0xFFu) != elo) && (((ew >> 8) & 0xFFu) != elo) && (((ew >> 16) & 0xFFu) != elo) &&
+            ((ew >> 24) != elo))
+          continue;
+        const uint4 v = ids4[i];
+        const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const uint32_t id = x[c];
+          if (((ew >> (8 * c)) & 0xFFu) == elo && (sh == 24 || (id >> (sh + 8)) == (prefix >> (sh + 8))))
+            atomicAdd(&h2[(id >> sh) & 255u], 1u);
+        }
+      }
+      __syncthreads();
+      if (warp == 0) {
+        uint32_t v[8], sum = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) { v[i] = h2[lane * 8 + i]; sum += v[i]; }
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+          if (lane >= (uint32_t)o) inc += u;
+        }
+        const uint32_t ex = inc - sum;
+        if (ex < need && need <= inc) {
+          uint32_t cum = ex;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            if (cum + v[i] >= need) {
+              ctrl[S_PFX] = prefix | ((lane * 8u + i) << sh);
+              ctrl[S_NEED] = need - cum;
+              break;
+            }
+            cum += v[i];
+          }
+        }
+      }
+      __syncthreads();
+      prefix = ctrl[S_PFX];
+      need = ctrl[S_NEED];
+    }
+    idmax = prefix;  // >= k*mu occurrences (so >= k distinct ids) of the bin are <= idmax
+  }
+  // -- pool: buffer indices of the occurrences above the bin, and of the bin's up to idmax
+  for (uint32_t i0 = 0; i0 < n4; i0 += T) {
+    const uint32_t i = i0 + threadIdx.x;
+    uint32_t ew = 0;
+    uint4 v = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+    if (i < n4) {
+      ew = est4[i];
+      v = ids4[i];
+    }
+    const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint32_t e = (ew >> (8 * c)) & 0xFFu;
+      const bool take = x[c] != kEmpty && (e > elo || (e == elo && x[c] <= idmax));
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, take);
+      if (!m) continue;
+      uint32_t base = 0;
+      if (lane == (uint32_t)(__ffs(m) - 1)) base = atomicAdd(&ctrl[S_NPOOL], (uint32_t)__popc(m));
+      base = __shfl_sync(0xFFFFFFFFu, base, __ffs(m) - 1);
+      const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
+      if (take && pos < lay.pcap) pool[pos] = 4u * i + (uint32_t)c;
+    }
+  }
+  __syncthreads();
+  const uint32_t P = ctrl[S_NPOOL];
+  if (warp == 0) {
+    if (P > lay.pcap) {  // only when the capped bin decides: leave the query to k_query_redo
+      if (lane == 0) ids_out[0] = kRedoMark;
+    } else {
+      // one pass: each lane keeps its kLocalTop smallest distinct keys, sorted;
+      // then k rounds take the warp minimum of the lanes' heads
+      uint64_t loc[kLocalTop];
+#pragma unroll
+      for (int t = 0; t < (int)kLocalTop; ++t) loc[t] = ~0ull;
+      for (uint32_t i = lane; i < P; i += 32) {
+        const uint32_t ix = pool[i];
+        const uint32_t id = ids[ix];
+        uint32_t e = est8[ix];
+        if (e == kHistBins - 1u) e = estimate(g, cmw, id);  // exact value of a capped estimate
+        const uint64_t key = rank_key(e, id);
+        if (key >= loc[kLocalTop - 1]) continue;
+        bool dup = false;
+#pragma unroll
+        for (int t = 0; t < (int)kLocalTop; ++t) dup |= loc[t] == key;
+        if (dup) continue;
+#pragma unroll
+        for (int t = (int)kLocalTop - 1; t > 0; --t)
+          loc[t] = loc[t - 1] > key ? loc[t - 1] : (loc[t] > key ? key : loc[t]);
+        loc[0] = loc[0] > key ? key : loc[0];
+      }
+      for (uint32_t j = 0; j < k; ++j) {
+        const uint64_t best = warp_min_u64(loc[0]);
+        if (lane == 0) {
+          ids_out[j] = best != ~0ull ? (int32_t)(uint32_t)best : -1;
+          scores_out[j] = best != ~0ull ? 0xFFFFu - (uint32_t)(best >> 32) : 0u;
+        }
+        if (best != ~0ull && loc[0] == best) {
+#pragma unroll
+          for (int t = 0; t < (int)kLocalTop - 1; ++t) loc[t] = loc[t + 1];
+          loc[kLocalTop - 1] = ~0ull;
+        }
+      }
+    }
+  }
+  return true;
+}
+
+// Staged engine, one persistent CTA pulls queries from a per-launch work counter.
+// kFused = false: the bucket addresses come from the hash kernel (qbkt[t*ldq + q]);
+// kFused = true: the CTA hashes each query itself (DOPH binning by all threads,
+// densification and table addresses by warp 0, in the id buffer's space).
+template <int kThreads, bool kFused>
+__global__ void __launch_bounds__(kThreads, kThreads <= 512 ? 2 : 1)
+k_query_staged(const __grid_constant__ Geo g, const StagedLayout lay, const uint32_t* __restrict__ qbkt,
+               uint64_t ldq, const uint64_t* __restrict__ offs, const uint32_t* __restrict__ cols, uint32_t nq,
+               uint32_t k, const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill,
+               int32_t* __restrict__ ids_out, uint32_t* __restrict__ scores_out, uint32_t* __restrict__ work,
+               uint32_t* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char qsm[];
+  uint32_t* cmw = reinterpret_cast<uint32_t*>(qsm + lay.off_cm);
+  uint32_t* bkey = reinterpret_cast<uint32_t*>(qsm + lay.off_bkey);
+  uint32_t* hist = reinterpret_cast<uint32_t*>(qsm + lay.off_hist);
+  uint32_t* ctrl = reinterpret_cast<uint32_t*>(qsm + lay.off_ctrl);
+  uint32_t* m = reinterpret_cast<uint32_t*>(qsm + lay.off_ids);  // fused: bin minima, then the id buffer
+  uint32_t* mask = m + g.nb;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t bar = smem_u32(qsm + lay.off_bar);
+  const uint32_t cm4n = (g.d * g.w) >> 3;  // uint4 words of the packed sketch
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1u);
+    mbar_fence_init();
+  }
+  uint32_t parity = 0;
+  for (;;) {
+    if (threadIdx.x == 0) ctrl[S_Q] = atomicAdd(work, 1u);
+    if (threadIdx.x < S_N && threadIdx.x != S_Q) ctrl[threadIdx.x] = 0u;
+    uint4* cm4 = reinterpret_cast<uint4*>(cmw);
+    for (uint32_t i = threadIdx.x; i < cm4n; i += blockDim.x) cm4[i] = make_uint4(0, 0, 0, 0);
+    for (uint32_t i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
+    if (kFused) {
+      for (uint32_t j = threadIdx.x; j < g.nb; j += blockDim.x) m[j] = kEmpty;
+      if (threadIdx.x < g.nw) mask[threadIdx.x] = 0u;
+    }
+    __syncthreads();
+    const uint32_t q = ctrl[S_Q];
+    if (q >= nq) break;
+    if (kFused) {
+      uint64_t b0 = offs[q], b1 = offs[q + 1];
+      if (b1 < b0) {
+        if (threadIdx.x == 0) atomicOr(err, kErrOffs);
+        b1 = b0;
+      }
+      if (doph_scatter(g, cols, b0, b1, m, mask, threadIdx.x, blockDim.x)) atomicOr(err, kErrCol);
+      __syncthreads();
+      if (warp == 0) {
+        doph_densify(g, m, mask, lane);
+        for (uint32_t it = lane; it < lay.nbk; it += 32) {
+          const uint32_t s = it / g.L, t = it - s * g.L;
+          bkey[it] = ((s * g.L + t) << g.B) | table_address(g, m, t);
+        }
+        __syncwarp();
+        staged_issue(g, lay, qsm, slots, fill, bar, lane);
+      }
+    } else if (warp == 0) {
+      for (uint32_t it = lane; it < lay.nbk; it += 32) {
+        const uint32_t s = it / g.L, t = it - s * g.L;
+        bkey[it] = ((s * g.L + t) << g.B) | __ldg(qbkt + t * ldq + q);
+      }
+      __syncwarp();
+      staged_issue(g, lay, qsm, slots, fill, bar, lane);
+    }
+    if (!staged_answer(g, lay, qsm, bar, parity, k, ids_out + (uint64_t)q * k, scores_out + (uint64_t)q * k, err))
+      return;
+    parity ^= 1u;
+    __syncthreads();  // the buffers are reused by the next query
+  }
+}
+
+// Answers, with query_core, every query of the batch whose first output id is
+// kRedoMark (left by k_query_staged); the query is hashed again in the CTA.
+// Each CTA scans its strided share of the batch a block of queries at a time.
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads, 1)
+k_query_redo(const __grid_constant__ Geo g, const QueryLayout lay, const uint64_t* __restrict__ offs,
+             const uint32_t* __restrict__ cols, uint32_t nq, uint32_t k, const uint32_t* __restrict__ slots,
+             const uint32_t* __restrict__ fill, int32_t* __restrict__ ids_out, uint32_t* __restrict__ scores_out,
+             uint32_t* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char qsm[];
+  uint32_t* bkey = reinterpret_cast<uint32_t*>(qsm + lay.off_bkey);
+  uint32_t* m = reinterpret_cast<uint32_t*>(qsm + lay.off_m);
+  uint32_t* mask = reinterpret_cast<uint32_t*>(qsm + lay.off_mask);
+  uint32_t* ctrl = reinterpret_cast<uint32_t*>(qsm + lay.off_ctrl);
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint64_t q0 = (uint64_t)blockIdx.x * kThreads; q0 < nq; q0 += (uint64_t)gridDim.x * kThreads) {
+    const uint64_t mine = q0 + threadIdx.x;
+    const bool marked = mine < nq && ids_out[mine * k] == kRedoMark;
+    if (threadIdx.x == 0) ctrl[C_N] = 0u;
+    __syncthreads();
+    if (marked) atomicAdd(&ctrl[C_N], 1u);
+    __syncthreads();
+    const uint32_t any = ctrl[C_N];
+    __syncthreads();
+    if (!any) continue;
+    for (uint32_t t = 0; t < kThreads; ++t) {
+      const uint64_t q = q0 + t;
+      if (q >= nq) break;
+      __syncthreads();
+      if (ids_out[q * k] != kRedoMark) continue;  // uniform: every thread reads the same word
+      __syncthreads();
+      for (uint32_t j = threadIdx.x; j < g.nb; j += blockDim.x) m[j] = kEmpty;
+      if (threadIdx.x < g.nw) mask[threadIdx.x] = 0u;
+      __syncthreads();
+      uint64_t b0 = offs[q], b1 = offs[q + 1];
+      if (b1 < b0) b1 = b0;
+      doph_scatter(g, cols, b0, b1, m, mask, threadIdx.x, blockDim.x);
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        doph_densify(g, m, mask, lane);
+        for (uint32_t it = lane; it < lay.nbk; it += 32) {
+          const uint32_t s = it / g.L, tt = it - s * g.L;
+          bkey[it] = ((s * g.L + tt) << g.B) | table_address(g, m, tt);
+        }
+      }
+      __syncthreads();
+      query_core(g, lay, qsm, slots, fill, k, ids_out + q * k, scores_out + q * k);
+    }
+  }
+}
+
 // Offsets staged from a host CSR array, made relative to their first column.
 __global__ void k_rebase(uint64_t* __restrict__ offs, uint64_t n, uint64_t base) {
   const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1281,6 +1759,9 @@ struct slash_index {
   slash_query_opts qdef{SLASH_QUERY_FUSED, 512, 0};  // default query schedule (autotuned)
   uint32_t* work = nullptr;                          // ring of fused-kernel work counters
   int qbps[2][3] = {};                               // CTAs/SM per (mode, threads); -1 = does not fit
+  int sbps[2][3] = {};                               // the same for the staged engine
+  bool staged = false;                               // the staged engine serves k <= kLocalTop
+  uint32_t redo_threads = 256;                       // CTA size of k_query_redo (query_core layout fits)
   std::atomic<uint32_t> work_next{0};                // next ring slot (one per fused launch)
   // per-launch event profile (off unless slash_profile enables it)
   struct ProfRec { const char* name; cudaEvent_t a, b; };
@@ -1288,6 +1769,8 @@ struct slash_index {
   std::vector<ProfRec> prof;
   std::vector<cudaEvent_t> prof_pool;
   uint64_t launches = 0;  // kernel launches issued since the index was built
+  uint32_t fail_allocs = 0;  // test support: workspace allocations still to fail (slash_debug_fail_alloc)
+  bool stall_copies = false; // test support: staged queries wait for bytes never sent (slash_debug_stall_copies)
 };
 
 namespace {
@@ -1300,6 +1783,12 @@ constexpr uint32_t kWorkRing = 4096;  // fused launches that may be in flight at
     if (e_ != cudaSuccess) {                                                           \
       return e_ == cudaErrorMemoryAllocation ? SLASH_ENOMEM : SLASH_ECUDA;             \
     }                                                                                  \
+  } while (0)
+
+#define SLASH_CK_RC(call)         \
+  do {                            \
+    const int rc_ = (call);       \
+    if (rc_ != SLASH_OK) return rc_; \
   } while (0)
 
 cudaEvent_t prof_event(slash_index* ix) {
@@ -1321,6 +1810,7 @@ struct Launch {
   cudaStream_t st;
   cudaEvent_t a = nullptr;
   Launch(slash_index* ix_, const char* name_, cudaStream_t st_) : ix(ix_), name(name_), st(st_) {
+    nvtxRangePushA(name_);  // one NVTX range per stage (kernel enqueue) for timeline tools
     ++ix->launches;
     if (ix->prof_on) {
       a = prof_event(ix);
@@ -1333,8 +1823,26 @@ struct Launch {
       cudaEventRecord(b, st);
       ix->prof.push_back({name, a, b});
     }
+    nvtxRangePop();
   }
 };
+
+// NVTX range around one C-ABI call.
+struct ApiRange {
+  explicit ApiRange(const char* name) { nvtxRangePushA(name); }
+  ~ApiRange() { nvtxRangePop(); }
+};
+
+// Workspace allocation; slash_debug_fail_alloc can make the next ones fail
+// exactly as an exhausted device would.
+cudaError_t ws_malloc(slash_index* ix, void** p, size_t bytes) {
+  if (ix->fail_allocs) {
+    --ix->fail_allocs;
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
 
 uint64_t insert_chunk_rows(const slash_index* ix) {
   const char* env = std::getenv("SLASH_INSERT_CHUNK_ROWS");
@@ -1356,12 +1864,12 @@ int grow_insert_ws(slash_index* ix, uint64_t rows) {
   const uint64_t big_cap = (L * rows) / (kSmallMax / 2) + 1;  // > 512 survivors per big bucket
   const uint64_t fb_cap = std::min<uint64_t>(ix->nk, L * rows);
   uint32_t *bkt = nullptr, *stage = nullptr, *big = nullptr, *fb = nullptr, *fboff = nullptr, *fbcur = nullptr;
-  cudaError_t e = cudaMalloc(&bkt, sizeof(uint32_t) * L * rows);
-  if (e == cudaSuccess) e = cudaMalloc(&stage, sizeof(uint32_t) * L * rows);
-  if (e == cudaSuccess) e = cudaMalloc(&big, sizeof(uint32_t) * 3 * big_cap);
-  if (e == cudaSuccess) e = cudaMalloc(&fb, sizeof(uint32_t) * 2 * fb_cap);
-  if (e == cudaSuccess) e = cudaMalloc(&fboff, sizeof(uint32_t) * fb_cap);
-  if (e == cudaSuccess) e = cudaMalloc(&fbcur, sizeof(uint32_t) * fb_cap);
+  cudaError_t e = ws_malloc(ix, (void**)&bkt, sizeof(uint32_t) * L * rows);
+  if (e == cudaSuccess) e = ws_malloc(ix, (void**)&stage, sizeof(uint32_t) * L * rows);
+  if (e == cudaSuccess) e = ws_malloc(ix, (void**)&big, sizeof(uint32_t) * 3 * big_cap);
+  if (e == cudaSuccess) e = ws_malloc(ix, (void**)&fb, sizeof(uint32_t) * 2 * fb_cap);
+  if (e == cudaSuccess) e = ws_malloc(ix, (void**)&fboff, sizeof(uint32_t) * fb_cap);
+  if (e == cudaSuccess) e = ws_malloc(ix, (void**)&fbcur, sizeof(uint32_t) * fb_cap);
   if (e != cudaSuccess) {
     cudaGetLastError();
     cudaFree(bkt); cudaFree(stage); cudaFree(big); cudaFree(fb); cudaFree(fboff); cudaFree(fbcur);
@@ -1379,7 +1887,7 @@ int grow_insert_ws(slash_index* ix, uint64_t rows) {
 int grow_query_ws(slash_index* ix, uint64_t nq) {
   if (nq <= ix->qws) return SLASH_OK;
   uint32_t* q = nullptr;
-  if (cudaMalloc(&q, sizeof(uint32_t) * ix->p.L * nq) != cudaSuccess) { cudaGetLastError(); return SLASH_ENOMEM; }
+  if (ws_malloc(ix, (void**)&q, sizeof(uint32_t) * ix->p.L * nq) != cudaSuccess) { cudaGetLastError(); return SLASH_ENOMEM; }
   cudaFree(ix->qbkt);
   ix->qbkt = q;
   ix->qws = nq;
@@ -1424,6 +1932,29 @@ uint32_t default_query_threads(const slash_params& p) {
   uint32_t t = 256;
   while (t < 1024 && t * kRegIds < maxm) t <<= 1;
   return t;
+}
+
+// Shared-memory layout of a staged query CTA (independent of the CTA size).
+StagedLayout make_staged_layout(const slash_params& p) {
+  StagedLayout l{};
+  l.nbk = p.shards * p.L;
+  l.maxmult = p.shards * p.L;
+  l.idcap = (p.shards * p.L * p.reservoir + 3u) & ~3u;
+  l.pcap = (2u * kLocalTop + 1u) * l.maxmult + 32u;
+  const uint32_t nb = p.K * p.L, nw = (nb + 31) / 32;
+  auto al = [](uint32_t x) { return (x + 127u) & ~127u; };
+  uint32_t o = 0;
+  l.off_cm = o;   o = al(o + (p.cm_rows * p.cm_width / 2u) * 4u);
+  l.off_ids = o;  o = al(o + std::max(l.idcap * 4u, (nb + nw) * 4u));  // fused: the bin minima live here first
+  l.off_est = o;  o = al(o + l.idcap);
+  l.off_pool = o; o = al(o + l.pcap * 4u);
+  l.off_bkey = o; o = al(o + l.nbk * 4u);
+  l.off_boff = o; o = al(o + 4u);
+  l.off_hist = o; o = al(o + kHistBins * 4u);
+  l.off_ctrl = o; o = al(o + 16u * 4u);
+  l.off_bar = o;  o = al(o + 8u);
+  l.bytes = o;
+  return l;
 }
 
 int run_hash(slash_index* ix, const uint64_t* offs, const uint32_t* cols, uint32_t n, uint64_t id0,
@@ -1503,6 +2034,71 @@ int insert_tail(slash_index* ix, uint32_t n, uint64_t id0, cudaStream_t st) {
     Launch l(ix, "k_merge_fallback", st);
     k_merge_big<<<ix->num_sms * 2, kBigThreads, 0, st>>>(ix->geo, ix->fb, ix->ctr + 1, 1, ix->fboff, ix->stage,
                                                        ix->slots, ix->fill, ix->meta);
+  }
+  SLASH_CK(cudaGetLastError());
+  return SLASH_OK;
+}
+
+// Resident CTAs per SM of a query kernel, looked up once per index and schedule
+// (later calls, e.g. under stream capture, make no occupancy query).
+int cached_bps(int& cached, const void* fn, uint32_t thr, size_t smem, int* out) {
+  if (cached == 0) {
+    int b = 0;
+    SLASH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, (int)thr, smem));
+    cached = b > 0 ? b : -1;
+  }
+  *out = cached;
+  return SLASH_OK;
+}
+
+const void* staged_fn(bool fused, uint32_t thr) {
+  if (fused)
+    return thr == 256 ? (const void*)k_query_staged<256, true>
+                      : thr == 512 ? (const void*)k_query_staged<512, true> : (const void*)k_query_staged<1024, true>;
+  return thr == 256 ? (const void*)k_query_staged<256, false>
+                    : thr == 512 ? (const void*)k_query_staged<512, false> : (const void*)k_query_staged<1024, false>;
+}
+
+// The staged engine on n queries (rows offs[0..n] of cols): fused (each CTA
+// hashes its queries) or plain (addresses qbkt[t*ldq + q] from the hash
+// kernel), then k_query_redo for the queries it left marked.
+int launch_staged(slash_index* ix, bool fused, uint32_t thr, uint32_t ctas_cap, const uint64_t* offs,
+                  const uint32_t* cols, const uint32_t* qbkt, uint64_t ldq, uint32_t n, uint32_t topk, int32_t* ids,
+                  uint32_t* scores, cudaStream_t st) {
+  StagedLayout lay = make_staged_layout(ix->p);
+  lay.extra_tx = ix->stall_copies ? 16u : 0u;
+  const int ti = thr == 256 ? 0 : thr == 512 ? 1 : 2;
+  int bps = 0;
+  int rc = cached_bps(ix->sbps[fused ? 0 : 1][ti], staged_fn(fused, thr), thr, lay.bytes, &bps);
+  if (rc) return rc;
+  if (bps < 1) return SLASH_EINVAL;
+  if (ctas_cap) bps = std::min<int>(bps, (int)ctas_cap);
+  const uint32_t grid = (uint32_t)std::min<uint64_t>(n, (uint64_t)ix->num_sms * bps);
+  // a private counter per launch: launches on different streams may overlap
+  uint32_t* work = ix->work + (ix->work_next.fetch_add(1u) % kWorkRing);
+  SLASH_CK(cudaMemsetAsync(work, 0, sizeof(uint32_t), st));
+  {
+    Launch lq(ix, fused ? "k_query_staged_fused" : "k_query_staged", st);
+#define SLASH_STAGED(T, F)                                                                                  \
+  k_query_staged<T, F><<<grid, T, lay.bytes, st>>>(ix->geo, lay, qbkt, ldq, offs, cols, n, topk, ix->slots, \
+                                                   ix->fill, ids, scores, work, ix->err)
+    if (fused) {
+      if (thr == 256) SLASH_STAGED(256, true); else if (thr == 512) SLASH_STAGED(512, true); else SLASH_STAGED(1024, true);
+    } else {
+      if (thr == 256) SLASH_STAGED(256, false); else if (thr == 512) SLASH_STAGED(512, false); else SLASH_STAGED(1024, false);
+    }
+#undef SLASH_STAGED
+  }
+  SLASH_CK(cudaGetLastError());
+  const uint32_t rt = ix->redo_threads;
+  const QueryLayout rl = make_query_layout(ix->p, rt);
+  const uint32_t rgrid = (uint32_t)std::min<uint64_t>((n + rt - 1) / rt, (uint64_t)ix->num_sms);
+  {
+    Launch lr(ix, "k_query_redo", st);
+#define SLASH_REDO(T) \
+  k_query_redo<T><<<rgrid, T, rl.bytes, st>>>(ix->geo, rl, offs, cols, n, topk, ix->slots, ix->fill, ids, scores, ix->err)
+    if (rt == 256) SLASH_REDO(256); else if (rt == 512) SLASH_REDO(512); else SLASH_REDO(1024);
+#undef SLASH_REDO
   }
   SLASH_CK(cudaGetLastError());
   return SLASH_OK;
@@ -1588,6 +2184,12 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
     uint32_t t = default_query_threads(*p);
     while (t > 256u && make_query_layout(*p, t).bytes > ix->smem_optin) t >>= 1;
     ix->qdef.threads = t;
+    ix->redo_threads = t;
+    // the staged engine: runs of 4 ids stay inside a bucket (R % 4 == 0), warp 0 plans
+    // at most kStagedMaxBuckets buckets, and its layout fits
+    ix->staged = p->reservoir % 4u == 0u && p->shards * p->L <= kStagedMaxBuckets &&
+                 make_staged_layout(*p).bytes <= ix->smem_optin;
+    if (ix->staged) ix->qdef.threads = 512;
   }
   const uint64_t nblk = (ix->nk + kScanTile - 1) / kScanTile;
   cudaError_t e = cudaSuccess;
@@ -1619,6 +2221,12 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
   cudaFuncSetAttribute(k_query_fused<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_query_fused<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_merge_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ix->smem_optin);
+#define SLASH_SATTR(T)                                                                                   \
+  cudaFuncSetAttribute(k_query_staged<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);       \
+  cudaFuncSetAttribute(k_query_staged<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);        \
+  cudaFuncSetAttribute(k_query_redo<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  SLASH_SATTR(256) SLASH_SATTR(512) SLASH_SATTR(1024)
+#undef SLASH_SATTR
   init_hash_kernels(so);
   *out = ix;
   return SLASH_OK;
@@ -1626,6 +2234,7 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
 
 int slash_insert(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_cols, uint32_t n_rows,
                  uint64_t* first_id_out, void* cuda_stream) {
+  ApiRange api("slash_insert");
   if (!ix) return SLASH_EINVAL;
   if (n_rows == 0) {
     if (first_id_out) *first_id_out = ix->next_id;
@@ -1650,6 +2259,7 @@ int slash_insert(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_cols
 
 int slash_insert_host(slash_index* ix, const uint64_t* h_offs, const uint32_t* h_cols, uint32_t n_rows,
                       uint64_t* first_id_out, void* cuda_stream) {
+  ApiRange api("slash_insert_host");
   if (!ix) return SLASH_EINVAL;
   if (n_rows == 0) {
     if (first_id_out) *first_id_out = ix->next_id;
@@ -1686,8 +2296,8 @@ int slash_insert_host(slash_index* ix, const uint64_t* h_offs, const uint32_t* h
     }
     ix->h2d_rows = ix->h2d_nnz = 0;
     for (int i = 0; i < 2; ++i) {
-      SLASH_CK(cudaMalloc(&ix->h2d_offs[i], sizeof(uint64_t) * (piece + 1)));
-      SLASH_CK(cudaMalloc(&ix->h2d_cols[i], sizeof(uint32_t) * std::max<uint64_t>(most_nnz, 1)));
+      SLASH_CK(ws_malloc(ix, (void**)&ix->h2d_offs[i], sizeof(uint64_t) * (piece + 1)));
+      SLASH_CK(ws_malloc(ix, (void**)&ix->h2d_cols[i], sizeof(uint32_t) * std::max<uint64_t>(most_nnz, 1)));
     }
     ix->h2d_rows = piece;
     ix->h2d_nnz = most_nnz;
@@ -1731,6 +2341,7 @@ int slash_insert_host(slash_index* ix, const uint64_t* h_offs, const uint32_t* h
 int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_cols, uint32_t n_queries,
                    uint32_t topk, int32_t* d_ids_out, uint32_t* d_scores_out, const slash_query_opts* opts,
                    void* cuda_stream) {
+  ApiRange api("slash_query");
   if (!ix || topk == 0 || topk > SLASH_MAX_TOPK) return SLASH_EINVAL;
   const slash_query_opts o = opts ? *opts : ix->qdef;
   if (o.mode != SLASH_QUERY_PLAIN && o.mode != SLASH_QUERY_FUSED) return SLASH_EINVAL;
@@ -1739,6 +2350,23 @@ int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
   if (n_queries == 0) return SLASH_OK;
   if (!d_offs || !d_cols || !d_ids_out || !d_scores_out) return SLASH_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (ix->staged && topk <= kLocalTop) {
+    if (o.mode == SLASH_QUERY_FUSED)
+      return launch_staged(ix, true, thr, o.ctas_per_sm, d_offs, d_cols, nullptr, 0, n_queries, topk, d_ids_out,
+                           d_scores_out, st);
+    const uint64_t chunk = std::min<uint64_t>(n_queries, 1ull << 22);
+    int rc = grow_query_ws(ix, chunk);
+    if (rc) return rc;
+    for (uint64_t q0 = 0; q0 < n_queries; q0 += chunk) {
+      const uint32_t n = (uint32_t)std::min<uint64_t>(chunk, n_queries - q0);
+      rc = run_hash(ix, d_offs + q0, d_cols, n, 0, ix->qbkt, n, nullptr, false, st);
+      if (rc) return rc;
+      rc = launch_staged(ix, false, thr, o.ctas_per_sm, d_offs + q0, d_cols, ix->qbkt, n, n, topk,
+                         d_ids_out + q0 * topk, d_scores_out + q0 * topk, st);
+      if (rc) return rc;
+    }
+    return SLASH_OK;
+  }
   const QueryLayout lay = make_query_layout(ix->p, thr);
   if (lay.bytes > ix->smem_optin) return SLASH_EINVAL;
   const void* fn = nullptr;
@@ -1750,13 +2378,8 @@ int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
   // resident CTAs per SM for this schedule, looked up once per index (so that
   // later calls, e.g. under stream capture, make no occupancy query)
   const int ti = thr == 256 ? 0 : thr == 512 ? 1 : 2;
-  int& cached = ix->qbps[o.mode == SLASH_QUERY_PLAIN ? 1 : 0][ti];
-  if (cached == 0) {
-    int b = 0;
-    SLASH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, (int)thr, lay.bytes));
-    cached = b > 0 ? b : -1;
-  }
-  int bps = cached;
+  int bps = 0;
+  SLASH_CK_RC(cached_bps(ix->qbps[o.mode == SLASH_QUERY_PLAIN ? 1 : 0][ti], fn, thr, lay.bytes, &bps));
   if (bps < 1) return SLASH_EINVAL;
   if (o.ctas_per_sm) bps = std::min<int>(bps, (int)o.ctas_per_sm);
   const uint64_t slots_per_gpu = (uint64_t)ix->num_sms * bps;
@@ -1869,7 +2492,7 @@ int slash_sync(slash_index* ix, void* cuda_stream) {
   SLASH_CK(cudaMemcpy(&e, ix->err, sizeof(uint32_t), cudaMemcpyDeviceToHost));
   if (e) {
     SLASH_CK(cudaMemset(ix->err, 0, sizeof(uint32_t)));
-    return SLASH_EDATA;
+    return (e & kErrWait) ? SLASH_ETIMEOUT : SLASH_EDATA;
   }
   return SLASH_OK;
 }
@@ -1970,6 +2593,18 @@ int slash_debug_hash(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_
   return run_hash(ix, d_offs, d_cols, n, 0, d_buckets, n, d_codes, false, (cudaStream_t)cuda_stream);
 }
 
+int slash_debug_stall_copies(slash_index* ix, int enable) {
+  if (!ix) return SLASH_EINVAL;
+  ix->stall_copies = enable != 0;
+  return ix->staged ? SLASH_OK : SLASH_EINVAL;
+}
+
+int slash_debug_fail_alloc(slash_index* ix, uint32_t count) {
+  if (!ix) return SLASH_EINVAL;
+  ix->fail_allocs = count;
+  return SLASH_OK;
+}
+
 int slash_debug_export(slash_index* ix, uint32_t* h_slots, uint32_t* h_fill) {
   if (!ix) return SLASH_EINVAL;
   SLASH_CK(cudaDeviceSynchronize());
@@ -2049,10 +2684,17 @@ extern "C" int slash_query_static(slash_index* ix, const uint64_t* d_offs, const
   int rc = static_scratch(cur, &qbkt);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (ix->staged && topk <= kLocalTop) {
+    rc = run_hash(ix, d_offs, d_cols, n_queries, 0, qbkt, n_queries, nullptr, false, st);
+    if (rc) return rc;
+    return launch_staged(ix, false, 512u, 0u, d_offs, d_cols, qbkt, n_queries, n_queries, topk, d_ids_out,
+                         d_scores_out, st);
+  }
   const QueryLayout lay = make_query_layout(ix->p, 512u);
   if (lay.bytes > ix->smem_optin) return SLASH_EINVAL;
   int bps = 0;
-  SLASH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_query<512>, 512, lay.bytes));
+  rc = cached_bps(ix->qbps[1][1], (const void*)k_query<512>, 512u, lay.bytes, &bps);  // plain, 512 threads
+  if (rc) return rc;
   if (bps < 1) return SLASH_EINVAL;
   rc = run_hash(ix, d_offs, d_cols, n_queries, 0, qbkt, n_queries, nullptr, false, st);
   if (rc) return rc;

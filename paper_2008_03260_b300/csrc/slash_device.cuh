@@ -17,6 +17,7 @@ constexpr uint32_t kGold32 = 0x9E3779B1u;   // odd multiplier of the K-code comb
 constexpr uint32_t kMaxShards = 64;
 constexpr uint32_t kErrCol = 1u;            // a feature id >= dim was skipped
 constexpr uint32_t kErrOffs = 2u;           // a row with d_offs[i+1] < d_offs[i] was read as empty
+constexpr uint32_t kErrWait = 4u;           // a bounded wait on a shared-memory copy gave up
 constexpr uint32_t kOptProbes = 32u;        // optimal densification: probes per empty bin, times nb
 
 // MurmurHash3 32-bit finaliser (Appleby): a bijection of uint32.

@@ -7,7 +7,11 @@ a slot finishes, the requests that arrived meanwhile are admitted in arrival
 order into the next batch, as long as the batch stays under
 ``max_batch_queries`` and the device bytes of all in-flight batches (CSR
 inputs + outputs) stay under ``mem_budget``.  A request that could never fit
-is refused (``SLASH_EBUSY``).  Latency = completion on the device - arrival.
+is refused (``SLASH_EBUSY``).  A request may carry a deadline: if it is still
+queued when its deadline passes it is cancelled (``SLASH_ETIMEOUT``, no
+result) instead of launched.  Latency = completion on the device - arrival;
+each result also records when its batch was launched, so a latency splits
+into time spent queued on the host and time on the device.
 
 The batching logic (:class:`Batcher`) is host code with no device calls; the
 device work is behind :class:`GpuExecutor`, which issues the fused query
@@ -24,6 +28,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 SLASH_EBUSY = -5
+SLASH_ETIMEOUT = -6
 
 
 @dataclass
@@ -32,6 +37,7 @@ class Request:
     offs: np.ndarray          # uint64 [nq+1], offs[0] == 0
     cols: np.ndarray          # uint32 [nnz]
     arrival: float            # seconds since the start of the run
+    deadline: float = math.inf  # cancel if not launched by then (seconds since the start)
 
     @property
     def nq(self) -> int:
@@ -88,6 +94,14 @@ class Batcher:
     def free_slots(self) -> list[int]:
         return [s for s, b in enumerate(self.inflight) if b is None]
 
+    def expire(self, now: float) -> list[Request]:
+        """Remove and return the queued requests whose deadline has passed."""
+        if not any(r.deadline < now for r in self.queue):
+            return []
+        gone = [r for r in self.queue if r.deadline < now]
+        self.queue = collections.deque(r for r in self.queue if r.deadline >= now)
+        return gone
+
     def next_batch(self, slot: int) -> Batch | None:
         """Requests in arrival order while the batch and the memory budget allow."""
         reqs, nq, nb = [], 0, 0
@@ -116,62 +130,98 @@ class Batcher:
         return bool(self.queue) or any(b is not None for b in self.inflight)
 
 
-def concat_csr(reqs: list[Request]) -> tuple[np.ndarray, np.ndarray]:
+def concat_csr(reqs: list[Request], offs_out: np.ndarray | None = None,
+               cols_out: np.ndarray | None = None) -> tuple[np.ndarray, np.ndarray]:
+    """One CSR batch of the requests' queries (into the given buffers if any)."""
     nqs = [r.nq for r in reqs]
-    offs = np.zeros(sum(nqs) + 1, dtype=np.uint64)
+    nq, nnz = sum(nqs), sum(len(r.cols) for r in reqs)
+    offs = np.zeros(nq + 1, dtype=np.uint64) if offs_out is None else offs_out[:nq + 1]
+    cols = np.empty(nnz, dtype=np.uint32) if cols_out is None else cols_out[:nnz]
+    offs[0] = 0
     pos, base = 0, 0
     for r in reqs:
-        offs[pos + 1:pos + r.nq + 1] = r.offs[1:] + base
+        offs[pos + 1:pos + r.nq + 1] = r.offs[1:] + np.uint64(base)
+        cols[base:base + len(r.cols)] = r.cols
         pos += r.nq
         base += len(r.cols)
-    cols = np.concatenate([r.cols for r in reqs]) if reqs else np.zeros(0, np.uint32)
     return offs, cols
 
 
-class GpuExecutor:
-    """One CUDA stream per slot; H2D of the batch, fused query, D2H of the results."""
+class _SlotBuffers:
+    """Page-locked host and device buffers of one slot, grown (doubling) only
+    when a batch needs more: after warm-up no batch pins or allocates memory."""
 
-    def __init__(self, ix, topk: int, slots: int, threads: int = 0):
+    def __init__(self, torch, topk: int, queries: int, nnz: int):
+        self.torch, self.topk = torch, topk
+        self.q_cap = self.nnz_cap = 0
+        self.ensure(queries, nnz)
+
+    def ensure(self, queries: int, nnz: int) -> None:
+        torch = self.torch
+        if queries > self.q_cap:
+            self.q_cap = max(queries, 2 * self.q_cap)
+            self.h_offs = torch.empty(self.q_cap + 1, dtype=torch.int64, pin_memory=True)
+            self.d_offs = torch.empty(self.q_cap + 1, dtype=torch.int64, device="cuda")
+            self.h_ids = torch.empty((self.q_cap, self.topk), dtype=torch.int32, pin_memory=True)
+            self.h_sc = torch.empty((self.q_cap, self.topk), dtype=torch.int32, pin_memory=True)
+            self.d_ids = torch.empty((self.q_cap, self.topk), dtype=torch.int32, device="cuda")
+            self.d_sc = torch.empty_like(self.d_ids)
+        if nnz > self.nnz_cap:
+            self.nnz_cap = max(nnz, 2 * self.nnz_cap, 1)
+            self.h_cols = torch.empty(self.nnz_cap, dtype=torch.int32, pin_memory=True)
+            self.d_cols = torch.empty(self.nnz_cap, dtype=torch.int32, device="cuda")
+
+
+class GpuExecutor:
+    """One CUDA stream and one set of preallocated buffers per slot: the batch
+    is written into the slot's page-locked buffers, copied to the device, queried
+    (fused schedule) and the results copied back, all on the slot's stream."""
+
+    def __init__(self, ix, topk: int, slots: int, threads: int = 0, queries: int = 1 << 12, nnz: int = 1 << 18):
         import torch
         self.torch = torch
         self.ix, self.topk, self.threads = ix, topk, threads
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.bufs = [_SlotBuffers(torch, topk, queries, nnz) for _ in range(slots)]
+        self.events = [torch.cuda.Event(enable_timing=True) for _ in range(slots)]
         self.ref = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         self.ref.record(torch.cuda.current_stream())
         self.ref.synchronize()
         self.t_ref = time.perf_counter()
 
-    def launch(self, slot: int, offs: np.ndarray, cols: np.ndarray):
+    def launch_reqs(self, slot: int, reqs: list[Request]):
         torch = self.torch
-        st = self.streams[slot]
-        nq = len(offs) - 1
+        st, b = self.streams[slot], self.bufs[slot]
+        nq, nnz = sum(r.nq for r in reqs), sum(len(r.cols) for r in reqs)
+        b.ensure(nq, nnz)
+        # the slot's previous batch has completed (the loop only reuses a free
+        # slot), so its host buffers can be overwritten
+        concat_csr(reqs, b.h_offs.numpy().view(np.uint64), b.h_cols.numpy().view(np.uint32))
         with torch.cuda.stream(st):
-            h_offs = torch.from_numpy(offs.view(np.int64)).pin_memory()
-            h_cols = torch.from_numpy(cols.view(np.int32)).pin_memory()
-            d_offs = h_offs.to("cuda", non_blocking=True)
-            d_cols = h_cols.to("cuda", non_blocking=True)
-            d_ids = torch.empty((nq, self.topk), dtype=torch.int32, device="cuda")
-            d_sc = torch.empty_like(d_ids)
-            self.ix.query(d_offs, d_cols, self.topk, st, d_ids_out=d_ids, d_scores_out=d_sc, mode="fused",
-                          threads=self.threads)
-            h_ids = torch.empty((nq, self.topk), dtype=torch.int32, pin_memory=True)
-            h_sc = torch.empty((nq, self.topk), dtype=torch.int32, pin_memory=True)
-            h_ids.copy_(d_ids, non_blocking=True)
-            h_sc.copy_(d_sc, non_blocking=True)
-            ev = torch.cuda.Event(enable_timing=True)
+            b.d_offs[:nq + 1].copy_(b.h_offs[:nq + 1], non_blocking=True)
+            b.d_cols[:nnz].copy_(b.h_cols[:nnz], non_blocking=True)
+            self.ix.query(b.d_offs[:nq + 1], b.d_cols[:max(nnz, 1)], self.topk, st, d_ids_out=b.d_ids,
+                          d_scores_out=b.d_sc, mode="fused", threads=self.threads)
+            b.h_ids[:nq].copy_(b.d_ids[:nq], non_blocking=True)
+            b.h_sc[:nq].copy_(b.d_sc[:nq], non_blocking=True)
+            ev = self.events[slot]
             ev.record(st)
-        # keep every buffer alive until the event completes
-        return (ev, h_offs, h_cols, d_offs, d_cols, d_ids, d_sc, h_ids, h_sc)
+        return (ev, slot, nq)
+
+    def launch(self, slot: int, offs: np.ndarray, cols: np.ndarray):
+        """A batch given as one CSR array (offs[0] == 0)."""
+        return self.launch_reqs(slot, [Request(-1, offs, cols, 0.0)])
 
     def done(self, h) -> bool:
         return h[0].query()
 
     def collect(self, h) -> tuple[np.ndarray, np.ndarray, float]:
-        ev = h[0]
+        ev, slot, nq = h
         ev.synchronize()
         t_done = self.t_ref + self.ref.elapsed_time(ev) / 1e3
-        return h[7].numpy(), h[8].numpy().view(np.uint32), t_done
+        b = self.bufs[slot]
+        return b.h_ids[:nq].numpy().copy(), b.h_sc[:nq].numpy().view(np.uint32).copy(), t_done
 
 
 def serve(requests: list[Request], executor, *, topk: int, slots: int = 4, mem_budget: int = 16 << 30,
@@ -196,13 +246,19 @@ def serve(requests: list[Request], executor, *, topk: int, slots: int = 4, mem_b
                     rr.ids, rr.scores = ids[q:q + r.nq], sc[q:q + r.nq]
                     rr.launched, rr.done = b.launched, t_done - t0
                     q += r.nq
+        if realtime:
+            for r in bat.expire(time.perf_counter() - t0):
+                res[r.rid].status = SLASH_ETIMEOUT
         for s in bat.free_slots():
             b = bat.next_batch(s)
             if b is None:
                 break
-            offs, cols = concat_csr(b.reqs)
             b.launched = time.perf_counter() - t0
-            b.handle = executor.launch(s, offs, cols)
+            if hasattr(executor, "launch_reqs"):
+                b.handle = executor.launch_reqs(s, b.reqs)
+            else:
+                offs, cols = concat_csr(b.reqs)
+                b.handle = executor.launch(s, offs, cols)
             n_batches += 1
         if not bat.queue and pending and realtime:
             wait = pending[0].arrival - (time.perf_counter() - t0)
@@ -214,17 +270,26 @@ def serve(requests: list[Request], executor, *, topk: int, slots: int = 4, mem_b
     lat = np.array([r.latency for r in done]) if done else np.zeros(1)
     nq = sum(q.nq for q in requests if res[q.rid].status == 0)
     span = max(r.done for r in done) - min(r.arrival for r in done) if done else 1.0
-    summary = {"requests": len(done), "refused": len(bat.refused), "queries": nq, "batches": n_batches,
-               "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+    p99 = float(np.percentile(lat, 99))
+    tail = [r for r in done if r.latency >= p99] or done
+    summary = {"requests": len(done), "refused": len(bat.refused),
+               "cancelled": sum(1 for r in res.values() if r.status == SLASH_ETIMEOUT),
+               "queries": nq, "batches": n_batches,
+               "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * p99,
                "mean_ms": 1e3 * float(lat.mean()), "queries_per_s": nq / span if span > 0 else float("nan"),
-               "span_s": span}
+               "span_s": span,
+               # where the slowest 1% spent their time: queued on the host before
+               # launch, and from launch to completion on the device
+               "p99_queued_ms": 1e3 * float(np.mean([r.launched - r.arrival for r in tail])) if tail else 0.0,
+               "p99_device_ms": 1e3 * float(np.mean([r.done - r.launched for r in tail])) if tail else 0.0}
     return list(res.values()), summary
 
 
 def poisson_requests(rate: float, n: int, pool_offs: np.ndarray, pool_cols: np.ndarray, *, seed: int = 0,
-                     max_size: int = 4096, start: float = 0.0) -> list[Request]:
+                     max_size: int = 4096, start: float = 0.0, timeout: float = math.inf) -> list[Request]:
     """n requests with exponential inter-arrival times (rate per second) and
-    log-uniform sizes floor(max_size^u) in [1, max_size], cut from a query pool."""
+    log-uniform sizes floor(max_size^u) in [1, max_size], cut from a query pool;
+    each must be launched within `timeout` seconds of its arrival."""
     rng = np.random.default_rng(seed)
     t = start + np.cumsum(rng.exponential(1.0 / rate, n))
     sizes = np.clip(np.floor(max_size ** rng.random(n)).astype(np.int64), 1, max_size)
@@ -235,5 +300,5 @@ def poisson_requests(rate: float, n: int, pool_offs: np.ndarray, pool_cols: np.n
         b = min(npool, a + int(sizes[i]))
         o = pool_offs[a:b + 1]
         c = pool_cols[int(o[0]):int(o[-1])]
-        out.append(Request(i, (o - o[0]).astype(np.uint64), c, float(t[i])))
+        out.append(Request(i, (o - o[0]).astype(np.uint64), c, float(t[i]), float(t[i]) + timeout))
     return out

@@ -195,6 +195,52 @@ def test_query_heavy_collisions_and_capped_estimates():
     assert np.array_equal(_host_u32(sc), want_sc)
 
 
+@pytest.mark.parametrize("shards,L,R,d", [(1, 128, 128, 1), (4, 64, 32, 1), (2, 64, 64, 2)])
+def test_query_capped_bin_decides_top10(shards, L, R, d):
+    """k = 10 with a 32-wide sketch and up to 16k candidate occurrences: most
+    estimates reach the 255 cap, so the cap bin alone decides the top-k.  Where
+    its pool would outgrow the bound of the staged query, that query is
+    answered again by the general one; both paths against the oracle."""
+    s = _slash()
+    g = datagen.Generator()
+    n = 20_000
+    offs, cols = g.rows(21, 0, n)
+    qo, qc = _queries(g, n, 200, seed=22)
+    p = s.Params(K=2, L=L, log2_buckets=3, reservoir=R, cm_rows=d, cm_width=32, shards=shards, capacity=n, seed=21)
+    want_ids, want_sc = _oracle_index(p, offs, cols).query(qo, qc, 10)
+    assert want_sc.max() >= 255
+    with s.Index(p) as ix:
+        ix.insert(_dev(offs), _dev(cols))
+        for mode in ("fused", "plain"):
+            ids, sc = ix.query(_dev(qo), _dev(qc), 10, mode=mode)
+            ix.sync()
+            assert np.array_equal(ids.cpu().numpy(), want_ids), mode
+            assert np.array_equal(_host_u32(sc), want_sc), mode
+
+
+def test_query_few_distinct_ids_many_occurrences_pads():
+    """One row inserted many times: its query meets more than 64 occurrences of
+    fewer than k distinct ids, so the top-10 is padded with (-1, 0)."""
+    s = _slash()
+    g = datagen.Generator()
+    offs, cols = g.rows(23, 0, 300)
+    row = cols[int(offs[7]):int(offs[8])]
+    rows = [cols[int(offs[i]):int(offs[i + 1])] for i in range(300)]
+    rows = rows[:50] + [row] * 6 + rows[50:]
+    o2, c2 = _csr(rows)
+    qo, qc = _csr([row, row[: len(row) // 2], np.zeros(0, np.uint32)])
+    p = s.Params(K=4, L=16, log2_buckets=16, reservoir=32, cm_rows=4, cm_width=4096, capacity=1000, seed=23)
+    want_ids, want_sc = _oracle_index(p, o2, c2).query(qo, qc, 10)
+    assert (want_ids[0] == -1).any() and want_ids[0][0] >= 0
+    with s.Index(p) as ix:
+        ix.insert(_dev(o2), _dev(c2))
+        for mode in ("fused", "plain"):
+            ids, sc = ix.query(_dev(qo), _dev(qc), 10, mode=mode)
+            ix.sync()
+            assert np.array_equal(ids.cpu().numpy(), want_ids), mode
+            assert np.array_equal(_host_u32(sc), want_sc), mode
+
+
 def test_invalid_columns_are_skipped_and_reported():
     s = _slash()
     g = datagen.Generator()
@@ -240,8 +286,10 @@ def test_argument_errors():
         assert fill.max() == 0 and np.all(slots == EMPTY)
 
 
-@pytest.mark.parametrize("shards,R,B,w", [(1, 32, 16, 4096), (8, 16, 8, 8192), (2, 128, 12, 1024)])
-def test_every_query_schedule_is_bit_exact(shards, R, B, w):
+@pytest.mark.parametrize("shards,R,B,w,topk", [(1, 32, 16, 4096, 20), (8, 16, 8, 8192, 20), (2, 128, 12, 1024, 20),
+                                                (1, 32, 16, 4096, 10), (8, 16, 8, 8192, 10), (2, 128, 12, 1024, 7),
+                                                (4, 30, 9, 2048, 10)])
+def test_every_query_schedule_is_bit_exact(shards, R, B, w, topk):
     """Fused persistent and plain per-stage kernels, every CTA size and CTAs/SM
     cap: the same ids and scores as the oracle (integer work, tolerance zero)."""
     s = _slash()
@@ -251,20 +299,20 @@ def test_every_query_schedule_is_bit_exact(shards, R, B, w):
     qo, qc = _queries(g, n, 700, seed=13, planted_frac=0.3, p_perturb=0.2)
     p = s.Params(K=4, L=16, log2_buckets=B, reservoir=R, cm_rows=4, cm_width=w, shards=shards,
                  capacity=n, seed=12)
-    want_ids, want_sc = _oracle_index(p, offs, cols).query(qo, qc, 20)
+    want_ids, want_sc = _oracle_index(p, offs, cols).query(qo, qc, topk)
     with s.Index(p) as ix:
         ix.insert(_dev(offs), _dev(cols))
         dq, dc = _dev(qo), _dev(qc)
         for mode in ("fused", "plain"):
             for threads in (256, 512, 1024):
                 for cps in (0, 1):
-                    ids, sc = ix.query(dq, dc, 20, mode=mode, threads=threads, ctas_per_sm=cps)
+                    ids, sc = ix.query(dq, dc, topk, mode=mode, threads=threads, ctas_per_sm=cps)
                     ix.sync()
                     assert np.array_equal(ids.cpu().numpy(), want_ids), (mode, threads, cps)
                     assert np.array_equal(_host_u32(sc), want_sc), (mode, threads, cps)
-        best, ms = ix.autotune(dq, dc, 20)
+        best, ms = ix.autotune(dq, dc, topk)
         assert ms > 0 and best.threads in (256, 512, 1024)
-        ids, sc = ix.query(dq, dc, 20)   # the tuned default
+        ids, sc = ix.query(dq, dc, topk)   # the tuned default
         ix.sync()
         assert np.array_equal(ids.cpu().numpy(), want_ids)
         assert np.array_equal(_host_u32(sc), want_sc)

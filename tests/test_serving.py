@@ -127,3 +127,24 @@ def test_gpu_serving_results_equal_alone():
     for q in reqs[:40]:
         want_ids, want_sc = oix.query(q.offs, q.cols, 10)
         assert np.array_equal(by[q.rid].ids, want_ids) and np.array_equal(by[q.rid].scores, want_sc)
+
+
+def test_queued_requests_past_their_deadline_are_cancelled():
+    """A deadline that passes while the request waits in the queue cancels it
+    (SLASH_ETIMEOUT, no result); the others are answered as usual."""
+    from paper_2008_03260_b300.serve import SLASH_ETIMEOUT, Request, serve
+    qo, qc = _pool(40)
+    reqs = []
+    for i in range(12):
+        o = qo[i * 3:i * 3 + 4]
+        dl = 0.005 if i % 3 == 2 else float("inf")     # a third must start within 5 ms
+        reqs.append(Request(i, (o - o[0]).astype(np.uint64), qc[int(o[0]):int(o[-1])], 0.0, dl))
+    ex = FakeExecutor(topk=4, delay=0.05)                # one slot, 50 ms per batch
+    res, summ = serve(reqs, ex, topk=4, slots=1, mem_budget=1 << 20, max_batch_queries=3)
+    by = {r.rid: r for r in res}
+    assert by[0].status == 0 and by[0].ids is not None   # launched at once
+    late = [i for i in range(12) if i % 3 == 2 and i > 0]
+    assert all(by[i].status == SLASH_ETIMEOUT and by[i].ids is None for i in late)
+    assert all(by[i].status == 0 for i in range(12) if i not in late)
+    assert summ["cancelled"] == len(late) and summ["requests"] == 12 - len(late)
+    assert summ["p99_queued_ms"] >= 0 and summ["p99_device_ms"] >= 0
