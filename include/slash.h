@@ -176,6 +176,49 @@ int slash_autotune(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_co
 int slash_query_static(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n_queries,
                        uint32_t topk, int32_t *d_ids_out, uint32_t *d_scores_out, void *cuda_stream);
 
+/* ---- One logical index over several processes (Sec. 3 partitions; Algorithm 2's
+ * merge across machines as one exchange of candidates).  Process r indexes the
+ * ids [ceil(r*N/W), ceil((r+1)*N/W)) of N rows (W processes, one index each
+ * with shards = 1, capacity = N and the shared seed).  A query batch, the same
+ * on every process, is answered by: slash_query_candidates on each process; an
+ * all-gather of the counts and ids; slash_query_cells on each process; a sum
+ * over processes of the cells; slash_rank_candidates.  Because partitions hold
+ * disjoint ids, the summed cells are those of the one index whose shards are
+ * the partitions, and the ranking is identical to its slash_query. */
+
+/* Rows inserted next get ids from next_id on (the first global id of this
+ * process's partition).  next_id may not be below the index's next id nor above
+ * its capacity (else SLASH_EINVAL). */
+int slash_set_next_id(slash_index *ix, uint64_t next_id);
+
+/* Each query's distinct candidates in this index (the ids of its S*L buckets):
+ * d_counts int32 [n_queries], d_ids int32 [n_queries][m] in ascending order, -1
+ * past the count; m >= S*L*R.  Uses the plain-query workspace (SLASH_ENOMEM
+ * if it cannot grow).  Errors: SLASH_EINVAL (m too small, NULL, or S*L*R too
+ * large for one CTA's shared memory), SLASH_ENOMEM, SLASH_ECUDA. */
+int slash_query_candidates(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n_queries,
+                           uint32_t m, int32_t *d_counts, int32_t *d_ids, void *cuda_stream);
+
+/* This index's count-min cells of the gathered candidates: for process w <
+ * world, query q and j < m, d_cells[((w*n_queries + q)*m + j)*d + r] = this
+ * index's sketch count in row r (d = cm_rows) at the cell of d_ids[(w*n_queries
+ * + q)*m + j], the sketch being the one query q builds from its own buckets;
+ * 0 for j >= d_counts[w*n_queries + q].  Errors as slash_query_candidates
+ * (world 1..64). */
+int slash_query_cells(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n_queries,
+                      uint32_t world, uint32_t m, const int32_t *d_counts, const int32_t *d_ids, uint32_t *d_cells,
+                      void *cuda_stream);
+
+/* The ranking of Algorithm 2 from gathered candidates and their cells summed
+ * over processes: per query, every id j < d_counts[w*n_queries + q] of every
+ * process w gets the estimate min over r of its d cells; the top-k by (estimate
+ * descending, id ascending) go to d_ids_out int32 [n_queries][topk] and
+ * d_scores_out uint32 (padding -1 / 0).  Needs no index.  Errors: SLASH_EINVAL
+ * (world 1..64, d 1..SLASH_MAX_CMROWS, topk 1..SLASH_MAX_TOPK, NULL), SLASH_ECUDA. */
+int slash_rank_candidates(uint32_t world, uint32_t n_queries, uint32_t m, uint32_t d, const int32_t *d_counts,
+                          const int32_t *d_ids, const uint32_t *d_cells, uint32_t topk, int32_t *d_ids_out,
+                          uint32_t *d_scores_out, void *cuda_stream);
+
 /* Checkpoint (no counterpart in the paper, whose index lives only for one run):
  * write the whole index state -- parameters, the next id, fill counts and
  * bucket slots -- to the file `path` (created or truncated), after a header
@@ -246,6 +289,11 @@ int slash_debug_hash(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_
 int slash_probe_smem(uint32_t mode, uint32_t words, uint32_t iters, uint32_t threads, uint32_t ctas_per_sm,
                      float *ms_out, uint64_t *ops_out);
 
+/* Test support -- resident CTAs per SM that the occupancy calculator allows
+ * the query kernel of schedule (mode, threads) at this index's shape, before any
+ * cap the launch applies.  Errors: SLASH_EINVAL, SLASH_ECUDA. */
+int slash_debug_occupancy(slash_index *ix, uint32_t mode, uint32_t threads, int *ctas_per_sm_out);
+
 /* Test support -- the next `count` device allocations this index makes for its
  * workspace (insert, plain-query and host-staging buffers) fail as if the device
  * were out of memory: the call that needed them returns SLASH_ENOMEM before any
@@ -254,7 +302,8 @@ int slash_probe_smem(uint32_t mode, uint32_t words, uint32_t iters, uint32_t thr
 int slash_debug_fail_alloc(slash_index *ix, uint32_t count);
 
 /* Test support -- while enabled, the shared-memory copy wait of the staged
- * query engine (the one serving topk <= 10 when R is a multiple of 4) waits for
+ * query engine (the one serving topk <= 10 when R is a multiple of 4 and S*L <=
+ * 128) waits for
  * 16 bytes that no copy delivers, so every such wait gives up after its 1 s
  * limit: the kernel sets the sticky error word and returns, the next
  * slash_sync() reports SLASH_ETIMEOUT, and the device stays usable.  Query

@@ -86,6 +86,8 @@ def _load():
             lib.or_query.argtypes = [vp, vp, vp, u64, u32, vp, vp]
             lib.or_next_id.restype = u64
             lib.or_next_id.argtypes = [vp]
+            lib.or_set_next_id.restype = i32
+            lib.or_set_next_id.argtypes = [vp, u64]
             lib.or_tk_update.argtypes = [ctypes.POINTER(u32), ctypes.POINTER(u32), u32]
             lib.or_tk_merge_cell.argtypes = [ctypes.POINTER(u32), ctypes.POINTER(u32), u32, u32]
             lib.or_tk_new.restype = vp
@@ -227,6 +229,11 @@ class Index:
     @property
     def next_id(self) -> int:
         return int(self._lib.or_next_id(self._h))
+
+    def set_next_id(self, id_: int) -> None:
+        """Rows inserted next take ids from id_ on (a partition starting at its global id)."""
+        if self._lib.or_set_next_id(self._h, id_):
+            raise ValueError("next id must not go back nor pass the capacity")
 
     def insert(self, offs, cols, threads: int = 1) -> int:
         offs, cols = _u64(offs), _u32(cols)

@@ -515,6 +515,16 @@ int or_query(const void *p, const uint64_t *offs, const uint32_t *cols, uint64_t
 
 uint64_t or_next_id(const void *p) { return ((const or_index *)p)->next_id; }
 
+/* Rows inserted next take ids from `id` on: a partition D_i of Sec. 3 built on
+ * its own starts at its first global id.  Only forward; -1 if id < next id or
+ * id > capacity. */
+int or_set_next_id(void *p, uint64_t id) {
+  or_index *ix = (or_index *)p;
+  if (id < ix->next_id || id > ix->capacity) return -1;
+  ix->next_id = id;
+  return 0;
+}
+
 /* ------------------------------------------------------------------ TopKAPI buckets
  * SLASH's own bucket (Sec. 3.1 and Appendix 2): every bucket address holds a
  * TopKAPI sketch of W rows x Bc cells, each cell a (heavy hitter, count) pair,

@@ -96,7 +96,12 @@ def _load() -> ctypes.CDLL:
         "slash_debug_hash": (i32, [vp, vp, vp, u32, vp, vp, vp]),
         "slash_debug_export": (i32, [vp, vp, vp]),
         "slash_debug_fail_alloc": (i32, [vp, u32]),
+        "slash_debug_occupancy": (i32, [vp, u32, u32, P(ctypes.c_int)]),
         "slash_probe_smem": (i32, [u32, u32, u32, u32, u32, P(ctypes.c_float), P(u64)]),
+        "slash_set_next_id": (i32, [vp, u64]),
+        "slash_query_candidates": (i32, [vp, vp, vp, u32, u32, vp, vp, vp]),
+        "slash_query_cells": (i32, [vp, vp, vp, u32, u32, u32, vp, vp, vp, vp]),
+        "slash_rank_candidates": (i32, [u32, u32, u32, u32, vp, vp, vp, u32, vp, vp, vp]),
         "slash_debug_stall_copies": (i32, [vp, i32]),
         "slash_debug_buckets": (i32, [vp, vp, vp, vp, u32, vp, vp]),
         "slash_query_ex": (i32, [vp, vp, vp, u32, u32, vp, vp, P(slash_query_opts), vp]),
@@ -299,6 +304,44 @@ def slash_debug_fail_alloc(ix: int, count: int) -> None:
     _check(_lib.slash_debug_fail_alloc(ix, count), "slash_debug_fail_alloc")
 
 
+def slash_set_next_id(ix: int, next_id: int) -> None:
+    """Rows inserted next take ids from next_id on (a partition starting at its global id)."""
+    _check(_lib.slash_set_next_id(ix, next_id), "slash_set_next_id")
+
+
+def slash_query_candidates(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, m: int, stream=None):
+    """Each query's distinct local candidates: counts int32 [nq], ids int32 [nq, m] (ascending, -1 past the count)."""
+    nq = d_offs.numel() - 1
+    counts = torch.empty(nq, dtype=torch.int32, device=d_offs.device)
+    ids = torch.empty((nq, m), dtype=torch.int32, device=d_offs.device)
+    _check(_lib.slash_query_candidates(ix, _dev_ptr(d_offs, 8, "d_offs"), _dev_ptr(d_cols, 4, "d_cols"), nq, m,
+                                       counts.data_ptr(), ids.data_ptr(), _stream(stream)), "slash_query_candidates")
+    return counts, ids
+
+
+def slash_query_cells(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, ids: torch.Tensor, counts: torch.Tensor,
+                      d: int, stream=None) -> torch.Tensor:
+    """This index's count-min cells of gathered candidates ids [W, nq, m] (counts [W, nq]): int32 [W, nq, m, d]."""
+    W, nq, m = ids.shape
+    cells = torch.empty((W, nq, m, d), dtype=torch.int32, device=ids.device)
+    _check(_lib.slash_query_cells(ix, _dev_ptr(d_offs, 8, "d_offs"), _dev_ptr(d_cols, 4, "d_cols"), nq, W, m,
+                                  _dev_ptr(counts, 4, "counts"), _dev_ptr(ids, 4, "ids"), cells.data_ptr(),
+                                  _stream(stream)), "slash_query_cells")
+    return cells
+
+
+def slash_rank_candidates(ids: torch.Tensor, counts: torch.Tensor, cells: torch.Tensor, topk: int, stream=None):
+    """Top-k (ids int32 [nq, k], scores int32 [nq, k]) from gathered ids and their summed cells."""
+    W, nq, m = ids.shape
+    d = cells.shape[-1]
+    out_ids = torch.empty((nq, topk), dtype=torch.int32, device=ids.device)
+    out_sc = torch.empty((nq, topk), dtype=torch.int32, device=ids.device)
+    _check(_lib.slash_rank_candidates(W, nq, m, d, _dev_ptr(counts, 4, "counts"), _dev_ptr(ids, 4, "ids"),
+                                      _dev_ptr(cells, 4, "cells"), topk, out_ids.data_ptr(), out_sc.data_ptr(),
+                                      _stream(stream)), "slash_rank_candidates")
+    return out_ids, out_sc
+
+
 def slash_probe_smem(mode: int, words: int = 16384, iters: int = 4096, threads: int = 512,
                      ctas_per_sm: int = 2) -> tuple[float, int]:
     """Shared-memory microbenchmark (see include/slash.h): (ms, operations)."""
@@ -306,6 +349,14 @@ def slash_probe_smem(mode: int, words: int = 16384, iters: int = 4096, threads: 
     _check(_lib.slash_probe_smem(mode, words, iters, threads, ctas_per_sm, ctypes.byref(ms), ctypes.byref(ops)),
            "slash_probe_smem")
     return float(ms.value), int(ops.value)
+
+
+def slash_debug_occupancy(ix: int, mode, threads: int) -> int:
+    """Test support: CTAs per SM the occupancy calculator allows the query kernel of a schedule."""
+    m = {"fused": SLASH_QUERY_FUSED, "plain": SLASH_QUERY_PLAIN}.get(mode, mode)
+    out = ctypes.c_int()
+    _check(_lib.slash_debug_occupancy(ix, int(m), threads, ctypes.byref(out)), "slash_debug_occupancy")
+    return int(out.value)
 
 
 def slash_debug_stall_copies(ix: int, enable: bool) -> None:
@@ -395,6 +446,9 @@ class Index:
 
     def insert(self, d_offs, d_cols, stream=None) -> int:
         return slash_insert(self.h, d_offs, d_cols, stream)
+
+    def set_next_id(self, next_id: int) -> None:
+        slash_set_next_id(self.h, next_id)
 
     def insert_host(self, h_offs, h_cols, stream=None) -> int:
         return slash_insert_host(self.h, h_offs, h_cols, stream)

@@ -1182,24 +1182,30 @@ k_query_fused(const __grid_constant__ Geo g, const QueryLayout lay, const uint64
 // ----------------------------------------------------------------------------- query, staged
 // The query engine for the common case (R a multiple of 4, k <= kLocalTop, at
 // most kStagedMaxBuckets buckets per query); query_core stays the general one.
-// Per query (Algorithm 2, local and cross-partition merge):
-//   - warp 0 reads the S*L bucket keys and fills and issues one bulk copy per
-//     non-empty bucket (cp.async.bulk, completed on an mbarrier), moving its
-//     ids into a shared-memory buffer; a bucket's run is rounded up to 4 ids,
-//     which is safe because the slots past a bucket's fill hold 0xFFFFFFFF.
-//     Meanwhile the other warps clear the sketch;
-//   - every thread counts its share of the buffer into the packed sketch;
-//   - each occurrence's estimate is computed once and kept as a byte (255 =
-//     "at least 255", recomputed exactly where it matters), with a histogram;
+// A team of threads answers one query at a time (Algorithm 2, local and
+// cross-partition merge):
+//   - its warp 0 issues one bulk copy per non-empty bucket (cp.async.bulk,
+//     completed on an mbarrier), moving the bucket's ids into a shared-memory
+//     buffer; a bucket's run is rounded up to 4 ids, which is safe because the
+//     slots past a bucket's fill hold 0xFFFFFFFF.  With the plain schedule the
+//     keys and fills of the next query are already in the warp's registers:
+//     they were loaded while the previous query was counted;
+//   - every thread counts its share of the buffer into the packed sketch.  With
+//     four rows each thread keeps the 16 cells of its 4-id groups in its lane
+//     of tensor memory (TMEM), so the estimates need no second hashing;
+//   - each occurrence's estimate is kept as a byte (255 = "at least 255",
+//     recomputed exactly where it matters), with a histogram;
 //   - cut-off and tie bound exactly as in query_core.  The pool holds buffer
 //     indices; by the cut-off's construction it has fewer than (2k+1)*S*L
 //     entries unless the capped bin (estimates >= 255) decides.  That query is
 //     marked (id -2 in its first output slot) and answered by k_query_redo;
-//   - warp 0 ranks the pool with per-lane register lists (k <= kLocalTop).
-// A CTA needs about 110 KB of shared memory at the criteo shape (64 KB of
-// sketch, 32 KB of ids), so two 512-thread CTAs share an SM: one CTA's
-// single-warp phases overlap the other's counting.
-constexpr uint32_t kStagedMaxBuckets = 256;     // S*L of the staged engine
+//   - one warp per 256 pool entries keeps per-lane register lists (k <=
+//     kLocalTop); warp minima (two 32-bit reductions) merge them.
+// A team needs about 110 KB of shared memory at the criteo shape (64 KB of
+// sketch, 32 KB of ids).  Kernels holding TMEM run one CTA per SM, so their CTA
+// carries two such teams: one team's single-warp phases overlap the other's
+// counting.
+constexpr uint32_t kStagedMaxBuckets = 128;     // S*L of the staged engine (the issuing warp holds 4 per lane)
 constexpr uint64_t kStagedWaitNs = 1000000000ull;   // bounded mbarrier wait: 1 s of %globaltimer
 constexpr uint64_t kStagedDrainNs = 100000000ull;   // after a timeout: 0.1 s for copies still in flight
 constexpr int32_t kRedoMark = -2;               // first output id of a query left to k_query_redo
@@ -1211,6 +1217,7 @@ struct StagedLayout {
   uint32_t pcap;     // pool entries, (2k+1)*S*L for k = kLocalTop
   uint32_t off_cm, off_ids, off_est, off_pool, off_bkey, off_boff, off_hist, off_ctrl, off_bar, bytes;
   uint32_t extra_tx;  // test support: bytes announced on the mbarrier beyond the copies (0 in service)
+  uint32_t tmem_cols, tmem_j;  // four-row sketches: TMEM columns per CTA, 4-id groups per thread
 };
 
 enum { S_NPOOL = 0, S_ELO, S_PFX, S_NEED, S_Q, S_TOT, S_N };
@@ -1265,24 +1272,96 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
-// Warp 0: read the fills of the buckets in bkey[0..nbk), lay their runs out in
-// the id buffer (bucket order, each rounded up to 4 ids), announce the bytes on
-// the mbarrier and issue the copies.  Returns the buffer's length in ids.
-__device__ __forceinline__ void staged_issue(const Geo& g, const StagedLayout& lay, unsigned char* qsm,
-                                             const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill,
-                                             uint32_t bar, uint32_t lane) {
-  constexpr int kPer = kStagedMaxBuckets / 32;
-  const uint32_t* bkey = reinterpret_cast<const uint32_t*>(qsm + lay.off_bkey);
-  uint32_t* ctrl = reinterpret_cast<uint32_t*>(qsm + lay.off_ctrl);
-  const uint32_t ids_s = smem_u32(qsm + lay.off_ids);
-  uint32_t f[kPer], key[kPer], sum = 0;
+// Tensor memory (TMEM) as a per-thread cache of the sketch cells: every warp
+// reaches the 32 TMEM lanes of its quadrant (warp % 4), each thread its own lane.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {  // one whole warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {  // the allocating warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before_sync() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_fence_after_sync() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// 8 consecutive 32-bit columns of this thread's lane (whole warp)
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+      : "r"(taddr)
+      : "memory");
+}
+
+// A team: threads [id*T, (id + 1)*T) of a CTA that answer queries on their own,
+// with their own shared-memory layout, mbarrier and named barrier 1 + id.
+// Kernels that take tensor memory run one CTA per SM, so a CTA holds up to four
+// teams to keep several queries in flight per SM.
+struct Team {
+  uint32_t id, T, tid, warp, lane;
+  __device__ __forceinline__ void sync() const {
+    asm volatile("bar.sync %0, %1;" ::"r"(1u + id), "r"(T) : "memory");
+  }
+  // barrier that also returns whether any thread of the team passed pred
+  __device__ __forceinline__ bool sync_or(bool pred) const {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred q, o;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred o, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, o;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(1u + id), "r"(T)
+        : "memory");
+    return r != 0u;
+  }
+};
+
+constexpr int kPer = kStagedMaxBuckets / 32;  // buckets per lane of the issuing warp
+
+// Issuing warp: the keys of a query's S*L buckets from the hash kernel's
+// addresses (lane l holds buckets l*kPer + j).
+__device__ __forceinline__ void staged_keys(const Geo& g, const StagedLayout& lay, const uint32_t* __restrict__ qbkt,
+                                            uint64_t ldq, uint32_t q, uint32_t lane, uint32_t (&key)[kPer]) {
 #pragma unroll
   for (int j = 0; j < kPer; ++j) {
-    const uint32_t i = lane * kPer + j;  // a lane's buckets are consecutive: runs stay in bucket order
-    key[j] = i < lay.nbk ? bkey[i] : 0u;
-    f[j] = i < lay.nbk ? min(__ldg(fill + key[j]), g.R) : 0u;  // a fill never exceeds R; the copy stays in bounds
-    sum += (f[j] + 3u) & ~3u;
+    const uint32_t i = lane * kPer + j;
+    key[j] = 0u;
+    if (i < lay.nbk) {
+      const uint32_t s = i / g.L, t = i - s * g.L;
+      key[j] = ((s * g.L + t) << g.B) | __ldg(qbkt + t * ldq + q);
+    }
   }
+}
+
+// Issuing warp: the fills of those buckets (never above R: a copy stays inside its bucket).
+__device__ __forceinline__ void staged_fills(const Geo& g, const StagedLayout& lay, const uint32_t* __restrict__ fill,
+                                             uint32_t lane, const uint32_t (&key)[kPer], uint32_t (&f)[kPer]) {
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) f[j] = lane * kPer + j < lay.nbk ? min(__ldg(fill + key[j]), g.R) : 0u;
+}
+
+// Issuing warp: lay the buckets' runs out in the id buffer (bucket order, each
+// rounded up to 4 ids), announce the bytes on the mbarrier, issue the copies.
+__device__ __forceinline__ void staged_issue(const Geo& g, const StagedLayout& lay, unsigned char* qsm,
+                                             const uint32_t* __restrict__ slots, const uint32_t (&key)[kPer],
+                                             const uint32_t (&f)[kPer], uint32_t bar, uint32_t lane) {
+  uint32_t* ctrl = reinterpret_cast<uint32_t*>(qsm + lay.off_ctrl);
+  const uint32_t ids_s = smem_u32(qsm + lay.off_ids);
+  uint32_t sum = 0;
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) sum += (f[j] + 3u) & ~3u;
   uint32_t inc = sum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -1305,6 +1384,17 @@ __device__ __forceinline__ void staged_issue(const Geo& g, const StagedLayout& l
   }
 }
 
+// Plain schedule: the issuing warp fetches the next query's number, keys and
+// fills into registers while the team answers the current query (the loads are
+// issued at two points of the answer and consumed at the next query), so the
+// next query starts by issuing its copies at once.
+struct Prefetch {
+  bool on = false;
+  uint32_t raw = 0xFFFFFFFFu;  // lane 0: the work counter's answer
+  uint32_t q = 0xFFFFFFFFu;    // the next query (every lane)
+  uint32_t key[kPer], f[kPer];
+};
+
 // 64-bit warp minimum
 __device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
 #pragma unroll
@@ -1315,11 +1405,72 @@ __device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
   return v;
 }
 
-// The staged query of one CTA, after bkey[] is in place (synced) and warp 0
-// has issued the copies.  Returns false if the bounded wait gave up.
-__device__ bool staged_answer(const Geo& g, const StagedLayout& lay, unsigned char* qsm, uint32_t bar,
-                              uint32_t parity, uint32_t k, int32_t* __restrict__ ids_out,
-                              uint32_t* __restrict__ scores_out, uint32_t* __restrict__ err) {
+// The count-min rows of the packed sketch.  kD > 0 fixes the number of rows at
+// compile time (the loops unroll and the row seeds sit in registers); kD = 0
+// reads it from the index at run time.
+template <int kD>
+struct SketchRows {
+  uint32_t sc[kD > 0 ? kD : 1];
+  uint32_t d, wm, hw;  // rows, w - 1, 32-bit words per row (w / 2)
+  const Geo* g;
+  __device__ __forceinline__ explicit SketchRows(const Geo& geo) : g(&geo) {
+    d = kD > 0 ? (uint32_t)kD : geo.d;
+    wm = geo.w - 1u;
+    hw = geo.w >> 1;
+#pragma unroll
+    for (int r = 0; r < (kD > 0 ? kD : 1); ++r) sc[r] = geo.sc[r];
+  }
+  __device__ __forceinline__ uint32_t seed(uint32_t r) const { return kD > 0 ? sc[r] : g->sc[r]; }
+  // one occurrence of id: +1 in its cell of every row
+  __device__ __forceinline__ void add(uint32_t* cmw, uint32_t id) const {
+#pragma unroll
+    for (uint32_t r = 0; r < (kD > 0 ? (uint32_t)kD : d); ++r) {
+      const uint32_t c = mix32(id ^ seed(r)) & wm;
+      atomicAdd(&cmw[r * hw + (c >> 1)], 1u << ((c & 1u) << 4));
+    }
+  }
+  // add() that also returns the cells of the first two rows (c01) and the last two (c23), 16 bits each
+  __device__ __forceinline__ void add_cells(uint32_t* cmw, uint32_t id, uint32_t& c01, uint32_t& c23) const {
+    uint32_t c[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (uint32_t r = 0; r < 4; ++r) {
+      c[r] = mix32(id ^ seed(r)) & wm;
+      atomicAdd(&cmw[r * hw + (c[r] >> 1)], 1u << ((c[r] & 1u) << 4));
+    }
+    c01 = c[0] | (c[1] << 16);
+    c23 = c[2] | (c[3] << 16);
+  }
+  // the estimate from cached cells (four rows)
+  __device__ __forceinline__ uint32_t est_cells(const uint32_t* cmw, uint32_t c01, uint32_t c23) const {
+    const uint32_t c[4] = {c01 & 0xFFFFu, c01 >> 16, c23 & 0xFFFFu, c23 >> 16};
+    uint32_t e = 0xFFFFu;
+#pragma unroll
+    for (uint32_t r = 0; r < 4; ++r) e = min(e, (cmw[r * hw + (c[r] >> 1)] >> ((c[r] & 1u) << 4)) & 0xFFFFu);
+    return e;
+  }
+  // the count-min estimate of id: the smallest of its cells
+  __device__ __forceinline__ uint32_t est(const uint32_t* cmw, uint32_t id) const {
+    uint32_t e = 0xFFFFu;
+#pragma unroll
+    for (uint32_t r = 0; r < (kD > 0 ? (uint32_t)kD : d); ++r) {
+      const uint32_t c = mix32(id ^ seed(r)) & wm;
+      e = min(e, (cmw[r * hw + (c >> 1)] >> ((c & 1u) << 4)) & 0xFFFFu);
+    }
+    return e;
+  }
+};
+
+// The staged answer of one query by a team, after its bucket keys are planned
+// and the team's issuing warp (its warp 0) has issued the copies.  Returns false
+// if the bounded copy wait gave up.  `tw` is the TMEM address of the team's
+// cell cache (four-row sketches; lay.tmem_cols != 0).
+template <int kD>
+__device__ bool staged_answer(const Geo& g, const StagedLayout& lay, unsigned char* qsm, const Team& tm,
+                              uint32_t bar, uint32_t parity, uint32_t tbase, uint32_t k, int32_t* __restrict__ ids_out,
+                              uint32_t* __restrict__ scores_out, uint32_t* __restrict__ err, Prefetch& pf,
+                              const uint32_t* __restrict__ qbkt, uint64_t ldq, uint32_t nq,
+                              const uint32_t* __restrict__ fill) {
+  const SketchRows<kD> rows(g);
   uint32_t* cmw = reinterpret_cast<uint32_t*>(qsm + lay.off_cm);
   const uint32_t* ids = reinterpret_cast<const uint32_t*>(qsm + lay.off_ids);
   const uint4* ids4 = reinterpret_cast<const uint4*>(ids);
@@ -1328,67 +1479,96 @@ __device__ bool staged_answer(const Geo& g, const StagedLayout& lay, unsigned ch
   uint32_t* pool = reinterpret_cast<uint32_t*>(qsm + lay.off_pool);
   uint32_t* hist = reinterpret_cast<uint32_t*>(qsm + lay.off_hist);
   uint32_t* ctrl = reinterpret_cast<uint32_t*>(qsm + lay.off_ctrl);
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, T = blockDim.x;
-  const uint32_t wmask = g.w - 1u;
+  const uint32_t lane = tm.lane, warp = tm.warp, T = tm.T, tid = tm.tid;
   const bool ok = mbar_wait_bounded(bar, parity, kStagedWaitNs);
-  if (__syncthreads_or(!ok)) {
-    if (threadIdx.x == 0) atomicOr(err, kErrWait);
-    mbar_wait_bounded(bar, parity, kStagedDrainNs);  // let copies still in flight land before the CTA leaves
+  if (tm.sync_or(!ok)) {
+    if (tid == 0) atomicOr(err, kErrWait);
+    mbar_wait_bounded(bar, parity, kStagedDrainNs);  // let copies still in flight land before the team leaves
     return false;
   }
   const uint32_t n4 = ctrl[S_TOT] >> 2;
-  // -- count every occurrence into the sketch
-  for (uint32_t i = threadIdx.x; i < n4; i += T) {
-    const uint4 v = ids4[i];
-    const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+  const bool cache = kD == 4 && lay.tmem_cols != 0u;
+  // TMEM lanes of this warp's quadrant (warp % 4), columns of its group of warps
+  const uint32_t tw = tbase + ((32u * (warp & 3u)) << 16) + (warp >> 2) * 8u * lay.tmem_j;
+  // -- count every occurrence into the sketch (four rows: keep each 4-id group's
+  //    16 cells in this thread's TMEM lane, group j at columns 8j; 0xFFFF = no id)
+  if (cache) {
+    for (uint32_t j = 0; j < lay.tmem_j; ++j) {
+      const uint32_t i = tid + j * T;
+      uint32_t cw[8];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      if (x[c] == kEmpty) continue;
-      for (uint32_t r = 0; r < g.d; ++r) cm_add(cmw, r * g.w + cm_cell(x[c], g.sc[r], wmask));
+      for (int c = 0; c < 8; ++c) cw[c] = 0xFFFFFFFFu;
+      if (i < n4) {
+        const uint4 v = ids4[i];
+        const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (x[c] != kEmpty) rows.add_cells(cmw, x[c], cw[2 * c], cw[2 * c + 1]);
+      }
+      tmem_st8(tw + 8u * j, cw);
     }
-  }
-  __syncthreads();
-  // -- estimates (bytes, 255 = at least 255) and their histogram; bins 1..3 hold
-  //    most occurrences, so they are counted by warp ballots instead of atomics
-  uint32_t c1 = 0, c2 = 0, c3 = 0;
-  for (uint32_t i0 = 0; i0 < n4; i0 += T) {
-    const uint32_t i = i0 + threadIdx.x;
-    uint32_t packed = 0;
-    uint32_t e4[4] = {0u, 0u, 0u, 0u};
-    if (i < n4) {
+    tmem_wait_st();
+  } else {
+    for (uint32_t i = tid; i < n4; i += T) {
       const uint4 v = ids4[i];
       const uint32_t x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (x[c] != kEmpty) rows.add(cmw, x[c]);
+    }
+  }
+  tm.sync();
+  if (pf.on && warp == 0) {  // the next query's number, then its keys (loads in flight)
+    pf.q = __shfl_sync(0xFFFFFFFFu, pf.raw, 0);
+    if (pf.q < nq) staged_keys(g, lay, qbkt, ldq, pf.q, lane, pf.key);
+  }
+  // -- estimates (bytes, 255 = at least 255) and their histogram
+  if (cache) {
+    for (uint32_t j = 0; j < lay.tmem_j; ++j) {
+      const uint32_t i = tid + j * T;
+      uint32_t cw[8];
+      tmem_ld8(tw + 8u * j, cw);
+      if (i < n4) {
+        uint32_t packed = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          if ((cw[2 * c] & 0xFFFFu) == 0xFFFFu) continue;
+          const uint32_t e = min(rows.est_cells(cmw, cw[2 * c], cw[2 * c + 1]), kHistBins - 1u);
+          packed |= e << (8 * c);
+          atomicAdd(&hist[e], 1u);
+        }
+        est4[i] = packed;
+      }
+    }
+  } else {
+    for (uint32_t i = tid; i < n4; i += T) {
+      const uint4 v = ids4[i];
+      const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+      uint32_t packed = 0;
+#pragma unroll
       for (int c = 0; c < 4; ++c) {
         if (x[c] == kEmpty) continue;
-        const uint32_t e = min(estimate(g, cmw, x[c]), kHistBins - 1u);
-        e4[c] = e;
+        const uint32_t e = min(rows.est(cmw, x[c]), kHistBins - 1u);
         packed |= e << (8 * c);
+        atomicAdd(&hist[e], 1u);
       }
       est4[i] = packed;
     }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      c1 += __popc(__ballot_sync(0xFFFFFFFFu, e4[c] == 1u));
-      c2 += __popc(__ballot_sync(0xFFFFFFFFu, e4[c] == 2u));
-      c3 += __popc(__ballot_sync(0xFFFFFFFFu, e4[c] == 3u));
-      if (e4[c] > 3u) atomicAdd(&hist[e4[c]], 1u);
-    }
   }
-  if (lane == 0) {
-    if (c1) atomicAdd(&hist[1], c1);
-    if (c2) atomicAdd(&hist[2], c2);
-    if (c3) atomicAdd(&hist[3], c3);
-  }
-  __syncthreads();
+  tm.sync();
+  if (pf.on && warp == 0 && pf.q < nq) staged_fills(g, lay, fill, lane, pf.key, pf.f);  // loads in flight
   // -- cut-off: the largest bin e_lo whose bins at or above it surely hold >= k distinct ids
   if (warp == 0) {
     uint32_t v[8], sum = 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const uint32_t bin = kHistBins - 1u - (lane * 8u + i);  // lane 0 holds the top bins
-      const uint32_t div = bin == kHistBins - 1u ? lay.maxmult : max(1u, min(bin, lay.maxmult));
-      v[i] = bin == 0u ? 0u : (hist[bin] + div - 1u) / div;
+      const uint32_t h = bin == 0u ? 0u : hist[bin];
+      v[i] = 0u;
+      if (h) {
+        const uint32_t div = bin == kHistBins - 1u ? lay.maxmult : max(1u, min(bin, lay.maxmult));
+        v[i] = (h + div - 1u) / div;
+      }
       sum += v[i];
     }
     uint32_t inc = sum;
@@ -1407,21 +1587,24 @@ __device__ bool staged_answer(const Geo& g, const StagedLayout& lay, unsigned ch
       }
     }
   }
-  __syncthreads();
+  tm.sync();
   const uint32_t elo = ctrl[S_ELO];
-  // -- ties in bin e_lo (not the capped bin): the (k*mu)-th smallest occurrence id bounds them
+  // -- ties in bin e_lo (not the capped bin): the (k*mu)-th smallest occurrence id bounds them.
+  //    The bins above e_lo hold fewer than k*S*L occurrences (at most (k-1)*S*L): when bin
+  //    e_lo fits in the rest of the pool it is pooled whole and the selection is skipped.
   uint32_t idmax = 0xFFFFFFFFu;
   const bool tie_bin = elo > 0u && elo < kHistBins - 1u;
   const uint32_t mu = tie_bin ? min(elo, lay.maxmult) : 0u;
   const uint32_t need0 = k * mu;
-  if (tie_bin && hist[elo] > need0) {
+  const uint32_t room = lay.pcap - min(lay.pcap, (k - 1u) * lay.maxmult);
+  if (tie_bin && hist[elo] > need0 && hist[elo] > room) {
     uint32_t prefix = 0, need = need0;
     uint32_t* h2 = hist;  // the estimate histogram is no longer needed
     for (int sh = 24; sh >= 0; sh -= 8) {
-      __syncthreads();
-      for (uint32_t i = threadIdx.x; i < kHistBins; i += T) h2[i] = 0u;
-      __syncthreads();
-      for (uint32_t i = threadIdx.x; i < n4; i += T) {
+      tm.sync();
+      for (uint32_t i = tid; i < kHistBins; i += T) h2[i] = 0u;
+      tm.sync();
+      for (uint32_t i = tid; i < n4; i += T) {
         const uint32_t ew = est4[i];
         if (((ew & 0xFFu) != elo) && (((ew >> 8) & 0xFFu) != elo) && (((ew >> 16) & 0xFFu) != elo) &&
             ((ew >> 24) != elo))
@@ -1435,7 +1618,7 @@ __device__ bool staged_answer(const Geo& g, const StagedLayout& lay, unsigned ch
             atomicAdd(&h2[(id >> sh) & 255u], 1u);
         }
       }
-      __syncthreads();
+      tm.sync();
       if (warp == 0) {
         uint32_t v[8], sum = 0;
 #pragma unroll
@@ -1460,126 +1643,204 @@ __device__ bool staged_answer(const Geo& g, const StagedLayout& lay, unsigned ch
           }
         }
       }
-      __syncthreads();
+      tm.sync();
       prefix = ctrl[S_PFX];
       need = ctrl[S_NEED];
     }
     idmax = prefix;  // >= k*mu occurrences (so >= k distinct ids) of the bin are <= idmax
   }
-  // -- pool: buffer indices of the occurrences above the bin, and of the bin's up to idmax
-  for (uint32_t i0 = 0; i0 < n4; i0 += T) {
-    const uint32_t i = i0 + threadIdx.x;
-    uint32_t ew = 0;
-    uint4 v = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
-    if (i < n4) {
-      ew = est4[i];
-      v = ids4[i];
-    }
-    const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+  // -- pool: buffer indices of the occurrences above the bin, and of the bin's up to idmax.
+  //    A thread marks its takes in a 32-bit mask (8 groups of 4 at a time); one
+  //    atomic per warp and round reserves the warp's slots.
+  for (uint32_t j0 = 0; j0 * T < n4; j0 += 8) {
+    uint32_t mask = 0;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const uint32_t e = (ew >> (8 * c)) & 0xFFu;
-      const bool take = x[c] != kEmpty && (e > elo || (e == elo && x[c] <= idmax));
-      const uint32_t m = __ballot_sync(0xFFFFFFFFu, take);
-      if (!m) continue;
-      uint32_t base = 0;
-      if (lane == (uint32_t)(__ffs(m) - 1)) base = atomicAdd(&ctrl[S_NPOOL], (uint32_t)__popc(m));
-      base = __shfl_sync(0xFFFFFFFFu, base, __ffs(m) - 1);
-      const uint32_t pos = base + __popc(m & ((1u << lane) - 1u));
-      if (take && pos < lay.pcap) pool[pos] = 4u * i + (uint32_t)c;
+    for (uint32_t jj = 0; jj < 8; ++jj) {
+      const uint32_t i = tid + (j0 + jj) * T;
+      if (i >= n4) break;
+      const uint32_t ew = est4[i];
+      if ((ew & 0xFFu) < elo && ((ew >> 8) & 0xFFu) < elo && ((ew >> 16) & 0xFFu) < elo && (ew >> 24) < elo) continue;
+      const uint4 v = ids4[i];
+      const uint32_t x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const uint32_t e = (ew >> (8 * c)) & 0xFFu;
+        if (x[c] != kEmpty && (e > elo || (e == elo && x[c] <= idmax))) mask |= 1u << (4u * jj + (uint32_t)c);
+      }
+    }
+    const uint32_t cnt = __popc(mask);
+    uint32_t inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+      if (lane >= (uint32_t)o) inc += u;
+    }
+    const uint32_t wtot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    uint32_t base = 0;
+    if (lane == 31 && wtot) base = atomicAdd(&ctrl[S_NPOOL], wtot);
+    base = __shfl_sync(0xFFFFFFFFu, base, 31) + inc - cnt;
+    while (mask) {
+      const uint32_t b = (uint32_t)(__ffs(mask) - 1);
+      mask &= mask - 1u;
+      if (base < lay.pcap) pool[base] = 4u * (tid + (j0 + (b >> 2)) * T) + (b & 3u);
+      ++base;
     }
   }
-  __syncthreads();
+  tm.sync();
   const uint32_t P = ctrl[S_NPOOL];
+  if (P > lay.pcap) {  // only when the capped bin decides: leave the query to k_query_redo
+    if (tid == 0) ids_out[0] = kRedoMark;
+    return true;
+  }
+  // -- rank the pool: each active warp keeps, per lane, its kLocalTop smallest
+  //    distinct keys (sorted, in registers); k rounds of warp minima give the
+  //    warp's first k distinct keys; warp 0 merges the warps' lists the same way
+  //    (a key is one id at its estimate, so equal keys are duplicates of one id)
+  uint64_t loc[kLocalTop];
+#pragma unroll
+  for (int t = 0; t < (int)kLocalTop; ++t) loc[t] = ~0ull;
+  auto push = [&](uint64_t key) {
+    if (key >= loc[kLocalTop - 1]) return;
+    bool dup = false;
+#pragma unroll
+    for (int t = 0; t < (int)kLocalTop; ++t) dup |= loc[t] == key;
+    if (dup) return;
+#pragma unroll
+    for (int t = (int)kLocalTop - 1; t > 0; --t) loc[t] = loc[t - 1] > key ? loc[t - 1] : (loc[t] > key ? key : loc[t]);
+    loc[0] = loc[0] > key ? key : loc[0];
+  };
+  auto pop_min = [&]() -> uint64_t {  // the warp's smallest head (two 32-bit reductions); its holders pop it
+    const uint32_t hi = (uint32_t)(loc[0] >> 32), lo = (uint32_t)loc[0];
+    const uint32_t mh = __reduce_min_sync(0xFFFFFFFFu, hi);
+    const uint32_t ml = __reduce_min_sync(0xFFFFFFFFu, hi == mh ? lo : 0xFFFFFFFFu);
+    const uint64_t best = ((uint64_t)mh << 32) | ml;
+    if (best != ~0ull && loc[0] == best) {
+#pragma unroll
+      for (int t = 0; t < (int)kLocalTop - 1; ++t) loc[t] = loc[t + 1];
+      loc[kLocalTop - 1] = ~0ull;
+    }
+    return best;
+  };
+  // warps at work: about 256 pool entries each (one warp for a small pool)
+  const uint32_t NW = T >> 5;
+  const uint32_t wact = min(NW, max(1u, (P + 255u) / 256u));
+  uint64_t mine[kLocalTop];
+  if (warp < wact) {
+    for (uint32_t i = warp * 32u + lane; i < P; i += wact * 32u) {
+      const uint32_t ix = pool[i];
+      const uint32_t id = ids[ix];
+      uint32_t e = est8[ix];
+      if (e == kHistBins - 1u) e = rows.est(cmw, id);  // exact value of a capped estimate
+      push(rank_key(e, id));
+    }
+    bool spent = false;  // warp-uniform: no keys left
+#pragma unroll
+    for (int j = 0; j < (int)kLocalTop; ++j) {
+      mine[j] = ((uint32_t)j < k && !spent) ? pop_min() : ~0ull;
+      spent |= mine[j] == ~0ull;
+    }
+  }
+  uint64_t* wtop = reinterpret_cast<uint64_t*>(est4);  // [warps][k]; the estimates are consumed
+  if (wact > 1u) {
+    tm.sync();
+    if (warp < wact && lane == 0) {
+#pragma unroll
+      for (int j = 0; j < (int)kLocalTop; ++j)
+        if ((uint32_t)j < k) wtop[warp * k + j] = mine[j];
+    }
+    tm.sync();
+  }
   if (warp == 0) {
-    if (P > lay.pcap) {  // only when the capped bin decides: leave the query to k_query_redo
-      if (lane == 0) ids_out[0] = kRedoMark;
-    } else {
-      // one pass: each lane keeps its kLocalTop smallest distinct keys, sorted;
-      // then k rounds take the warp minimum of the lanes' heads
-      uint64_t loc[kLocalTop];
+    if (wact > 1u) {  // merge the warps' lists
 #pragma unroll
       for (int t = 0; t < (int)kLocalTop; ++t) loc[t] = ~0ull;
-      for (uint32_t i = lane; i < P; i += 32) {
-        const uint32_t ix = pool[i];
-        const uint32_t id = ids[ix];
-        uint32_t e = est8[ix];
-        if (e == kHistBins - 1u) e = estimate(g, cmw, id);  // exact value of a capped estimate
-        const uint64_t key = rank_key(e, id);
-        if (key >= loc[kLocalTop - 1]) continue;
-        bool dup = false;
+      for (uint32_t i = lane; i < wact * k; i += 32) push(wtop[i]);
 #pragma unroll
-        for (int t = 0; t < (int)kLocalTop; ++t) dup |= loc[t] == key;
-        if (dup) continue;
+      for (int j = 0; j < (int)kLocalTop; ++j) mine[j] = (uint32_t)j < k ? pop_min() : ~0ull;
+    }
+    if (lane == 0) {
 #pragma unroll
-        for (int t = (int)kLocalTop - 1; t > 0; --t)
-          loc[t] = loc[t - 1] > key ? loc[t - 1] : (loc[t] > key ? key : loc[t]);
-        loc[0] = loc[0] > key ? key : loc[0];
-      }
-      for (uint32_t j = 0; j < k; ++j) {
-        const uint64_t best = warp_min_u64(loc[0]);
-        if (lane == 0) {
-          ids_out[j] = best != ~0ull ? (int32_t)(uint32_t)best : -1;
-          scores_out[j] = best != ~0ull ? 0xFFFFu - (uint32_t)(best >> 32) : 0u;
-        }
-        if (best != ~0ull && loc[0] == best) {
-#pragma unroll
-          for (int t = 0; t < (int)kLocalTop - 1; ++t) loc[t] = loc[t + 1];
-          loc[kLocalTop - 1] = ~0ull;
-        }
+      for (int j = 0; j < (int)kLocalTop; ++j) {
+        if ((uint32_t)j >= k) break;
+        const uint64_t best = mine[j];
+        ids_out[j] = best != ~0ull ? (int32_t)(uint32_t)best : -1;
+        scores_out[j] = best != ~0ull ? 0xFFFFu - (uint32_t)(best >> 32) : 0u;
       }
     }
   }
   return true;
 }
 
-// Staged engine, one persistent CTA pulls queries from a per-launch work counter.
-// kFused = false: the bucket addresses come from the hash kernel (qbkt[t*ldq + q]);
-// kFused = true: the CTA hashes each query itself (DOPH binning by all threads,
-// densification and table addresses by warp 0, in the id buffer's space).
-template <int kThreads, bool kFused>
-__global__ void __launch_bounds__(kThreads, kThreads <= 512 ? 2 : 1)
+// Staged engine: persistent CTAs of blockDim.x / kTeamT teams; every team pulls
+// queries from the launch's work counter.  kFused = false: bucket addresses from
+// the hash kernel (qbkt[t*ldq + q]), the next query's keys and fills prefetched;
+// kFused = true: the team hashes each query itself (DOPH binning by all its
+// threads, densification and table addresses by its warp 0, in the id buffer's
+// space).  Four-row sketches (kD = 4) cache the cells in TMEM, which holds such
+// kernels to one CTA per SM: hence the teams.
+template <int kTeamT, bool kFused, int kD>
+__global__ void __launch_bounds__(kD == 4 ? 1024 : kTeamT, kD == 4 ? 1 : (kTeamT <= 512 ? 2 : 1))
 k_query_staged(const __grid_constant__ Geo g, const StagedLayout lay, const uint32_t* __restrict__ qbkt,
                uint64_t ldq, const uint64_t* __restrict__ offs, const uint32_t* __restrict__ cols, uint32_t nq,
                uint32_t k, const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill,
                int32_t* __restrict__ ids_out, uint32_t* __restrict__ scores_out, uint32_t* __restrict__ work,
                uint32_t* __restrict__ err) {
-  extern __shared__ __align__(128) unsigned char qsm[];
+  extern __shared__ __align__(128) unsigned char ssm[];
+  const Team tm{threadIdx.x / kTeamT, kTeamT, threadIdx.x % kTeamT, (threadIdx.x % kTeamT) >> 5, threadIdx.x & 31u};
+  const uint32_t teams = blockDim.x / kTeamT;
+  unsigned char* qsm = ssm + (size_t)tm.id * lay.bytes;
   uint32_t* cmw = reinterpret_cast<uint32_t*>(qsm + lay.off_cm);
   uint32_t* bkey = reinterpret_cast<uint32_t*>(qsm + lay.off_bkey);
   uint32_t* hist = reinterpret_cast<uint32_t*>(qsm + lay.off_hist);
   uint32_t* ctrl = reinterpret_cast<uint32_t*>(qsm + lay.off_ctrl);
   uint32_t* m = reinterpret_cast<uint32_t*>(qsm + lay.off_ids);  // fused: bin minima, then the id buffer
   uint32_t* mask = m + g.nb;
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(ssm + lay.off_ctrl) + 15;  // team 0's ctrl[15]: TMEM base
+  const uint32_t lane = tm.lane, warp = tm.warp, tid = tm.tid;
   const uint32_t bar = smem_u32(qsm + lay.off_bar);
   const uint32_t cm4n = (g.d * g.w) >> 3;  // uint4 words of the packed sketch
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     mbar_init(bar, 1u);
     mbar_fence_init();
   }
+  const bool tmem = kD == 4 && lay.tmem_cols != 0u;
+  if (tmem && threadIdx.x < 32) tmem_alloc(tslot, lay.tmem_cols * teams);  // whole warp 0 of the CTA
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t tbase = tmem ? *tslot + tm.id * lay.tmem_cols : 0u;
+  Prefetch pf;
+  pf.on = !kFused;
+  if (!kFused && warp == 0) {  // the team's first query, its keys and fills
+    if (lane == 0) pf.raw = atomicAdd(work, 1u);
+    pf.q = __shfl_sync(0xFFFFFFFFu, pf.raw, 0);
+    if (pf.q < nq) {
+      staged_keys(g, lay, qbkt, ldq, pf.q, lane, pf.key);
+      staged_fills(g, lay, fill, lane, pf.key, pf.f);
+    }
+  }
   uint32_t parity = 0;
   for (;;) {
-    if (threadIdx.x == 0) ctrl[S_Q] = atomicAdd(work, 1u);
-    if (threadIdx.x < S_N && threadIdx.x != S_Q) ctrl[threadIdx.x] = 0u;
+    if (tid == 0) ctrl[S_Q] = kFused ? atomicAdd(work, 1u) : pf.q;
+    if (tid < S_N && tid != S_Q) ctrl[tid] = 0u;
     uint4* cm4 = reinterpret_cast<uint4*>(cmw);
-    for (uint32_t i = threadIdx.x; i < cm4n; i += blockDim.x) cm4[i] = make_uint4(0, 0, 0, 0);
-    for (uint32_t i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
+    for (uint32_t i = tid; i < cm4n; i += kTeamT) cm4[i] = make_uint4(0, 0, 0, 0);
+    for (uint32_t i = tid; i < kHistBins; i += kTeamT) hist[i] = 0u;
     if (kFused) {
-      for (uint32_t j = threadIdx.x; j < g.nb; j += blockDim.x) m[j] = kEmpty;
-      if (threadIdx.x < g.nw) mask[threadIdx.x] = 0u;
+      for (uint32_t j = tid; j < g.nb; j += kTeamT) m[j] = kEmpty;
+      if (tid < g.nw) mask[tid] = 0u;
     }
-    __syncthreads();
+    tm.sync();
     const uint32_t q = ctrl[S_Q];
     if (q >= nq) break;
     if (kFused) {
       uint64_t b0 = offs[q], b1 = offs[q + 1];
       if (b1 < b0) {
-        if (threadIdx.x == 0) atomicOr(err, kErrOffs);
+        if (tid == 0) atomicOr(err, kErrOffs);
         b1 = b0;
       }
-      if (doph_scatter(g, cols, b0, b1, m, mask, threadIdx.x, blockDim.x)) atomicOr(err, kErrCol);
-      __syncthreads();
+      if (doph_scatter(g, cols, b0, b1, m, mask, tid, kTeamT)) atomicOr(err, kErrCol);
+      tm.sync();
       if (warp == 0) {
         doph_densify(g, m, mask, lane);
         for (uint32_t it = lane; it < lay.nbk; it += 32) {
@@ -1587,20 +1848,28 @@ k_query_staged(const __grid_constant__ Geo g, const StagedLayout lay, const uint
           bkey[it] = ((s * g.L + t) << g.B) | table_address(g, m, t);
         }
         __syncwarp();
-        staged_issue(g, lay, qsm, slots, fill, bar, lane);
+        uint32_t key[kPer], f[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) key[j] = lane * kPer + j < lay.nbk ? bkey[lane * kPer + j] : 0u;
+        staged_fills(g, lay, fill, lane, key, f);
+        staged_issue(g, lay, qsm, slots, key, f, bar, lane);
       }
     } else if (warp == 0) {
-      for (uint32_t it = lane; it < lay.nbk; it += 32) {
-        const uint32_t s = it / g.L, t = it - s * g.L;
-        bkey[it] = ((s * g.L + t) << g.B) | __ldg(qbkt + t * ldq + q);
-      }
-      __syncwarp();
-      staged_issue(g, lay, qsm, slots, fill, bar, lane);
+      staged_issue(g, lay, qsm, slots, pf.key, pf.f, bar, lane);
+      if (lane == 0) pf.raw = atomicAdd(work, 1u);  // the next query (consumed after the count)
     }
-    if (!staged_answer(g, lay, qsm, bar, parity, k, ids_out + (uint64_t)q * k, scores_out + (uint64_t)q * k, err))
-      return;
+    if (!staged_answer<kD>(g, lay, qsm, tm, bar, parity, tbase, k, ids_out + (uint64_t)q * k,
+                           scores_out + (uint64_t)q * k, err, pf, qbkt, ldq, nq, fill))
+      break;  // a copy wait gave up (reported in err): leave through the common exit
     parity ^= 1u;
-    __syncthreads();  // the buffers are reused by the next query
+    tm.sync();  // the buffers are reused by the next query
+  }
+  // every exit: the CTA's TMEM columns are released by the warp that took them
+  tmem_fence_before_sync();
+  __syncthreads();
+  if (tmem && threadIdx.x < 32) {
+    tmem_fence_after_sync();
+    tmem_dealloc(*tslot, lay.tmem_cols * teams);
   }
 }
 
@@ -1946,7 +2215,7 @@ StagedLayout make_staged_layout(const slash_params& p) {
   uint32_t o = 0;
   l.off_cm = o;   o = al(o + (p.cm_rows * p.cm_width / 2u) * 4u);
   l.off_ids = o;  o = al(o + std::max(l.idcap * 4u, (nb + nw) * 4u));  // fused: the bin minima live here first
-  l.off_est = o;  o = al(o + l.idcap);
+  l.off_est = o;  o = al(o + std::max(l.idcap, 32u * kLocalTop * 8u));  // then the warps' top-k lists
   l.off_pool = o; o = al(o + l.pcap * 4u);
   l.off_bkey = o; o = al(o + l.nbk * 4u);
   l.off_boff = o; o = al(o + 4u);
@@ -2051,12 +2320,28 @@ int cached_bps(int& cached, const void* fn, uint32_t thr, size_t smem, int* out)
   return SLASH_OK;
 }
 
-const void* staged_fn(bool fused, uint32_t thr) {
+// The staged kernel for (schedule, team size, sketch rows): four rows (every
+// workload here) are compiled apart; other row counts take the generic kernel.
+template <int kD>
+const void* staged_fn_d(bool fused, uint32_t thr) {
   if (fused)
-    return thr == 256 ? (const void*)k_query_staged<256, true>
-                      : thr == 512 ? (const void*)k_query_staged<512, true> : (const void*)k_query_staged<1024, true>;
-  return thr == 256 ? (const void*)k_query_staged<256, false>
-                    : thr == 512 ? (const void*)k_query_staged<512, false> : (const void*)k_query_staged<1024, false>;
+    return thr == 256 ? (const void*)k_query_staged<256, true, kD>
+                      : thr == 512 ? (const void*)k_query_staged<512, true, kD>
+                                   : (const void*)k_query_staged<1024, true, kD>;
+  return thr == 256 ? (const void*)k_query_staged<256, false, kD>
+                    : thr == 512 ? (const void*)k_query_staged<512, false, kD>
+                                 : (const void*)k_query_staged<1024, false, kD>;
+}
+const void* staged_fn(bool fused, uint32_t thr, uint32_t d) {
+  return d == 4u ? staged_fn_d<4>(fused, thr) : staged_fn_d<0>(fused, thr);
+}
+
+// Teams of `thr` threads per staged CTA: one, or with a four-row sketch (one CTA
+// per SM) as many as shared memory and 1024 threads allow, at most four.
+uint32_t staged_teams(const slash_index* ix, uint32_t thr, const StagedLayout& lay) {
+  if (ix->p.cm_rows != 4u) return 1u;
+  const uint32_t t = std::min<uint32_t>(std::min<uint32_t>(1024u / thr, 4u), (uint32_t)(ix->smem_optin / lay.bytes));
+  return t < 1u ? 1u : t;
 }
 
 // The staged engine on n queries (rows offs[0..n] of cols): fused (each CTA
@@ -2067,29 +2352,51 @@ int launch_staged(slash_index* ix, bool fused, uint32_t thr, uint32_t ctas_cap, 
                   uint32_t* scores, cudaStream_t st) {
   StagedLayout lay = make_staged_layout(ix->p);
   lay.extra_tx = ix->stall_copies ? 16u : 0u;
+  // Four-row sketches run the kernel that caches the cells in TMEM; such kernels
+  // hold one CTA per SM, so a CTA carries as many teams of `thr` threads as its
+  // shared memory and 1024 threads allow (at most four).
+  const bool four = ix->p.cm_rows == 4u;
+  const uint32_t teams = staged_teams(ix, thr, lay);
+  if (four) {
+    if (ix->p.cm_width <= 32768u) {
+      // each thread keeps 8 columns per 4-id group of its share; warps of one TMEM
+      // quadrant (warp % 4) take consecutive column ranges; teams side by side
+      lay.tmem_j = ((lay.idcap / 4u) + thr - 1u) / thr;
+      const uint32_t need = (thr / 128u) * 8u * lay.tmem_j;
+      uint32_t cols = 32u;
+      while (cols < need) cols <<= 1;
+      if (cols * teams <= 512u) {
+        lay.tmem_cols = cols;
+      } else {
+        lay.tmem_j = 0u;
+      }
+    }
+  }
+  const uint32_t block = teams * thr;
   const int ti = thr == 256 ? 0 : thr == 512 ? 1 : 2;
   int bps = 0;
-  int rc = cached_bps(ix->sbps[fused ? 0 : 1][ti], staged_fn(fused, thr), thr, lay.bytes, &bps);
+  const void* fn = staged_fn(fused, thr, ix->p.cm_rows);
+  int rc = cached_bps(ix->sbps[fused ? 0 : 1][ti], fn, block, (size_t)teams * lay.bytes, &bps);
   if (rc) return rc;
   if (bps < 1) return SLASH_EINVAL;
   if (ctas_cap) bps = std::min<int>(bps, (int)ctas_cap);
-  const uint32_t grid = (uint32_t)std::min<uint64_t>(n, (uint64_t)ix->num_sms * bps);
+  const uint64_t teams_needed = (n + 0ull + teams - 1) / teams;
+  const uint32_t grid = (uint32_t)std::min<uint64_t>(teams_needed, (uint64_t)ix->num_sms * bps);
+  const size_t smem = (size_t)teams * lay.bytes;
   // a private counter per launch: launches on different streams may overlap
   uint32_t* work = ix->work + (ix->work_next.fetch_add(1u) % kWorkRing);
   SLASH_CK(cudaMemsetAsync(work, 0, sizeof(uint32_t), st));
   {
     Launch lq(ix, fused ? "k_query_staged_fused" : "k_query_staged", st);
-#define SLASH_STAGED(T, F)                                                                                  \
-  k_query_staged<T, F><<<grid, T, lay.bytes, st>>>(ix->geo, lay, qbkt, ldq, offs, cols, n, topk, ix->slots, \
-                                                   ix->fill, ids, scores, work, ix->err)
-    if (fused) {
-      if (thr == 256) SLASH_STAGED(256, true); else if (thr == 512) SLASH_STAGED(512, true); else SLASH_STAGED(1024, true);
-    } else {
-      if (thr == 256) SLASH_STAGED(256, false); else if (thr == 512) SLASH_STAGED(512, false); else SLASH_STAGED(1024, false);
-    }
-#undef SLASH_STAGED
+    const Geo* gp = &ix->geo;
+    const uint32_t* slots = ix->slots;
+    const uint32_t* fill = ix->fill;
+    uint32_t* err = ix->err;
+    void* args[] = {(void*)gp, (void*)&lay, (void*)&qbkt, (void*)&ldq, (void*)&offs, (void*)&cols, (void*)&n,
+                    (void*)&topk, (void*)&slots, (void*)&fill, (void*)&ids, (void*)&scores, (void*)&work,
+                    (void*)&err};
+    SLASH_CK(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, st));
   }
-  SLASH_CK(cudaGetLastError());
   const uint32_t rt = ix->redo_threads;
   const QueryLayout rl = make_query_layout(ix->p, rt);
   const uint32_t rgrid = (uint32_t)std::min<uint64_t>((n + rt - 1) / rt, (uint64_t)ix->num_sms);
@@ -2221,12 +2528,13 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
   cudaFuncSetAttribute(k_query_fused<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_query_fused<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_merge_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ix->smem_optin);
-#define SLASH_SATTR(T)                                                                                   \
-  cudaFuncSetAttribute(k_query_staged<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);       \
-  cudaFuncSetAttribute(k_query_staged<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);        \
-  cudaFuncSetAttribute(k_query_redo<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
-  SLASH_SATTR(256) SLASH_SATTR(512) SLASH_SATTR(1024)
-#undef SLASH_SATTR
+  for (uint32_t t : {256u, 512u, 1024u})
+    for (bool f : {false, true})
+      for (uint32_t d : {4u, 0u}) cudaFuncSetAttribute(staged_fn(f, t, d == 0u ? 1u : d),
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_query_redo<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_query_redo<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_query_redo<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   init_hash_kernels(so);
   *out = ix;
   return SLASH_OK;
@@ -2599,6 +2907,30 @@ int slash_debug_stall_copies(slash_index* ix, int enable) {
   return ix->staged ? SLASH_OK : SLASH_EINVAL;
 }
 
+int slash_debug_occupancy(slash_index* ix, uint32_t mode, uint32_t threads, int* ctas_per_sm_out) {
+  if (!ix || !ctas_per_sm_out || (mode != SLASH_QUERY_PLAIN && mode != SLASH_QUERY_FUSED) ||
+      (threads != 256u && threads != 512u && threads != 1024u))
+    return SLASH_EINVAL;
+  const bool fused = mode == SLASH_QUERY_FUSED;
+  int b = 0;
+  if (ix->staged) {
+    const StagedLayout lay = make_staged_layout(ix->p);
+    const uint32_t teams = staged_teams(ix, threads, lay);
+    SLASH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, staged_fn(fused, threads, ix->p.cm_rows),
+                                                           (int)(teams * threads), teams * lay.bytes));
+  } else {
+    const QueryLayout lay = make_query_layout(ix->p, threads);
+    const void* fn = fused ? (threads == 256 ? (const void*)k_query_fused<256>
+                                              : threads == 512 ? (const void*)k_query_fused<512>
+                                                               : (const void*)k_query_fused<1024>)
+                           : (threads == 256 ? (const void*)k_query<256>
+                                              : threads == 512 ? (const void*)k_query<512> : (const void*)k_query<1024>);
+    SLASH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, (int)threads, lay.bytes));
+  }
+  *ctas_per_sm_out = b;
+  return SLASH_OK;
+}
+
 int slash_debug_fail_alloc(slash_index* ix, uint32_t count) {
   if (!ix) return SLASH_EINVAL;
   ix->fail_allocs = count;
@@ -2705,3 +3037,297 @@ extern "C" int slash_query_static(slash_index* ix, const uint64_t* d_offs, const
   SLASH_CK(cudaGetLastError());
   return SLASH_OK;
 }
+
+// ----------------------------------------------------------------------------- candidate exchange
+// The local steps of one process of a multi-process index (Sec. 3 partitions,
+// Algorithm 2's merge across machines done as one exchange of candidates):
+//   k_candidates   each query's distinct local candidate ids, ascending;
+//   k_cells        this partition's count-min cells of every gathered id;
+//   k_rank         top-k from the summed cells (estimate = the smallest cell).
+// The collectives between them (all-gather of the ids, sum of the cells) are
+// the caller's.  Each kernel takes one CTA per query (grid-stride).
+namespace {
+
+constexpr int kExThreads = 512;
+constexpr uint32_t kExChunk = 8192;  // keys sorted at once by k_rank
+
+// ascending bitonic sort of buf[0..n2) (n2 a power of two) by the whole CTA
+__device__ __forceinline__ void block_bitonic_u32(uint32_t* buf, uint32_t n2) {
+  for (uint32_t k = 2; k <= n2; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < n2; i += blockDim.x) {
+        const uint32_t ixj = i ^ j;
+        if (ixj > i) {
+          const uint32_t a = buf[i], b = buf[ixj];
+          if ((a > b) == ((i & k) == 0)) { buf[i] = b; buf[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// The ids of query q's S*L buckets (addresses qbkt[t*ldq + q]) into ids[0..n);
+// returns n.  bk, bf: [nbk]; bo: [nbk + 1]; tmp: [nbk / 32 + 1] (shared).
+__device__ uint32_t ex_gather(const Geo& g, const uint32_t* __restrict__ qbkt, uint64_t ldq, uint32_t q,
+                              const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill, uint32_t* ids,
+                              uint32_t* bk, uint32_t* bf, uint32_t* bo, uint32_t* tmp) {
+  const uint32_t nbk = g.S * g.L, lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  for (uint32_t it = threadIdx.x; it < nbk; it += blockDim.x) {
+    const uint32_t s = it / g.L, t = it - s * g.L;
+    const uint32_t key = ((s * g.L + t) << g.B) | qbkt[t * ldq + q];
+    bk[it] = key;
+    bf[it] = min(fill[key], g.R);
+  }
+  __syncthreads();
+  block_scan_small(bf, bo, nbk, tmp);
+  for (uint32_t b = warp; b < nbk; b += NW)
+    for (uint32_t j = lane; j < bf[b]; j += 32) ids[bo[b] + j] = slots[(uint64_t)bk[b] * g.R + j];
+  __syncthreads();
+  return bo[nbk];
+}
+
+// Each query's distinct local candidates, ascending: counts[q], out[q*m .. q*m + m) (-1 past the count).
+__global__ void __launch_bounds__(kExThreads)
+k_candidates(const __grid_constant__ Geo g, const uint32_t* __restrict__ qbkt, uint64_t ldq, uint32_t nq, uint32_t m,
+             const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill, int32_t* __restrict__ counts,
+             int32_t* __restrict__ out) {
+  extern __shared__ __align__(16) uint32_t exs[];
+  const uint32_t nbk = g.S * g.L, maxm = nbk * g.R;
+  uint32_t n2 = 2;
+  while (n2 < maxm) n2 <<= 1;
+  uint32_t* ids = exs;                 // [n2]
+  uint32_t* bk = ids + n2;             // [nbk]
+  uint32_t* bf = bk + nbk;             // [nbk]
+  uint32_t* bo = bf + nbk;             // [nbk + 1]
+  uint32_t* tmp = bo + nbk + 1;        // [nbk / 32 + 1]
+  uint32_t* wcnt = tmp + nbk / 32 + 1; // [33]
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
+  for (uint32_t q = blockIdx.x; q < nq; q += gridDim.x) {
+    const uint32_t n = ex_gather(g, qbkt, ldq, q, slots, fill, ids, bk, bf, bo, tmp);
+    uint32_t p2 = 2;
+    while (p2 < n) p2 <<= 1;
+    for (uint32_t i = n + threadIdx.x; i < p2; i += blockDim.x) ids[i] = kEmpty;
+    __syncthreads();
+    block_bitonic_u32(ids, p2);
+    // keep the first of each run of equal ids, compacted in order
+    uint32_t base = 0;
+    for (uint32_t i0 = 0; i0 < n; i0 += blockDim.x) {
+      const uint32_t i = i0 + threadIdx.x;
+      const bool fresh = i < n && (i == 0 || ids[i - 1] != ids[i]);
+      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, fresh);
+      if (lane == 0) wcnt[warp] = __popc(bal);
+      __syncthreads();
+      if (warp == 0) {
+        const uint32_t v = lane < NW ? wcnt[lane] : 0u;
+        uint32_t inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+          if (lane >= (uint32_t)o) inc += u;
+        }
+        if (lane < NW) wcnt[lane] = inc - v;
+        if (lane == 31) wcnt[32] = inc;
+      }
+      __syncthreads();
+      if (fresh) out[(uint64_t)q * m + base + wcnt[warp] + __popc(bal & ((1u << lane) - 1u))] = (int32_t)ids[i];
+      base += wcnt[32];
+      __syncthreads();
+    }
+    for (uint32_t j = base + threadIdx.x; j < m; j += blockDim.x) out[(uint64_t)q * m + j] = -1;
+    if (threadIdx.x == 0) counts[q] = (int32_t)base;
+    __syncthreads();
+  }
+}
+
+// This partition's sketch cells of every gathered id: for rank w < W and
+// j < m, cells[((w*nq + q)*m + j)*d + r] = the partition's count in row r at
+// the id's cell (0 for j >= counts[w*nq + q]).
+__global__ void __launch_bounds__(kExThreads)
+k_cells(const __grid_constant__ Geo g, const uint32_t* __restrict__ qbkt, uint64_t ldq, uint32_t nq, uint32_t W,
+        uint32_t m, const int32_t* __restrict__ counts, const int32_t* __restrict__ gids,
+        const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill, uint32_t* __restrict__ cells) {
+  extern __shared__ __align__(16) uint32_t exs[];
+  const uint32_t nbk = g.S * g.L, maxm = nbk * g.R, cmwords = (g.d * g.w) >> 1, wmask = g.w - 1u;
+  uint32_t* cmw = exs;                 // [cmwords]
+  uint32_t* ids = cmw + cmwords;       // [maxm]
+  uint32_t* bk = ids + maxm;
+  uint32_t* bf = bk + nbk;
+  uint32_t* bo = bf + nbk;
+  uint32_t* tmp = bo + nbk + 1;
+  for (uint32_t q = blockIdx.x; q < nq; q += gridDim.x) {
+    for (uint32_t i = threadIdx.x; i < cmwords; i += blockDim.x) cmw[i] = 0u;
+    const uint32_t n = ex_gather(g, qbkt, ldq, q, slots, fill, ids, bk, bf, bo, tmp);  // syncs first
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
+      for (uint32_t r = 0; r < g.d; ++r) cm_add(cmw, r * g.w + cm_cell(ids[i], g.sc[r], wmask));
+    __syncthreads();
+    for (uint32_t w = 0; w < W; ++w) {
+      const uint64_t row = (uint64_t)w * nq + q;
+      const uint32_t c = (uint32_t)max(0, counts[row]);
+      for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) {
+        const uint32_t id = (uint32_t)gids[row * m + j];
+        for (uint32_t r = 0; r < g.d; ++r)
+          cells[(row * m + j) * g.d + r] = j < c ? cm_get(cmw, r * g.w + cm_cell(id, g.sc[r], wmask)) : 0u;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Top-k from the summed cells: estimate = the smallest of an id's d cells, order
+// (estimate desc, id asc), pad (-1, 0).  The ids of all ranks are distinct.
+__global__ void __launch_bounds__(kExThreads)
+k_rank(uint32_t W, uint32_t nq, uint32_t m, uint32_t d, const int32_t* __restrict__ counts,
+       const int32_t* __restrict__ gids, const uint32_t* __restrict__ cells, uint32_t k, int32_t* __restrict__ ids_out,
+       uint32_t* __restrict__ scores_out) {
+  extern __shared__ __align__(16) uint64_t exk[];
+  uint64_t* A = exk;              // [kExChunk] keys of one chunk
+  uint64_t* S = A + kExChunk;     // [kExChunk] survivors: each chunk's first k
+  __shared__ uint32_t pre[65];    // prefix of the ranks' counts (W <= 64)
+  for (uint32_t q = blockIdx.x; q < nq; q += gridDim.x) {
+    if (threadIdx.x == 0) {
+      uint32_t run = 0;
+      for (uint32_t w = 0; w < W; ++w) { pre[w] = run; run += (uint32_t)max(0, counts[(uint64_t)w * nq + q]); }
+      pre[W] = run;
+    }
+    __syncthreads();
+    const uint32_t E = pre[W];
+    uint32_t sn = 0;
+    for (uint32_t e0 = 0; e0 < E; e0 += kExChunk) {
+      const uint32_t ne = min(kExChunk, E - e0);
+      uint32_t p2 = 2;
+      while (p2 < ne) p2 <<= 1;
+      for (uint32_t i = threadIdx.x; i < p2; i += blockDim.x) {
+        uint64_t key = ~0ull;
+        if (i < ne) {
+          const uint32_t e = e0 + i;
+          uint32_t w = 0;
+          while (pre[w + 1] <= e) ++w;
+          const uint64_t row = (uint64_t)w * nq + q;
+          const uint32_t j = e - pre[w];
+          uint32_t est = 0xFFFFFFFFu;
+          for (uint32_t r = 0; r < d; ++r) est = min(est, cells[(row * m + j) * d + r]);
+          key = ((uint64_t)(0xFFFFFFFFu - est) << 32) | (uint32_t)gids[row * m + j];
+        }
+        A[i] = key;
+      }
+      __syncthreads();
+      block_bitonic(A, p2);
+      const uint32_t keep = min(k, ne);
+      if (sn + keep > kExChunk) {  // fold the survivors to their first k
+        uint32_t s2 = 2;
+        while (s2 < sn) s2 <<= 1;
+        for (uint32_t i = sn + threadIdx.x; i < s2; i += blockDim.x) S[i] = ~0ull;
+        __syncthreads();
+        block_bitonic(S, s2);
+        sn = min(sn, k);
+      }
+      for (uint32_t i = threadIdx.x; i < keep; i += blockDim.x) S[sn + i] = A[i];
+      sn += keep;
+      __syncthreads();
+    }
+    uint32_t s2 = 2;
+    while (s2 < sn) s2 <<= 1;
+    for (uint32_t i = sn + threadIdx.x; i < s2; i += blockDim.x) S[i] = ~0ull;
+    __syncthreads();
+    block_bitonic(S, s2);
+    for (uint32_t j = threadIdx.x; j < k; j += blockDim.x) {
+      const bool have = j < sn;
+      ids_out[(uint64_t)q * k + j] = have ? (int32_t)(uint32_t)S[j] : -1;
+      scores_out[(uint64_t)q * k + j] = have ? 0xFFFFFFFFu - (uint32_t)(S[j] >> 32) : 0u;
+    }
+    __syncthreads();
+  }
+}
+
+size_t ex_gather_smem(const slash_params& p) {
+  const size_t nbk = (size_t)p.shards * p.L;
+  return sizeof(uint32_t) * (3 * nbk + 1 + nbk / 32 + 1);
+}
+
+// the query's table addresses into the index's plain-query workspace
+int ex_addresses(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_cols, uint32_t nq, cudaStream_t st) {
+  int rc = grow_query_ws(ix, nq);
+  if (rc) return rc;
+  return run_hash(ix, d_offs, d_cols, nq, 0, ix->qbkt, nq, nullptr, false, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int slash_set_next_id(slash_index* ix, uint64_t next_id) {
+  if (!ix || next_id < ix->next_id || next_id > ix->p.capacity) return SLASH_EINVAL;
+  ix->next_id = next_id;
+  return SLASH_OK;
+}
+
+int slash_query_candidates(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_cols, uint32_t n_queries,
+                           uint32_t m, int32_t* d_counts, int32_t* d_ids, void* cuda_stream) {
+  if (!ix) return SLASH_EINVAL;
+  const uint64_t maxm = (uint64_t)ix->p.shards * ix->p.L * ix->p.reservoir;
+  if (m < maxm) return SLASH_EINVAL;
+  if (n_queries == 0) return SLASH_OK;
+  if (!d_offs || !d_cols || !d_counts || !d_ids) return SLASH_EINVAL;
+  uint32_t n2 = 2;
+  while (n2 < maxm) n2 <<= 1;
+  const size_t smem = sizeof(uint32_t) * (n2 + 33) + ex_gather_smem(ix->p);
+  if (smem > ix->smem_optin) return SLASH_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  ApiRange api("slash_query_candidates");
+  int rc = ex_addresses(ix, d_offs, d_cols, n_queries, st);
+  if (rc) return rc;
+  cudaFuncSetAttribute(k_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const uint32_t grid = (uint32_t)std::min<uint64_t>(n_queries, (uint64_t)ix->num_sms * 2);
+  Launch l(ix, "k_candidates", st);
+  k_candidates<<<grid, kExThreads, smem, st>>>(ix->geo, ix->qbkt, n_queries, n_queries, m, ix->slots, ix->fill,
+                                                d_counts, d_ids);
+  SLASH_CK(cudaGetLastError());
+  return SLASH_OK;
+}
+
+int slash_query_cells(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_cols, uint32_t n_queries,
+                      uint32_t world, uint32_t m, const int32_t* d_counts, const int32_t* d_ids, uint32_t* d_cells,
+                      void* cuda_stream) {
+  if (!ix || world == 0 || world > 64) return SLASH_EINVAL;
+  const uint64_t maxm = (uint64_t)ix->p.shards * ix->p.L * ix->p.reservoir;
+  if (m < maxm) return SLASH_EINVAL;
+  if (n_queries == 0) return SLASH_OK;
+  if (!d_offs || !d_cols || !d_counts || !d_ids || !d_cells) return SLASH_EINVAL;
+  const size_t smem = sizeof(uint32_t) * ((size_t)ix->p.cm_rows * ix->p.cm_width / 2 + maxm) + ex_gather_smem(ix->p);
+  if (smem > ix->smem_optin) return SLASH_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  ApiRange api("slash_query_cells");
+  int rc = ex_addresses(ix, d_offs, d_cols, n_queries, st);
+  if (rc) return rc;
+  cudaFuncSetAttribute(k_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const uint32_t grid = (uint32_t)std::min<uint64_t>(n_queries, (uint64_t)ix->num_sms * 2);
+  Launch l(ix, "k_cells", st);
+  k_cells<<<grid, kExThreads, smem, st>>>(ix->geo, ix->qbkt, n_queries, n_queries, world, m, d_counts, d_ids,
+                                           ix->slots, ix->fill, d_cells);
+  SLASH_CK(cudaGetLastError());
+  return SLASH_OK;
+}
+
+int slash_rank_candidates(uint32_t world, uint32_t n_queries, uint32_t m, uint32_t d, const int32_t* d_counts,
+                          const int32_t* d_ids, const uint32_t* d_cells, uint32_t topk, int32_t* d_ids_out,
+                          uint32_t* d_scores_out, void* cuda_stream) {
+  if (world == 0 || world > 64 || m == 0 || d == 0 || d > SLASH_MAX_CMROWS || topk == 0 || topk > SLASH_MAX_TOPK)
+    return SLASH_EINVAL;
+  if (n_queries == 0) return SLASH_OK;
+  if (!d_counts || !d_ids || !d_cells || !d_ids_out || !d_scores_out) return SLASH_EINVAL;
+  int dev = 0, sms = 0;
+  SLASH_CK(cudaGetDevice(&dev));
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t smem = sizeof(uint64_t) * 2 * kExChunk;
+  SLASH_CK(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  ApiRange api("slash_rank_candidates");
+  const uint32_t grid = (uint32_t)std::min<uint64_t>(n_queries, (uint64_t)sms);
+  k_rank<<<grid, kExThreads, smem, st>>>(world, n_queries, m, d, d_counts, d_ids, d_cells, topk, d_ids_out,
+                                         d_scores_out);
+  SLASH_CK(cudaGetLastError());
+  return SLASH_OK;
+}
+
+}  // extern "C"
