@@ -1218,6 +1218,7 @@ struct StagedLayout {
   uint32_t off_cm, off_ids, off_est, off_pool, off_bkey, off_boff, off_hist, off_ctrl, off_bar, bytes;
   uint32_t extra_tx;  // test support: bytes announced on the mbarrier beyond the copies (0 in service)
   uint32_t tmem_cols, tmem_j;  // four-row sketches: TMEM columns per CTA, 4-id groups per thread
+  uint32_t async16;  // 1: every warp copies the ids in 16-byte cp.async pieces; 0: one bulk copy per bucket
 };
 
 enum { S_NPOOL = 0, S_ELO, S_PFX, S_NEED, S_Q, S_TOT, S_N };
@@ -1270,6 +1271,14 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
                : "memory");
+}
+
+// 16-byte global -> shared copy through L2 (cp.async); both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 // Tensor memory (TMEM) as a per-thread cache of the sketch cells: every warp
@@ -1338,30 +1347,67 @@ __device__ __forceinline__ void staged_keys(const Geo& g, const StagedLayout& la
   for (int j = 0; j < kPer; ++j) {
     const uint32_t i = lane * kPer + j;
     key[j] = 0u;
-    if (i < lay.nbk) {
-      const uint32_t s = i / g.L, t = i - s * g.L;
-      key[j] = ((s * g.L + t) << g.B) | __ldg(qbkt + t * ldq + q);
-    }
+    if (i < lay.nbk) key[j] = (i << g.B) | __ldg(qbkt + (i % g.L) * ldq + q);  // i = s*L + t
   }
 }
 
-// Issuing warp: the fills of those buckets (never above R: a copy stays inside its bucket).
+// The same in two halves for the prefetch: the address loads are issued first
+// (their values are not used yet, so the warp does not wait for them) ...
+__device__ __forceinline__ void staged_keys_load(const Geo& g, const StagedLayout& lay,
+                                                 const uint32_t* __restrict__ qbkt, uint64_t ldq, uint32_t q,
+                                                 uint32_t lane, uint32_t (&raw)[kPer]) {
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const uint32_t i = lane * kPer + j;
+    raw[j] = 0u;
+    if (i < lay.nbk) raw[j] = __ldg(qbkt + (i % g.L) * ldq + q);
+  }
+}
+// ... and turned into keys later, when their fills are requested.
+__device__ __forceinline__ void staged_keys_finish(const Geo& g, const StagedLayout& lay, uint32_t lane,
+                                                   uint32_t (&key)[kPer]) {
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const uint32_t i = lane * kPer + j;
+    if (i < lay.nbk) key[j] |= i << g.B;  // bucket key ((s*L + t) << B) | address, i = s*L + t
+  }
+}
+
+// Issuing warp: pull the next query's bucket runs into L2 (one prefetch per
+// 128-byte line, fills already loaded), so that its copies meet L2, not DRAM.
+__device__ __forceinline__ void staged_prefetch_l2(const Geo& g, const StagedLayout& lay,
+                                                   const uint32_t* __restrict__ slots, uint32_t lane,
+                                                   const uint32_t (&key)[kPer], const uint32_t (&fill_raw)[kPer]) {
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    if (lane * kPer + j >= lay.nbk) continue;
+    const uint32_t* run = slots + (uint64_t)key[j] * g.R;
+    const uint32_t bytes = 4u * min(fill_raw[j], g.R);
+    for (uint32_t b = 0; b < bytes; b += 128u) asm volatile("prefetch.global.L2 [%0];" ::"l"(run + b / 4u));
+  }
+}
+
+// Issuing warp: the fills of those buckets (loads only; staged_issue caps them
+// at R, so a copy stays inside its bucket).
 __device__ __forceinline__ void staged_fills(const Geo& g, const StagedLayout& lay, const uint32_t* __restrict__ fill,
                                              uint32_t lane, const uint32_t (&key)[kPer], uint32_t (&f)[kPer]) {
 #pragma unroll
-  for (int j = 0; j < kPer; ++j) f[j] = lane * kPer + j < lay.nbk ? min(__ldg(fill + key[j]), g.R) : 0u;
+  for (int j = 0; j < kPer; ++j) f[j] = lane * kPer + j < lay.nbk ? __ldg(fill + key[j]) : 0u;
 }
 
 // Issuing warp: lay the buckets' runs out in the id buffer (bucket order, each
 // rounded up to 4 ids), announce the bytes on the mbarrier, issue the copies.
 __device__ __forceinline__ void staged_issue(const Geo& g, const StagedLayout& lay, unsigned char* qsm,
                                              const uint32_t* __restrict__ slots, const uint32_t (&key)[kPer],
-                                             const uint32_t (&f)[kPer], uint32_t bar, uint32_t lane) {
+                                             const uint32_t (&fill_raw)[kPer], uint32_t bar, uint32_t lane) {
   uint32_t* ctrl = reinterpret_cast<uint32_t*>(qsm + lay.off_ctrl);
   const uint32_t ids_s = smem_u32(qsm + lay.off_ids);
-  uint32_t sum = 0;
+  uint32_t f[kPer], sum = 0;
 #pragma unroll
-  for (int j = 0; j < kPer; ++j) sum += (f[j] + 3u) & ~3u;
+  for (int j = 0; j < kPer; ++j) {
+    f[j] = min(fill_raw[j], g.R);  // a fill never exceeds R: the copy stays inside its bucket
+    sum += (f[j] + 3u) & ~3u;
+  }
   uint32_t inc = sum;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -1369,6 +1415,25 @@ __device__ __forceinline__ void staged_issue(const Geo& g, const StagedLayout& l
     if (lane >= (uint32_t)o) inc += u;
   }
   const uint32_t total = __shfl_sync(0xFFFFFFFFu, inc, 31);
+  if (lay.async16) {  // the team copies: publish each bucket's key and run offset
+    uint32_t* bkey = reinterpret_cast<uint32_t*>(qsm + lay.off_bkey);
+    uint32_t* boff = reinterpret_cast<uint32_t*>(qsm + lay.off_boff);
+    uint32_t o = inc - sum;
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const uint32_t i = lane * kPer + j;
+      if (i < lay.nbk) {
+        bkey[i] = key[j];
+        boff[i] = o;
+      }
+      o += (f[j] + 3u) & ~3u;
+    }
+    if (lane == 0) {
+      ctrl[S_TOT] = total;
+      boff[lay.nbk] = total;
+    }
+    return;
+  }
   fence_proxy_async_smem();  // the buffer's earlier reads and writes come before the copies
   if (lane == 0) {
     ctrl[S_TOT] = total;
@@ -1469,7 +1534,7 @@ __device__ bool staged_answer(const Geo& g, const StagedLayout& lay, unsigned ch
                               uint32_t bar, uint32_t parity, uint32_t tbase, uint32_t k, int32_t* __restrict__ ids_out,
                               uint32_t* __restrict__ scores_out, uint32_t* __restrict__ err, Prefetch& pf,
                               const uint32_t* __restrict__ qbkt, uint64_t ldq, uint32_t nq,
-                              const uint32_t* __restrict__ fill) {
+                              const uint32_t* __restrict__ fill, const uint32_t* __restrict__ slots) {
   const SketchRows<kD> rows(g);
   uint32_t* cmw = reinterpret_cast<uint32_t*>(qsm + lay.off_cm);
   const uint32_t* ids = reinterpret_cast<const uint32_t*>(qsm + lay.off_ids);
@@ -1480,11 +1545,26 @@ __device__ bool staged_answer(const Geo& g, const StagedLayout& lay, unsigned ch
   uint32_t* hist = reinterpret_cast<uint32_t*>(qsm + lay.off_hist);
   uint32_t* ctrl = reinterpret_cast<uint32_t*>(qsm + lay.off_ctrl);
   const uint32_t lane = tm.lane, warp = tm.warp, T = tm.T, tid = tm.tid;
-  const bool ok = mbar_wait_bounded(bar, parity, kStagedWaitNs);
-  if (tm.sync_or(!ok)) {
-    if (tid == 0) atomicOr(err, kErrWait);
-    mbar_wait_bounded(bar, parity, kStagedDrainNs);  // let copies still in flight land before the team leaves
-    return false;
+  if (lay.async16) {
+    // every warp copies whole buckets: 16-byte pieces of bucket b's run of 4-id groups
+    tm.sync();
+    const uint32_t* bkey = reinterpret_cast<const uint32_t*>(qsm + lay.off_bkey);
+    const uint32_t* boff = reinterpret_cast<const uint32_t*>(qsm + lay.off_boff);
+    const uint32_t ids_s = smem_u32(qsm + lay.off_ids);
+    for (uint32_t b = warp; b < lay.nbk; b += (T >> 5)) {
+      const uint32_t o = boff[b], n4 = (boff[b + 1] - o) >> 2;
+      const uint32_t* src = slots + (uint64_t)bkey[b] * g.R;
+      for (uint32_t c = lane; c < n4; c += 32) cp_async16(ids_s + 16u * c + 4u * o, src + 4u * c);
+    }
+    cp_async_wait_all();
+    tm.sync();
+  } else {
+    const bool ok = mbar_wait_bounded(bar, parity, kStagedWaitNs);
+    if (tm.sync_or(!ok)) {
+      if (tid == 0) atomicOr(err, kErrWait);
+      mbar_wait_bounded(bar, parity, kStagedDrainNs);  // let copies still in flight land before the team leaves
+      return false;
+    }
   }
   const uint32_t n4 = ctrl[S_TOT] >> 2;
   const bool cache = kD == 4 && lay.tmem_cols != 0u;
@@ -1518,9 +1598,9 @@ __device__ bool staged_answer(const Geo& g, const StagedLayout& lay, unsigned ch
     }
   }
   tm.sync();
-  if (pf.on && warp == 0) {  // the next query's number, then its keys (loads in flight)
+  if (pf.on && warp == 0) {  // the next query's number, then its addresses (loads in flight)
     pf.q = __shfl_sync(0xFFFFFFFFu, pf.raw, 0);
-    if (pf.q < nq) staged_keys(g, lay, qbkt, ldq, pf.q, lane, pf.key);
+    if (pf.q < nq) staged_keys_load(g, lay, qbkt, ldq, pf.q, lane, pf.key);
   }
   // -- estimates (bytes, 255 = at least 255) and their histogram
   if (cache) {
@@ -1556,7 +1636,10 @@ __device__ bool staged_answer(const Geo& g, const StagedLayout& lay, unsigned ch
     }
   }
   tm.sync();
-  if (pf.on && warp == 0 && pf.q < nq) staged_fills(g, lay, fill, lane, pf.key, pf.f);  // loads in flight
+  if (pf.on && warp == 0 && pf.q < nq) {  // the keys, then the fills (loads in flight)
+    staged_keys_finish(g, lay, lane, pf.key);
+    staged_fills(g, lay, fill, lane, pf.key, pf.f);
+  }
   // -- cut-off: the largest bin e_lo whose bins at or above it surely hold >= k distinct ids
   if (warp == 0) {
     uint32_t v[8], sum = 0;
@@ -1687,6 +1770,7 @@ __device__ bool staged_answer(const Geo& g, const StagedLayout& lay, unsigned ch
     }
   }
   tm.sync();
+  if (pf.on && warp == 0 && pf.q < nq) staged_prefetch_l2(g, lay, slots, lane, pf.key, pf.f);  // next query's ids
   const uint32_t P = ctrl[S_NPOOL];
   if (P > lay.pcap) {  // only when the capped bin decides: leave the query to k_query_redo
     if (tid == 0) ids_out[0] = kRedoMark;
@@ -1859,7 +1943,7 @@ k_query_staged(const __grid_constant__ Geo g, const StagedLayout lay, const uint
       if (lane == 0) pf.raw = atomicAdd(work, 1u);  // the next query (consumed after the count)
     }
     if (!staged_answer<kD>(g, lay, qsm, tm, bar, parity, tbase, k, ids_out + (uint64_t)q * k,
-                           scores_out + (uint64_t)q * k, err, pf, qbkt, ldq, nq, fill))
+                           scores_out + (uint64_t)q * k, err, pf, qbkt, ldq, nq, fill, slots))
       break;  // a copy wait gave up (reported in err): leave through the common exit
     parity ^= 1u;
     tm.sync();  // the buffers are reused by the next query
@@ -2218,7 +2302,7 @@ StagedLayout make_staged_layout(const slash_params& p) {
   l.off_est = o;  o = al(o + std::max(l.idcap, 32u * kLocalTop * 8u));  // then the warps' top-k lists
   l.off_pool = o; o = al(o + l.pcap * 4u);
   l.off_bkey = o; o = al(o + l.nbk * 4u);
-  l.off_boff = o; o = al(o + 4u);
+  l.off_boff = o; o = al(o + (l.nbk + 1u) * 4u);
   l.off_hist = o; o = al(o + kHistBins * 4u);
   l.off_ctrl = o; o = al(o + 16u * 4u);
   l.off_bar = o;  o = al(o + 8u);
@@ -2352,6 +2436,9 @@ int launch_staged(slash_index* ix, bool fused, uint32_t thr, uint32_t ctas_cap, 
                   uint32_t* scores, cudaStream_t st) {
   StagedLayout lay = make_staged_layout(ix->p);
   lay.extra_tx = ix->stall_copies ? 16u : 0u;
+  // the team copies the ids itself in 16-byte pieces (one bulk copy per bucket
+  // costs the issuing warp ~37 cycles each); the copy-wait test uses the bulk path
+  lay.async16 = ix->stall_copies ? 0u : 1u;
   // Four-row sketches run the kernel that caches the cells in TMEM; such kernels
   // hold one CTA per SM, so a CTA carries as many teams of `thr` threads as its
   // shared memory and 1024 threads allow (at most four).
