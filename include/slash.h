@@ -134,14 +134,19 @@ int slash_insert_host(slash_index *ix, const uint64_t *h_offs, const uint32_t *h
 int slash_query(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n_queries,
                 uint32_t topk, int32_t *d_ids_out, uint32_t *d_scores_out, void *cuda_stream);
 
-/* Query schedules.  Both give bit-identical results. */
-#define SLASH_QUERY_FUSED 0u  /* one persistent launch: hash -> gather -> count -> top-k per CTA */
-#define SLASH_QUERY_PLAIN 1u  /* one launch per stage: hash kernel, then gather/count/top-k kernel */
+/* Query schedules.  All give bit-identical results. */
+#define SLASH_QUERY_FUSED 0u       /* one persistent launch: hash -> gather -> count -> top-k per CTA team   */
+#define SLASH_QUERY_PLAIN 1u       /* one launch per stage: hash kernel, then gather/count/top-k kernel      */
+#define SLASH_QUERY_WARP_FUSED 2u  /* one warp per query (hash included); for queries with few candidates:
+                                      up to 32 counted by warp matches, up to 512 in a per-warp table, more
+                                      by the general kernel.  topk <= 10 and cm_width <= 32768 only          */
+#define SLASH_QUERY_WARP_PLAIN 3u  /* the same after the hash kernel                                          */
 
 typedef struct {
-  uint32_t mode;         /* SLASH_QUERY_FUSED or SLASH_QUERY_PLAIN                     */
-  uint32_t threads;      /* threads per CTA: 256, 512 or 1024 (0 = the index's default)  */
-  uint32_t ctas_per_sm;  /* cap on resident CTAs per SM (0 = as many as smem allows)     */
+  uint32_t mode;         /* SLASH_QUERY_FUSED, _PLAIN, _WARP_FUSED or _WARP_PLAIN                   */
+  uint32_t threads;      /* threads per CTA (team): 256, 512 or 1024 (0 = the index's default);
+                            the warp schedules always run 8 warps per CTA                             */
+  uint32_t ctas_per_sm;  /* cap on resident CTAs per SM (0 = as many as fit)                          */
 } slash_query_opts;
 
 /* slash_query with an explicit schedule (opts == NULL: the index's default,
@@ -152,7 +157,9 @@ int slash_query_ex(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_co
                    uint32_t topk, int32_t *d_ids_out, uint32_t *d_scores_out, const slash_query_opts *opts,
                    void *cuda_stream);
 
-/* Autotuner: time every query schedule (mode x threads x CTAs/SM) on the given
+/* Autotuner: time every query schedule (mode x threads x CTAs/SM; the warp
+ * schedules suit batches of queries with few candidates, the team schedules
+ * those with many) on the given
  * sample batch (each twice after a warm-up, CUDA events on `cuda_stream`), make
  * the fastest the index's default, and report it (*best_out, *best_ms_out may be
  * NULL).  The outputs buffers receive the sample's results.  Synchronises. */

@@ -49,13 +49,17 @@ class SlashError(RuntimeError):
 
 SLASH_QUERY_FUSED = 0
 SLASH_QUERY_PLAIN = 1
+SLASH_QUERY_WARP_FUSED = 2
+SLASH_QUERY_WARP_PLAIN = 3
+_MODES = {"fused": SLASH_QUERY_FUSED, "plain": SLASH_QUERY_PLAIN, "warp_fused": SLASH_QUERY_WARP_FUSED,
+          "warp_plain": SLASH_QUERY_WARP_PLAIN}
 
 
 class slash_query_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
 
     def __repr__(self):
-        m = "fused" if self.mode == SLASH_QUERY_FUSED else "plain"
+        m = {v: k for k, v in _MODES.items()}.get(self.mode, str(self.mode))
         return f"slash_query_opts({m}, threads={self.threads}, ctas_per_sm={self.ctas_per_sm})"
 
 
@@ -226,7 +230,7 @@ def slash_insert_host(ix: int, h_offs: torch.Tensor, h_cols: torch.Tensor, strea
 def _opts(mode, threads, ctas_per_sm):
     if mode is None:
         return None
-    m = {"fused": SLASH_QUERY_FUSED, "plain": SLASH_QUERY_PLAIN}.get(mode, mode)
+    m = _MODES.get(mode, mode)
     return slash_query_opts(int(m), int(threads or 0), int(ctas_per_sm or 0))
 
 
@@ -235,7 +239,8 @@ def slash_query(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, topk: int,
                 stream=None, mode=None, threads: int = 0, ctas_per_sm: int = 0
                 ) -> tuple[torch.Tensor, torch.Tensor]:
     """Algorithm 2 for a batch.  ``mode`` None = the index's default schedule,
-    else "fused" / "plain" (with optional ``threads`` and ``ctas_per_sm``)."""
+    else "fused" / "plain" / "warp_fused" / "warp_plain" (with optional
+    ``threads`` and ``ctas_per_sm``)."""
     nq = d_offs.numel() - 1
     if nq < 0:
         raise ValueError("d_offs needs n+1 entries")
@@ -353,7 +358,7 @@ def slash_probe_smem(mode: int, words: int = 16384, iters: int = 4096, threads: 
 
 def slash_debug_occupancy(ix: int, mode, threads: int) -> int:
     """Test support: CTAs per SM the occupancy calculator allows the query kernel of a schedule."""
-    m = {"fused": SLASH_QUERY_FUSED, "plain": SLASH_QUERY_PLAIN}.get(mode, mode)
+    m = _MODES.get(mode, mode)
     out = ctypes.c_int()
     _check(_lib.slash_debug_occupancy(ix, int(m), threads, ctypes.byref(out)), "slash_debug_occupancy")
     return int(out.value)

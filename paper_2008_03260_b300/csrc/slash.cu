@@ -1957,6 +1957,191 @@ k_query_staged(const __grid_constant__ Geo g, const StagedLayout lay, const uint
   }
 }
 
+// ----------------------------------------------------------------------------- query, one warp
+// The engine for queries with few candidates (the uneven and serving mixes: a
+// few dozen ids in the query's buckets), one warp per query and no CTA-wide
+// barrier.  Per query the warp hashes it (fused) or reads its addresses
+// (plain), reads the S*L fills and, by the candidate count M, takes one class:
+//   M <= 32   one id per lane; the count of an id's cell in row r is the number
+//             of lanes whose id falls in the same cell (__match_any_sync);
+//   M <= 512  the ids in a per-warp buffer; per row, the cells are counted in a
+//             per-warp open-addressing table (16-bit cell key, 16-bit count),
+//             read back, and the touched entries reset;
+//   larger    the query is marked (id -2) and answered by k_query_redo.
+// Either way estimate = the smallest of an id's d counts (the count-min sketch
+// of the query's candidates read only at their own cells), and the per-lane
+// register lists of the staged engine rank them (k <= kLocalTop).
+constexpr int kWarpWarps = 8;             // warps (queries in flight) per CTA
+constexpr uint32_t kWarpMaxM = 512;       // candidates one warp answers
+constexpr uint32_t kWarpTable = 1024;     // hash-table entries per warp (load <= 1/2)
+
+struct WarpLayout {
+  uint32_t per_warp;  // 32-bit words of one warp's region
+  uint32_t off_bins, off_boff, off_ids, off_est, off_tab;  // word offsets inside it
+};
+
+template <bool kFused>
+__global__ void __launch_bounds__(kWarpWarps * 32, 4)
+k_query_warp(const __grid_constant__ Geo g, const WarpLayout lay, const uint32_t* __restrict__ qbkt, uint64_t ldq,
+             const uint64_t* __restrict__ offs, const uint32_t* __restrict__ cols, uint32_t nq, uint32_t k,
+             const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill, int32_t* __restrict__ ids_out,
+             uint32_t* __restrict__ scores_out, uint32_t* __restrict__ work, uint32_t* __restrict__ err) {
+  extern __shared__ __align__(16) uint32_t wsm[];
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  uint32_t* base = wsm + warp * lay.per_warp;
+  uint32_t* m = base + lay.off_bins;   // fused: bin minima [nb], then the occupancy mask [nw]
+  uint32_t* mask = m + g.nb;
+  uint32_t* boff = base + lay.off_boff;  // [nbk + 1] candidate offsets of the buckets
+  uint32_t* bkey = boff + (g.S * g.L + 1u);  // [nbk]
+  uint32_t* idbuf = base + lay.off_ids;  // [kWarpMaxM]
+  uint16_t* est16 = reinterpret_cast<uint16_t*>(base + lay.off_est);  // [kWarpMaxM]
+  uint32_t* tab = base + lay.off_tab;    // [kWarpTable]
+  const uint32_t nbk = g.S * g.L, wm = g.w - 1u;
+  for (uint32_t i = lane; i < kWarpTable; i += 32) tab[i] = kEmpty;
+  __syncwarp();
+  uint32_t blk = 0, left = 0;
+  for (;;) {
+    if (left == 0) {  // the next 32 queries of the batch for this warp
+      uint32_t b = 0;
+      if (lane == 0) b = atomicAdd(work, 1u);
+      blk = __shfl_sync(0xFFFFFFFFu, b, 0) * 32u;
+      left = 32;
+      if (blk >= nq) break;
+    }
+    const uint32_t q = blk + (32u - left);
+    --left;
+    if (q >= nq) { left = 0; continue; }
+    int32_t* io = ids_out + (uint64_t)q * k;
+    uint32_t* so = scores_out + (uint64_t)q * k;
+    // -- bucket keys and fills; M and the buckets' offsets among the candidates
+    if (kFused) {
+      uint64_t b0 = offs[q], b1 = offs[q + 1];
+      if (b1 < b0) {
+        if (lane == 0) atomicOr(err, kErrOffs);
+        b1 = b0;
+      }
+      doph_row(g, cols, b0, b1, m, mask, err, lane);
+    }
+    uint32_t run = 0;
+    for (uint32_t i0 = 0; i0 < nbk; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      uint32_t key = 0, f = 0;
+      if (i < nbk) {
+        const uint32_t t = i % g.L;
+        key = (i << g.B) | (kFused ? table_address(g, m, t) : __ldg(qbkt + t * ldq + q));
+        f = min(__ldg(fill + key), g.R);
+      }
+      uint32_t inc = f;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= (uint32_t)o) inc += u;
+      }
+      if (i < nbk) {
+        bkey[i] = key;
+        boff[i] = run + inc - f;
+      }
+      run += __shfl_sync(0xFFFFFFFFu, inc, 31);
+    }
+    if (lane == 0) boff[nbk] = run;
+    __syncwarp();
+    const uint32_t M = run;
+    if (M > kWarpMaxM) {  // too many candidates for one warp: the general kernel answers it
+      if (lane == 0) io[0] = kRedoMark;
+      continue;
+    }
+    // -- the candidates: occurrence i's bucket by binary search over the offsets
+    auto occurrence = [&](uint32_t i) -> uint32_t {
+      uint32_t lo = 0, hi = nbk;  // boff[lo] <= i < boff[hi]
+      while (hi - lo > 1u) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (boff[mid] <= i) lo = mid; else hi = mid;
+      }
+      return __ldg(slots + (uint64_t)bkey[lo] * g.R + (i - boff[lo]));
+    };
+    uint64_t loc[kLocalTop];
+#pragma unroll
+    for (int t = 0; t < (int)kLocalTop; ++t) loc[t] = ~0ull;
+    auto push = [&](uint64_t key) {
+      if (key >= loc[kLocalTop - 1]) return;
+      bool dup = false;
+#pragma unroll
+      for (int t = 0; t < (int)kLocalTop; ++t) dup |= loc[t] == key;
+      if (dup) return;
+#pragma unroll
+      for (int t = (int)kLocalTop - 1; t > 0; --t) loc[t] = loc[t - 1] > key ? loc[t - 1] : (loc[t] > key ? key : loc[t]);
+      loc[0] = loc[0] > key ? key : loc[0];
+    };
+    if (M <= 32u) {
+      const bool have = lane < M;
+      const uint32_t id = have ? occurrence(lane) : kEmpty;
+      uint32_t e = 0xFFFFu;
+      for (uint32_t r = 0; r < g.d; ++r) {
+        const uint32_t c = mix32(id ^ g.sc[r]) & wm;
+        // lanes without an id match only themselves
+        const uint32_t grp = __match_any_sync(0xFFFFFFFFu, have ? c : (0x80000000u | lane));
+        e = min(e, (uint32_t)__popc(grp));
+      }
+      if (have) push(rank_key(e, id));
+    } else {
+      for (uint32_t i = lane; i < M; i += 32) {
+        idbuf[i] = occurrence(i);
+        est16[i] = 0xFFFFu;
+      }
+      __syncwarp();
+      for (uint32_t r = 0; r < g.d; ++r) {
+        const uint32_t sr = g.sc[r];
+        // count: key = cell (cells < w <= 65535 never equal the empty key 0xFFFF)
+        for (uint32_t i = lane; i < M; i += 32) {
+          const uint32_t c = mix32(idbuf[i] ^ sr) & wm;
+          uint32_t h = mix32(c) & (kWarpTable - 1u);
+          for (uint32_t probe = 0; probe < kWarpTable; ++probe) {
+            const uint32_t old = atomicCAS(&tab[h], kEmpty, (c << 16) | 1u);
+            if (old == kEmpty) break;
+            if ((old >> 16) == c) { atomicAdd(&tab[h], 1u); break; }
+            h = (h + 1u) & (kWarpTable - 1u);
+          }
+        }
+        __syncwarp();
+        // read each occurrence's count
+        for (uint32_t i = lane; i < M; i += 32) {
+          const uint32_t c = mix32(idbuf[i] ^ sr) & wm;
+          uint32_t h = mix32(c) & (kWarpTable - 1u);
+          for (uint32_t probe = 0; probe < kWarpTable; ++probe) {
+            const uint32_t v = tab[h];
+            if ((v >> 16) == c) { est16[i] = (uint16_t)min((uint32_t)est16[i], v & 0xFFFFu); break; }
+            h = (h + 1u) & (kWarpTable - 1u);
+          }
+        }
+        __syncwarp();
+        // empty the table for the next row / query (whole: freeing single entries
+        // of an open-addressing table would cut other keys' probe chains)
+        uint4* t4 = reinterpret_cast<uint4*>(tab);
+        for (uint32_t i = lane; i < kWarpTable / 4u; i += 32) t4[i] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+        __syncwarp();
+      }
+      for (uint32_t i = lane; i < M; i += 32) push(rank_key(est16[i], idbuf[i]));
+    }
+    // -- k rounds of the warp's smallest head (two 32-bit reductions); its holders pop it
+    for (uint32_t j = 0; j < k; ++j) {
+      const uint32_t hi = (uint32_t)(loc[0] >> 32), lo = (uint32_t)loc[0];
+      const uint32_t mh = __reduce_min_sync(0xFFFFFFFFu, hi);
+      const uint32_t ml = __reduce_min_sync(0xFFFFFFFFu, hi == mh ? lo : 0xFFFFFFFFu);
+      const uint64_t best = ((uint64_t)mh << 32) | ml;
+      if (best != ~0ull && loc[0] == best) {
+#pragma unroll
+        for (int t = 0; t < (int)kLocalTop - 1; ++t) loc[t] = loc[t + 1];
+        loc[kLocalTop - 1] = ~0ull;
+      }
+      if (lane == 0) {
+        io[j] = best != ~0ull ? (int32_t)ml : -1;
+        so[j] = best != ~0ull ? 0xFFFFu - mh : 0u;
+      }
+    }
+    __syncwarp();
+  }
+}
+
 // Answers, with query_core, every query of the batch whose first output id is
 // kRedoMark (left by k_query_staged); the query is hashed again in the CTA.
 // Each CTA scans its strided share of the batch a block of queries at a time.
@@ -2113,6 +2298,7 @@ struct slash_index {
   uint32_t* work = nullptr;                          // ring of fused-kernel work counters
   int qbps[2][3] = {};                               // CTAs/SM per (mode, threads); -1 = does not fit
   int sbps[2][3] = {};                               // the same for the staged engine
+  int wbps[2] = {};                                  // the same for the warp engine (fused, plain)
   bool staged = false;                               // the staged engine serves k <= kLocalTop
   uint32_t redo_threads = 256;                       // CTA size of k_query_redo (query_core layout fits)
   std::atomic<uint32_t> work_next{0};                // next ring slot (one per fused launch)
@@ -2420,6 +2606,73 @@ const void* staged_fn(bool fused, uint32_t thr, uint32_t d) {
   return d == 4u ? staged_fn_d<4>(fused, thr) : staged_fn_d<0>(fused, thr);
 }
 
+// k_query_redo over a batch whose first output ids mark the queries left to it.
+int launch_redo(slash_index* ix, const uint64_t* offs, const uint32_t* cols, uint32_t n, uint32_t topk, int32_t* ids,
+                uint32_t* scores, cudaStream_t st) {
+  const uint32_t rt = ix->redo_threads;
+  const QueryLayout rl = make_query_layout(ix->p, rt);
+  const uint32_t rgrid = (uint32_t)std::min<uint64_t>((n + rt - 1) / rt, (uint64_t)ix->num_sms);
+  {
+    Launch lr(ix, "k_query_redo", st);
+#define SLASH_REDO(T) \
+  k_query_redo<T><<<rgrid, T, rl.bytes, st>>>(ix->geo, rl, offs, cols, n, topk, ix->slots, ix->fill, ids, scores, ix->err)
+    if (rt == 256) SLASH_REDO(256); else if (rt == 512) SLASH_REDO(512); else SLASH_REDO(1024);
+#undef SLASH_REDO
+  }
+  SLASH_CK(cudaGetLastError());
+  return SLASH_OK;
+}
+
+// Shared-memory layout of one warp of the warp engine (words).
+WarpLayout make_warp_layout(const slash_params& p) {
+  WarpLayout l{};
+  const uint32_t nb = p.K * p.L, nw = (nb + 31) / 32, nbk = p.shards * p.L;
+  auto al = [](uint32_t x) { return (x + 3u) & ~3u; };
+  l.off_bins = 0;
+  l.off_boff = al(nb + nw);
+  l.off_ids = al(l.off_boff + 2u * nbk + 1u);  // offsets [nbk + 1], then keys [nbk]
+  l.off_est = al(l.off_ids + kWarpMaxM);
+  l.off_tab = al(l.off_est + kWarpMaxM / 2u);  // 16-bit estimates
+  l.per_warp = al(l.off_tab + kWarpTable);
+  return l;
+}
+
+bool warp_ok(const slash_index* ix, uint32_t topk) {
+  return topk <= kLocalTop && ix->p.cm_width <= 32768u &&
+         (size_t)kWarpWarps * make_warp_layout(ix->p).per_warp * 4u <= ix->smem_optin;
+}
+
+// The warp engine on n queries (rows offs[0..n] of cols), then k_query_redo for
+// the queries it left to the general kernel.
+int launch_warp(slash_index* ix, bool fused, uint32_t ctas_cap, const uint64_t* offs, const uint32_t* cols,
+                const uint32_t* qbkt, uint64_t ldq, uint32_t n, uint32_t topk, int32_t* ids, uint32_t* scores,
+                cudaStream_t st) {
+  const WarpLayout lay = make_warp_layout(ix->p);
+  const size_t smem = (size_t)kWarpWarps * lay.per_warp * 4u;
+  const void* fn = fused ? (const void*)k_query_warp<true> : (const void*)k_query_warp<false>;
+  int bps = 0;
+  int rc = cached_bps(ix->wbps[fused ? 0 : 1], fn, kWarpWarps * 32u, smem, &bps);
+  if (rc) return rc;
+  if (bps < 1) return SLASH_EINVAL;
+  if (ctas_cap) bps = std::min<int>(bps, (int)ctas_cap);
+  const uint64_t blocks = ((uint64_t)n + 31u) / 32u;  // a warp takes 32 queries at a time
+  const uint32_t grid = (uint32_t)std::min<uint64_t>((blocks + kWarpWarps - 1) / kWarpWarps,
+                                                     (uint64_t)ix->num_sms * bps);
+  uint32_t* work = ix->work + (ix->work_next.fetch_add(1u) % kWorkRing);
+  SLASH_CK(cudaMemsetAsync(work, 0, sizeof(uint32_t), st));
+  {
+    Launch lq(ix, fused ? "k_query_warp_fused" : "k_query_warp", st);
+    if (fused)
+      k_query_warp<true><<<grid, kWarpWarps * 32, smem, st>>>(ix->geo, lay, qbkt, ldq, offs, cols, n, topk, ix->slots,
+                                                             ix->fill, ids, scores, work, ix->err);
+    else
+      k_query_warp<false><<<grid, kWarpWarps * 32, smem, st>>>(ix->geo, lay, qbkt, ldq, offs, cols, n, topk,
+                                                              ix->slots, ix->fill, ids, scores, work, ix->err);
+  }
+  SLASH_CK(cudaGetLastError());
+  return launch_redo(ix, offs, cols, n, topk, ids, scores, st);
+}
+
 // Teams of `thr` threads per staged CTA: one, or with a four-row sketch (one CTA
 // per SM) as many as shared memory and 1024 threads allow, at most four.
 uint32_t staged_teams(const slash_index* ix, uint32_t thr, const StagedLayout& lay) {
@@ -2484,18 +2737,7 @@ int launch_staged(slash_index* ix, bool fused, uint32_t thr, uint32_t ctas_cap, 
                     (void*)&err};
     SLASH_CK(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, st));
   }
-  const uint32_t rt = ix->redo_threads;
-  const QueryLayout rl = make_query_layout(ix->p, rt);
-  const uint32_t rgrid = (uint32_t)std::min<uint64_t>((n + rt - 1) / rt, (uint64_t)ix->num_sms);
-  {
-    Launch lr(ix, "k_query_redo", st);
-#define SLASH_REDO(T) \
-  k_query_redo<T><<<rgrid, T, rl.bytes, st>>>(ix->geo, rl, offs, cols, n, topk, ix->slots, ix->fill, ids, scores, ix->err)
-    if (rt == 256) SLASH_REDO(256); else if (rt == 512) SLASH_REDO(512); else SLASH_REDO(1024);
-#undef SLASH_REDO
-  }
-  SLASH_CK(cudaGetLastError());
-  return SLASH_OK;
+  return launch_redo(ix, offs, cols, n, topk, ids, scores, st);
 }
 
 bool params_ok(const slash_params* p) {
@@ -2619,6 +2861,8 @@ int slash_build_index(const slash_params* p, void* cuda_stream, slash_index** ou
     for (bool f : {false, true})
       for (uint32_t d : {4u, 0u}) cudaFuncSetAttribute(staged_fn(f, t, d == 0u ? 1u : d),
                                                        cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_query_warp<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_query_warp<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_query_redo<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_query_redo<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   cudaFuncSetAttribute(k_query_redo<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
@@ -2739,12 +2983,31 @@ int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
   ApiRange api("slash_query");
   if (!ix || topk == 0 || topk > SLASH_MAX_TOPK) return SLASH_EINVAL;
   const slash_query_opts o = opts ? *opts : ix->qdef;
-  if (o.mode != SLASH_QUERY_PLAIN && o.mode != SLASH_QUERY_FUSED) return SLASH_EINVAL;
+  if (o.mode > SLASH_QUERY_WARP_PLAIN) return SLASH_EINVAL;
   const uint32_t thr = o.threads ? o.threads : default_query_threads(ix->p);
   if (thr != 256u && thr != 512u && thr != 1024u) return SLASH_EINVAL;
+  const bool warp_mode = o.mode == SLASH_QUERY_WARP_FUSED || o.mode == SLASH_QUERY_WARP_PLAIN;
+  if (warp_mode && !warp_ok(ix, topk)) return SLASH_EINVAL;
   if (n_queries == 0) return SLASH_OK;
   if (!d_offs || !d_cols || !d_ids_out || !d_scores_out) return SLASH_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (warp_mode) {
+    if (o.mode == SLASH_QUERY_WARP_FUSED)
+      return launch_warp(ix, true, o.ctas_per_sm, d_offs, d_cols, nullptr, 0, n_queries, topk, d_ids_out,
+                         d_scores_out, st);
+    const uint64_t chunk = std::min<uint64_t>(n_queries, 1ull << 22);
+    int rc = grow_query_ws(ix, chunk);
+    if (rc) return rc;
+    for (uint64_t q0 = 0; q0 < n_queries; q0 += chunk) {
+      const uint32_t n = (uint32_t)std::min<uint64_t>(chunk, n_queries - q0);
+      rc = run_hash(ix, d_offs + q0, d_cols, n, 0, ix->qbkt, n, nullptr, false, st);
+      if (rc) return rc;
+      rc = launch_warp(ix, false, o.ctas_per_sm, d_offs + q0, d_cols, ix->qbkt, n, n, topk, d_ids_out + q0 * topk,
+                       d_scores_out + q0 * topk, st);
+      if (rc) return rc;
+    }
+    return SLASH_OK;
+  }
   if (ix->staged && topk <= kLocalTop) {
     if (o.mode == SLASH_QUERY_FUSED)
       return launch_staged(ix, true, thr, o.ctas_per_sm, d_offs, d_cols, nullptr, 0, n_queries, topk, d_ids_out,
@@ -2821,7 +3084,7 @@ int slash_autotune(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
                    slash_query_opts* best_out, float* best_ms_out) {
   if (!ix || n_queries == 0) return SLASH_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  const uint32_t modes[2] = {SLASH_QUERY_FUSED, SLASH_QUERY_PLAIN};
+  const uint32_t modes[4] = {SLASH_QUERY_FUSED, SLASH_QUERY_PLAIN, SLASH_QUERY_WARP_FUSED, SLASH_QUERY_WARP_PLAIN};
   const uint32_t threads[3] = {256, 512, 1024};
   cudaEvent_t a, b;
   SLASH_CK(cudaEventCreate(&a));
@@ -2831,6 +3094,7 @@ int slash_autotune(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
   int rc = SLASH_OK;
   for (uint32_t m : modes) {
     for (uint32_t t : threads) {
+      if (m >= SLASH_QUERY_WARP_FUSED && t != 256u) continue;  // the warp schedules have one CTA shape
       for (uint32_t cps = 0; cps <= 1; ++cps) {  // 0 = as many CTAs per SM as fit, 1 = one
         slash_query_opts o{m, t, cps};
         float ms = 3.4e38f;

@@ -146,6 +146,12 @@ def test_query_tiny_workload_bit_exact(topk):
         ix.sync()
         assert np.array_equal(ids.cpu().numpy(), want_ids)
         assert np.array_equal(_host_u32(sc), want_sc)
+        if topk <= 10:
+            for mode in ("warp_fused", "warp_plain"):
+                ids, sc = ix.query(_dev(qo), _dev(qc), topk, mode=mode)
+                ix.sync()
+                assert np.array_equal(ids.cpu().numpy(), want_ids), mode
+                assert np.array_equal(_host_u32(sc), want_sc), mode
         slots, fill = ix.export()
     ws, wf = oix.export()
     assert np.array_equal(fill, wf) and np.array_equal(slots, ws)
@@ -167,6 +173,11 @@ def test_query_sharded_bit_exact(shards, R, B):
         _gpu_insert(ix, offs, cols, [0, 5000, 5001, n])
         ids, sc = ix.query(_dev(qo), _dev(qc), 10)
         ix.sync()
+        for mode in ("warp_fused", "warp_plain"):
+            wi, ws_ = ix.query(_dev(qo), _dev(qc), 10, mode=mode)
+            ix.sync()
+            assert np.array_equal(wi.cpu().numpy(), ids.cpu().numpy()), mode
+            assert np.array_equal(_host_u32(ws_), _host_u32(sc)), mode
         slots, fill = ix.export()
     ws, wf = oix.export()
     assert np.array_equal(fill, wf) and np.array_equal(slots, ws)
@@ -211,7 +222,7 @@ def test_query_capped_bin_decides_top10(shards, L, R, d):
     assert want_sc.max() >= 255
     with s.Index(p) as ix:
         ix.insert(_dev(offs), _dev(cols))
-        for mode in ("fused", "plain"):
+        for mode in ("fused", "plain", "warp_fused", "warp_plain"):
             ids, sc = ix.query(_dev(qo), _dev(qc), 10, mode=mode)
             ix.sync()
             assert np.array_equal(ids.cpu().numpy(), want_ids), mode
@@ -234,7 +245,7 @@ def test_query_few_distinct_ids_many_occurrences_pads():
     assert (want_ids[0] == -1).any() and want_ids[0][0] >= 0
     with s.Index(p) as ix:
         ix.insert(_dev(o2), _dev(c2))
-        for mode in ("fused", "plain"):
+        for mode in ("fused", "plain", "warp_fused", "warp_plain"):
             ids, sc = ix.query(_dev(qo), _dev(qc), 10, mode=mode)
             ix.sync()
             assert np.array_equal(ids.cpu().numpy(), want_ids), mode
@@ -303,9 +314,15 @@ def test_every_query_schedule_is_bit_exact(shards, R, B, w, topk):
     with s.Index(p) as ix:
         ix.insert(_dev(offs), _dev(cols))
         dq, dc = _dev(qo), _dev(qc)
-        for mode in ("fused", "plain"):
+        for mode in ("fused", "plain", "warp_fused", "warp_plain"):
             for threads in (256, 512, 1024):
                 for cps in (0, 1):
+                    if mode.startswith("warp") and (topk > 10 or threads != 256):
+                        if topk > 10:  # the warp schedules serve k <= 10 only
+                            with pytest.raises(s.SlashError) as e:
+                                ix.query(dq, dc, topk, mode=mode, threads=threads, ctas_per_sm=cps)
+                            assert e.value.code == s.SLASH_EINVAL
+                        continue
                     ids, sc = ix.query(dq, dc, topk, mode=mode, threads=threads, ctas_per_sm=cps)
                     ix.sync()
                     assert np.array_equal(ids.cpu().numpy(), want_ids), (mode, threads, cps)
@@ -330,7 +347,7 @@ def test_uneven_queries_bit_exact():
     want_ids, want_sc = _oracle_index(p, offs, cols).query(qo, qc, w.topk)
     with s.Index(p) as ix:
         ix.insert(_dev(offs), _dev(cols))
-        for mode in ("fused", "plain"):
+        for mode in ("fused", "plain", "warp_fused", "warp_plain"):
             ids, sc = ix.query(_dev(qo), _dev(qc), w.topk, mode=mode)
             ix.sync()
             assert np.array_equal(ids.cpu().numpy(), want_ids), mode
