@@ -728,12 +728,45 @@ def bench_stream(args, w: workloads.Workload) -> dict:
     h_ids = ids.cpu().numpy()
     recall = float(np.mean((h_ids == src[:, None]).any(axis=1)))
     ix.close()
-    return {"metric": "streamed insert rows/s (device-generated, never stored) and top-100 queries/s",
-            "value": n_rows / t_all, "unit": "rows/s", "n_gpus": 1, "steps": 1, "warmup": 0,
-            "ms_per_step": 1e3 * t_all, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u32", "data": "synthetic (generated on the device)", "config": config_of(w, args),
-            "generate_rows_per_s": n_rows / t_gen, "insert_only_rows_per_s": n_rows / (t_all - t_gen),
-            "queries_per_s": nq / t_q, "planted_recall_at_k": recall, "clocks": clk.summary()}
+    out = {"metric": "streamed insert rows/s (device-generated, never stored) and top-100 queries/s",
+           "value": n_rows / t_all, "unit": "rows/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+           "ms_per_step": 1e3 * t_all, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u32", "data": "synthetic (generated on the device)", "config": config_of(w, args),
+           "generate_rows_per_s": n_rows / t_gen, "insert_only_rows_per_s": n_rows / (t_all - t_gen),
+           "queries_per_s": nq / t_q, "planted_recall_at_k": recall, "clocks": clk.summary()}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"], out["recall_vs_exact"] = stream_exact_baseline(w, g, retained, qo, qc, h_ids)
+    return out
+
+
+def stream_exact_baseline(w: workloads.Workload, g, retained: int, qo, qc, h_ids, n_eval: int = 1000):
+    """The oracle's exact search on the host: the brute-force Jaccard top-k of
+    the first n_eval queries over the retained rows (the first `retained` rows
+    of the stream, regenerated on the host), on every host core.  Its answers are
+    the ground truth of the index's recall on that subsample: of the returned
+    ids, only retained rows can be in the truth."""
+    import oracle
+    cores, model = cpu_info()
+    offs, cols = g.rows(w.seed, 0, retained, lo=w.nnz_lo, hi=w.nnz_hi)
+    ne = min(n_eval, len(qo) - 1)
+    t = time.perf_counter()
+    truth, inter, uni = oracle.jaccard_topk(offs, cols, qo[:ne + 1], qc[:int(qo[ne])], w.topk, dim=w.dim,
+                                            threads=cores)
+    dt = time.perf_counter() - t
+    got = h_ids[:ne]
+    hit = [len(set(got[i][got[i] >= 0].tolist()) & set(truth[i][truth[i] >= 0].tolist())) for i in range(ne)]
+    ret = [int(((got[i] >= 0) & (got[i] < retained)).sum()) for i in range(ne)]
+    k = w.topk
+    recall = {"queries": ne, "retained_rows": retained,
+              "recall_at_k": float(np.mean([h / k for h in hit])),
+              "precision_among_retained": float(sum(hit) / max(1, sum(ret))),
+              "exact_nn_found": float(np.mean([truth[i][0] in set(got[i].tolist()) for i in range(ne)])),
+              "note": "truth = exact Jaccard top-k over the retained rows; the index answers over all rows, so "
+                      "recall_at_k counts truth rows among ids that may also come from non-retained rows"}
+    base = {"value": ne / dt, "unit": "queries/s", "cores": cores, "kind": "oracle", "cpu_model": model,
+            "sample": f"exact brute-force Jaccard top-{k} of {ne} queries over the first {retained} rows "
+                      f"(all {cores} host cores, {dt:.1f}s)"}
+    return base, recall
 
 
 def bench_topkapi(args, w: workloads.Workload) -> dict:

@@ -86,6 +86,8 @@ def _load():
             lib.or_query.argtypes = [vp, vp, vp, u64, u32, vp, vp]
             lib.or_next_id.restype = u64
             lib.or_next_id.argtypes = [vp]
+            lib.or_jaccard_topk.restype = i32
+            lib.or_jaccard_topk.argtypes = [vp, vp, u64, u32, vp, vp, u64, u32, i32, vp, vp, vp]
             lib.or_set_next_id.restype = i32
             lib.or_set_next_id.argtypes = [vp, u64]
             lib.or_tk_update.argtypes = [ctypes.POINTER(u32), ctypes.POINTER(u32), u32]
@@ -308,6 +310,19 @@ def tk_merge(a: tuple[int, int], b: tuple[int, int]) -> tuple[int, int]:
     h, c = ctypes.c_uint32(a[0]), ctypes.c_uint32(a[1])
     _load().or_tk_merge_cell(ctypes.byref(h), ctypes.byref(c), b[0], b[1])
     return int(h.value), int(c.value)
+
+
+def jaccard_topk(offs, cols, qoffs, qcols, k: int, dim: int = 1 << 20, threads: int = 1):
+    """Exact Jaccard top-k of every query over the collection (brute force):
+    (ids [nq][k] (-1 pad), intersections, unions) ranked (similarity desc, id asc)."""
+    offs, cols, qoffs, qcols = _u64(offs), _u32(cols), _u64(qoffs), _u32(qcols)
+    nq = qoffs.size - 1
+    ids = np.empty((nq, k), np.int32)
+    inter = np.empty((nq, k), np.uint32)
+    uni = np.empty((nq, k), np.uint32)
+    _load().or_jaccard_topk(_p(offs), _p(cols), offs.size - 1, dim, _p(qoffs), _p(qcols), nq, k, threads, _p(ids),
+                            _p(inter), _p(uni))
+    return ids, inter, uni
 
 
 def tk_fold(sketches) -> tuple[np.ndarray, np.ndarray]:

@@ -788,3 +788,76 @@ int or_tk_query(const void *p, const uint64_t *offs, const uint32_t *cols, uint6
   free(codes); free(mh); free(mc); free(sh); free(sn);
   return rc;
 }
+
+/* ------------------------------------------------------------------ exact neighbours (ground truth)
+ * The quality the index approximates (Sec. 2.2: MinHash collides with
+ * probability equal to the Jaccard similarity): for each query, the k rows of
+ * the collection with the largest Jaccard similarity |q & x| / |q | x|,
+ * ranked (similarity desc, id asc), by brute force.  Rows and queries are sets
+ * of feature ids < dim (no duplicates); an empty union counts as similarity 0.
+ * ids[q*k + i] (-1 pad), inter/uni[q*k + i] the similarity's numerator and
+ * denominator.  `threads` workers take disjoint query ranges. */
+typedef struct {
+  const uint64_t *offs; const uint32_t *cols; uint64_t n; uint32_t dim;
+  const uint64_t *qoffs; const uint32_t *qcols; uint64_t q0, q1; uint32_t k;
+  int32_t *ids; uint32_t *inter, *uni;
+} or_jac_job;
+
+/* a/b > c/d for similarities (b, d > 0; a similarity with b == 0 is 0) */
+static int or_jac_better(uint32_t a, uint32_t b, uint64_t ia, uint32_t c, uint32_t d, uint64_t ic) {
+  uint64_t l = b ? (uint64_t)a * (d ? d : 1) : 0, r = d ? (uint64_t)c * (b ? b : 1) : 0;
+  if (b == 0) l = 0;
+  if (d == 0) r = 0;
+  if (l != r) return l > r;
+  return ia < ic;
+}
+
+static void *or_jac_run(void *arg) {
+  or_jac_job *j = (or_jac_job *)arg;
+  uint64_t words = ((uint64_t)j->dim + 63) / 64;
+  uint64_t *bits = (uint64_t *)calloc(words, sizeof(uint64_t));
+  for (uint64_t q = j->q0; q < j->q1; ++q) {
+    const uint32_t *qc = j->qcols + (j->qoffs[q] - j->qoffs[0]);
+    uint32_t qn = (uint32_t)(j->qoffs[q + 1] - j->qoffs[q]);
+    for (uint32_t i = 0; i < qn; ++i) bits[qc[i] >> 6] |= 1ull << (qc[i] & 63);
+    int32_t *bi = j->ids + q * j->k;
+    uint32_t *bn = j->inter + q * j->k, *bu = j->uni + q * j->k;
+    uint32_t have = 0;
+    for (uint64_t x = 0; x < j->n; ++x) {
+      const uint32_t *xc = j->cols + (j->offs[x] - j->offs[0]);
+      uint32_t xn = (uint32_t)(j->offs[x + 1] - j->offs[x]), in = 0;
+      for (uint32_t i = 0; i < xn; ++i) in += (uint32_t)((bits[xc[i] >> 6] >> (xc[i] & 63)) & 1u);
+      uint32_t un = qn + xn - in;
+      if (have == j->k && !or_jac_better(in, un, x, bn[have - 1], bu[have - 1], (uint64_t)bi[have - 1])) continue;
+      uint32_t pos = have < j->k ? have++ : j->k - 1;
+      while (pos > 0 && or_jac_better(in, un, x, bn[pos - 1], bu[pos - 1], (uint64_t)bi[pos - 1])) {
+        bi[pos] = bi[pos - 1]; bn[pos] = bn[pos - 1]; bu[pos] = bu[pos - 1];
+        --pos;
+      }
+      bi[pos] = (int32_t)x; bn[pos] = in; bu[pos] = un;
+    }
+    for (uint32_t i = have; i < j->k; ++i) { bi[i] = -1; bn[i] = 0; bu[i] = 0; }
+    for (uint32_t i = 0; i < qn; ++i) bits[qc[i] >> 6] = 0;
+  }
+  free(bits);
+  return NULL;
+}
+
+int or_jaccard_topk(const uint64_t *offs, const uint32_t *cols, uint64_t n, uint32_t dim, const uint64_t *qoffs,
+                    const uint32_t *qcols, uint64_t nq, uint32_t k, int threads, int32_t *ids, uint32_t *inter,
+                    uint32_t *uni) {
+  if (threads < 1) threads = 1;
+  if ((uint64_t)threads > nq) threads = nq ? (int)nq : 1;
+  or_jac_job *job = (or_jac_job *)calloc(threads, sizeof(or_jac_job));
+  pthread_t *tid = (pthread_t *)calloc(threads, sizeof(pthread_t));
+  for (int t = 0; t < threads; ++t) {
+    or_jac_job *j = &job[t];
+    j->offs = offs; j->cols = cols; j->n = n; j->dim = dim; j->qoffs = qoffs; j->qcols = qcols;
+    j->q0 = nq * (uint64_t)t / threads; j->q1 = nq * (uint64_t)(t + 1) / threads; j->k = k;
+    j->ids = ids; j->inter = inter; j->uni = uni;
+    pthread_create(&tid[t], NULL, or_jac_run, j);
+  }
+  for (int t = 0; t < threads; ++t) pthread_join(tid[t], NULL);
+  free(job); free(tid);
+  return 0;
+}

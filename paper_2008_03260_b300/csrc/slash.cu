@@ -2982,7 +2982,13 @@ int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
                    void* cuda_stream) {
   ApiRange api("slash_query");
   if (!ix || topk == 0 || topk > SLASH_MAX_TOPK) return SLASH_EINVAL;
-  const slash_query_opts o = opts ? *opts : ix->qdef;
+  slash_query_opts o = opts ? *opts : ix->qdef;
+  if (!opts && !(ix->staged && topk <= kLocalTop)) {
+    // the default for a k the staged and warp engines do not serve: the general
+    // kernel at its own default CTA size
+    o.mode = o.mode == SLASH_QUERY_PLAIN || o.mode == SLASH_QUERY_WARP_PLAIN ? SLASH_QUERY_PLAIN : SLASH_QUERY_FUSED;
+    o.threads = ix->redo_threads;
+  }
   if (o.mode > SLASH_QUERY_WARP_PLAIN) return SLASH_EINVAL;
   const uint32_t thr = o.threads ? o.threads : default_query_threads(ix->p);
   if (thr != 256u && thr != 512u && thr != 1024u) return SLASH_EINVAL;

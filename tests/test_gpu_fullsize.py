@@ -82,3 +82,45 @@ def test_topkapi_full_size_sampled_parity():
     want_ids, want_sc = oix.query(qo, qc, tw.topk)
     assert np.array_equal(gids, want_ids)
     assert np.array_equal(gsc, want_sc)
+
+
+def test_stream_at_scale_sampled_parity():
+    """The `stream` shape (K=8, L=32, 2^20 buckets per table, R=256, top-100)
+    with 64M rows generated on the device in 16M-row chunks and never stored:
+    the buckets of 200 queries plus 2000 random buckets, and the 200 answers,
+    against an oracle that keeps only those buckets and takes all 64M rows from
+    the host generator (64M rows: the largest stream whose host-side oracle
+    finishes within a test's time on the machine's cores)."""
+    import paper_2008_03260_b300 as s
+    from datagen.workloads import STREAM as sw
+    n, chunk = 64 << 20, sw.extra["chunk_rows"]
+    g = datagen.Generator()
+    dg = datagen.DeviceRows(g)
+    p = s.Params(**sw.params(capacity=n))
+    qo, qc, _ = g.queries(sw.seed, sw.qseed, 200, n, **sw.query_kwargs())
+    with s.Index(p) as ix:
+        for r0 in range(0, n, chunk):
+            o, c = dg.rows(sw.seed, r0, min(chunk, n - r0), lo=sw.nnz_lo, hi=sw.nnz_hi)
+            ix.insert(o, c)
+            del o, c
+        ids, sc = ix.query(_dev(qo), _dev(qc), sw.topk)
+        ix.sync()
+        _, qbk = oracle.hash_rows(sw.K, sw.L, sw.log2_buckets, sw.seed, sw.cm_rows, qo, qc, want_codes=False)
+        rng = np.random.default_rng(6)
+        rt = np.concatenate([np.tile(np.arange(sw.L), len(qo) - 1), rng.integers(0, sw.L, 2000)]).astype(np.uint32)
+        rb = np.concatenate([qbk.ravel(), rng.integers(0, 1 << sw.log2_buckets, 2000)]).astype(np.uint32)
+        gslots, gfill = ix.buckets(np.zeros_like(rt), rt, rb)
+        gids, gsc = ids.cpu().numpy(), sc.cpu().numpy().view(np.uint32)
+    oix = oracle.Index(K=sw.K, L=sw.L, log2_buckets=sw.log2_buckets, reservoir=sw.reservoir, cm_rows=sw.cm_rows,
+                       cm_width=sw.cm_width, seed=sw.seed, capacity=n, partial=(rt, rb))
+    for r0 in range(0, n, chunk):
+        o, c = g.rows(sw.seed, r0, min(chunk, n - r0), lo=sw.nnz_lo, hi=sw.nnz_hi)
+        assert oix.insert(o - o[0], c, threads=datagen.default_threads()) == r0
+        del o, c
+    for i in range(len(rt)):
+        want, wf = oix.bucket(int(rt[i]), int(rb[i]))
+        assert gfill[i] == wf and np.array_equal(gslots[i], want), (int(rt[i]), int(rb[i]))
+    assert gfill.sum() > 0
+    want_ids, want_sc = oix.query(qo, qc, sw.topk)
+    assert np.array_equal(gids, want_ids)
+    assert np.array_equal(gsc, want_sc)

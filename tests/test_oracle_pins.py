@@ -6,6 +6,7 @@ tiny inputs -- chosen so that a plausible slip (a dropped term, a wrong side,
 a transposed operand) fails at least one test here.
 """
 import os
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -368,3 +369,37 @@ def test_planted_recall_matches_binomial_model():
         js = [len(qs[i] & r) / len(qs[i] | r) for r in rows]
         nn_top1 += int(np.argmax(js)) == ids[i, 0]
     assert nn_top1 >= 85
+
+
+# ---------------------------------------------------------------------------- exact neighbours (ground truth)
+def _jaccard_brute(rows, q):
+    qs = set(int(v) for v in q)
+    out = []
+    for i, r in enumerate(rows):
+        rs = set(int(v) for v in r)
+        u = len(qs | rs)
+        out.append((Fraction(len(qs & rs), u) if u else Fraction(0), i))
+    out.sort(key=lambda t: (-t[0], t[1]))
+    return out
+
+
+def test_jaccard_topk_against_python_sets():
+    """The brute-force neighbours equal a Python-set computation of the
+    similarity (exact fractions), ties by id, on random small sets."""
+    rng = np.random.default_rng(11)
+    dim = 256
+    rows = [np.sort(rng.choice(dim, int(rng.integers(0, 12)), replace=False)).astype(np.uint32) for _ in range(300)]
+    qs = [np.sort(rng.choice(dim, int(rng.integers(0, 12)), replace=False)).astype(np.uint32) for _ in range(40)]
+    qs[0] = rows[17].copy()                      # a copy of a row: similarity 1
+    qs[1] = np.zeros(0, np.uint32)               # empty query: similarity 0 to all
+    offs = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.uint64)
+    qo = np.concatenate([[0], np.cumsum([len(q) for q in qs])]).astype(np.uint64)
+    ids, inter, uni = oracle.jaccard_topk(offs, np.concatenate(rows), qo, np.concatenate(qs), 7, dim=dim, threads=3)
+    for qi, q in enumerate(qs):
+        want = _jaccard_brute(rows, q)[:7]
+        assert [i for _, i in want] == ids[qi].tolist(), qi
+        for j, (f, _) in enumerate(want):
+            got = Fraction(int(inter[qi, j]), int(uni[qi, j])) if uni[qi, j] else Fraction(0)
+            assert got == f
+    assert ids[0, 0] == 17 and inter[0, 0] == uni[0, 0] == len(rows[17])
+    assert ids[1].tolist() == list(range(7))     # all similarities 0: smallest ids
