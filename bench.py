@@ -294,15 +294,21 @@ def config_of(w, args) -> dict:
 
 
 # ----------------------------------------------------------------------------- GPU arm
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# unchanged kernels, measured by ncu (one-pass metrics) on this full-size
-# workload: 50M rows, 64 tables, 2^18 buckets.
-TRAFFIC_PER_LAUNCH = {
-    "k_hash_insert": (9654329344 + 13679100928, "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel, full-size criteo insert, one-pass metrics"),
-    "k_scatter": (18967236096 + 13676748800, "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel, full-size criteo insert, one-pass metrics"),
-    "k_merge_small": (7899732224 + 8946798080, "ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel, full-size criteo insert, one-pass metrics"),
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per unit of work of
+# the unchanged kernels, from single-kernel ncu captures of a 2,000,000-row
+# criteo-shaped insert (2^14 buckets).  Both kernels' traffic is per row (the
+# CSR read and the address write) or per (row, table) pair (the record read and
+# the id write), so a full-size launch's traffic is the per-unit figure times
+# its units.
+TRAFFIC_PER_UNIT = {
+    "k_hash_insert": ((347228416 + 457842176) / 2_000_000, "row",
+                      "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_hash_reg<12, 6, 1> on 2M criteo-shaped "
+                      "rows (2^14 buckets), 402.5 B/row, scaled by the rows of the launch"),
+    "k_scatter": ((562054400 + 367997952) / 128_000_000, "pair",
+                  "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_scatter on 2M criteo-shaped rows x 64 tables "
+                  "(2^14 buckets), 7.27 B/pair, scaled by the (row, table) pairs of the launch"),
 }
-TRAFFIC_SHAPE = {"rows": 50_000_000, "L": 64, "log2_buckets": 18, "reservoir": 128}
+TRAFFIC_SHAPE = {"K": 6, "L": 64, "reservoir": 128}
 # Warp instructions per row of the insert hash (smsp__inst_executed.sum of a
 # 2M-row ncu capture / 2M; the count per row does not depend on the table size).
 HASH_WARP_INST_PER_ROW = (1094409036 / 2_000_000, "ncu smsp__inst_executed.sum of k_hash_reg<12, 6, 1> on 2M "
@@ -331,11 +337,12 @@ def smem_probe(words: int = 16384, threads: int = 512, ctas_per_sm: int = 2) -> 
     names = {0: "atomic_random", 1: "load_random", 2: "atomic_own_bank", 3: "atomic_same_word"}
     out = {"words": words, "threads": threads, "ctas_per_sm": ctas_per_sm}
     with Clocks(0) as clk:
-        for mode, nm in names.items():
-            ms, ops = slash.slash_probe_smem(mode, words, 4096 if mode != 3 else 512, threads, ctas_per_sm)
+        for mode, nm in names.items():  # long enough (~0.1 s a launch) for the clock samples to see the load
+            ms, ops = slash.slash_probe_smem(mode, words, 262144 if mode != 3 else 32768, threads, ctas_per_sm)
             out[nm + "_ops_per_s"] = ops / (ms / 1e3)
     c = clk.summary()
-    mhz = c.get("sm_mhz") or 2032.0
+    # per clock at the maximum SM clock: a lower bound if the clock sagged under load
+    mhz = c.get("sm_max_mhz") or 2032.0
     for nm in names.values():
         out[nm + "_per_sm_clk"] = out[nm + "_ops_per_s"] / (props.multi_processor_count * mhz * 1e6)
     out["clocks"] = c
@@ -529,10 +536,10 @@ def main():
         bytes_per_launch = algo[dom] / launches_per_step
         ach = bytes_per_launch / (kern[dom]["ms_per_launch"] / 1e3) / 1e9
         traffic, tsrc = None, None
-        shape = {"rows": rows, "L": L, "log2_buckets": w.log2_buckets, "reservoir": w.reservoir}
-        if dom in TRAFFIC_PER_LAUNCH and shape == TRAFFIC_SHAPE and launches_per_step == 1:
-            traffic, src = TRAFFIC_PER_LAUNCH[dom]
-            tsrc = src
+        shape = {"K": w.K, "L": L, "reservoir": w.reservoir}
+        if dom in TRAFFIC_PER_UNIT and shape == TRAFFIC_SHAPE and launches_per_step == 1:
+            per_unit, unit, tsrc = TRAFFIC_PER_UNIT[dom]
+            traffic = per_unit * (rows if unit == "row" else rows * L)
         roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / pk["hbm_gbs"], "traffic": traffic, "traffic_source": tsrc,
                 "peak_source": pk["source"],
