@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -362,8 +363,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--schedule", default="", help="query schedule without autotuning, e.g. plain:1024")
-    ap.add_argument("--serve-seconds", type=float, default=5.0)
-    ap.add_argument("--serve-max-requests", type=int, default=20_000)
+    ap.add_argument("--serve-seconds", type=float, default=30.0)
+    ap.add_argument("--serve-max-requests", type=int, default=100_000)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-max-batch", type=int, default=8192)
+    ap.add_argument("--serve-rates", default="1000,10000,100000")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--probe", action="store_true", help="print the shared-memory microbenchmark line and exit")
     args = ap.parse_args()
@@ -662,7 +666,7 @@ def bench_uneven(args, w: workloads.Workload) -> dict:
             "clocks": clk.summary()}
 
 
-def bench_serving(args, w: workloads.Workload, rates=(1_000, 10_000, 100_000)) -> dict:
+def bench_serving(args, w: workloads.Workload) -> dict:
     """Poisson request streams against an 8-shard resident index: p50/p99 latency."""
     torch, slash = _gpu_setup(w)
     from paper_2008_03260_b300.serve import GpuExecutor, poisson_requests, serve
@@ -673,13 +677,35 @@ def bench_serving(args, w: workloads.Workload, rates=(1_000, 10_000, 100_000)) -
     ix = slash.Index(slash.Params(**w.params()))
     ix.insert(dev(offs), dev(cols))
     ix.sync()
+    # the query schedule: slots run concurrently on their own streams, which the
+    # fused schedules allow (no shared workspace); the faster one on a batch of
+    # the request pool serves
+    sample = 1 << 16
+    d_qo = dev((qo[:sample + 1] - qo[0]).astype(np.uint64))
+    d_qc = dev(np.ascontiguousarray(qc[int(qo[0]):int(qo[sample])]))
+    ids = torch.empty((sample, w.topk), dtype=torch.int32, device="cuda")
+    sc = torch.empty_like(ids)
+    timings = {}
+    for mode in ("fused", "warp_fused"):
+        for i in range(4):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ix.query(d_qo, d_qc, w.topk, d_ids_out=ids, d_scores_out=sc, mode=mode)
+            b.record()
+            b.synchronize()
+            if i >= 2:
+                timings[mode] = min(timings.get(mode, math.inf), a.elapsed_time(b))
+    sched = {"mode": min(timings, key=timings.get), "threads": 0}
+    log(f"[bench] serving: schedule {sched} (ms per {sample} queries: {timings})")
     per_rate = {}
+    rates = [int(x) for x in args.serve_rates.split(",")]
     for rate in rates:
         n_req = int(min(args.serve_seconds * rate, args.serve_max_requests))
         reqs = poisson_requests(float(rate), n_req, qo, qc, seed=rate)
-        ex = GpuExecutor(ix, topk=w.topk, slots=4)
+        ex = GpuExecutor(ix, topk=w.topk, slots=args.serve_slots, mode=sched["mode"], threads=sched["threads"])
         with Clocks(0) as clk:
-            _, summ = serve(reqs, ex, topk=w.topk, slots=4, mem_budget=16 << 30, max_batch_queries=1 << 16)
+            _, summ = serve(reqs, ex, topk=w.topk, slots=args.serve_slots, mem_budget=16 << 30,
+                            max_batch_queries=args.serve_max_batch)
         summ["clocks"] = clk.summary()
         per_rate[str(rate)] = summ
         log(f"[bench] serving {rate} req/s: {summ}")
@@ -689,6 +715,8 @@ def bench_serving(args, w: workloads.Workload, rates=(1_000, 10_000, 100_000)) -
             "value": top["queries_per_s"], "unit": "queries/s", "n_gpus": 1, "steps": len(rates),
             "warmup": 0, "ms_per_step": top["p50_ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": config_of(w, args),
+            "schedule": sched, "schedule_ms_per_65536_queries": timings, "slots": args.serve_slots,
+            "max_batch_queries": args.serve_max_batch,
             "rates": per_rate}
 
 

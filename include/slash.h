@@ -27,9 +27,10 @@
  *     sticky error word is set, and the next slash_sync() returns SLASH_EDATA
  *     and clears it.
  *   - An index is not thread-safe: serialise calls on one index.  Inserts, plain
- *     queries and debug calls use per-index workspace, so issue them on one
- *     stream at a time.  Fused queries (the default schedule) use no shared
- *     workspace: up to 4096 of them may be in flight at once on different
+ *     queries (SLASH_QUERY_PLAIN, SLASH_QUERY_WARP_PLAIN) and debug calls use
+ *     per-index workspace, so issue them on one stream at a time.  Fused queries
+ *     (SLASH_QUERY_FUSED, the default schedule, and SLASH_QUERY_WARP_FUSED) use no
+ *     shared workspace: up to 4096 of them may be in flight at once on different
  *     streams, as long as no insert or reset runs meanwhile.
  *   - CSR input: row i's feature ids are d_cols[d_offs[i] .. d_offs[i+1]), ids
  *     in [0, dim); d_offs holds n+1 entries (d_offs[0] need not be 0).  Order

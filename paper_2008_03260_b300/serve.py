@@ -148,39 +148,66 @@ def concat_csr(reqs: list[Request], offs_out: np.ndarray | None = None,
 
 
 class _SlotBuffers:
-    """Page-locked host and device buffers of one slot, grown (doubling) only
-    when a batch needs more: after warm-up no batch pins or allocates memory."""
+    """Page-locked host and device buffers of one slot.  A batch's offsets and
+    features share one buffer (one copy to the device), its ids and scores
+    another (one copy back).  Grown (doubling) only when a batch needs more:
+    after warm-up no batch pins or allocates memory."""
 
     def __init__(self, torch, topk: int, queries: int, nnz: int):
         self.torch, self.topk = torch, topk
-        self.q_cap = self.nnz_cap = 0
+        self.in_cap = self.out_cap = 0
         self.ensure(queries, nnz)
+
+    @staticmethod
+    def _in_layout(queries: int, nnz: int) -> tuple[int, int]:
+        """Byte offset of the features (16-byte aligned, after the offsets) and the input size."""
+        c0 = (8 * (queries + 1) + 15) & ~15
+        return c0, c0 + 4 * max(nnz, 1)
 
     def ensure(self, queries: int, nnz: int) -> None:
         torch = self.torch
-        if queries > self.q_cap:
-            self.q_cap = max(queries, 2 * self.q_cap)
-            self.h_offs = torch.empty(self.q_cap + 1, dtype=torch.int64, pin_memory=True)
-            self.d_offs = torch.empty(self.q_cap + 1, dtype=torch.int64, device="cuda")
-            self.h_ids = torch.empty((self.q_cap, self.topk), dtype=torch.int32, pin_memory=True)
-            self.h_sc = torch.empty((self.q_cap, self.topk), dtype=torch.int32, pin_memory=True)
-            self.d_ids = torch.empty((self.q_cap, self.topk), dtype=torch.int32, device="cuda")
-            self.d_sc = torch.empty_like(self.d_ids)
-        if nnz > self.nnz_cap:
-            self.nnz_cap = max(nnz, 2 * self.nnz_cap, 1)
-            self.h_cols = torch.empty(self.nnz_cap, dtype=torch.int32, pin_memory=True)
-            self.d_cols = torch.empty(self.nnz_cap, dtype=torch.int32, device="cuda")
+        need = self._in_layout(queries, nnz)[1]
+        if need > self.in_cap:
+            self.in_cap = max(need, 2 * self.in_cap)
+            self.h_in = torch.empty(self.in_cap, dtype=torch.uint8, pin_memory=True)
+            self.d_in = torch.empty(self.in_cap, dtype=torch.uint8, device="cuda")
+        need = 8 * max(queries, 1) * self.topk
+        if need > self.out_cap:
+            self.out_cap = max(need, 2 * self.out_cap)
+            self.h_out = torch.empty(self.out_cap, dtype=torch.uint8, pin_memory=True)
+            self.d_out = torch.empty(self.out_cap, dtype=torch.uint8, device="cuda")
+
+    def views(self, nq: int, nnz: int):
+        """(host offsets, host features, device offsets, device features, input bytes,
+        device ids, device scores, output bytes) of an nq-query batch."""
+        torch = self.torch
+        c0, nin = self._in_layout(nq, nnz)
+        ob = 4 * nq * self.topk
+        return (self.h_in[:8 * (nq + 1)].view(torch.int64), self.h_in[c0:nin].view(torch.int32),
+                self.d_in[:8 * (nq + 1)].view(torch.int64), self.d_in[c0:nin].view(torch.int32), nin,
+                self.d_out[:ob].view(torch.int32).view(nq, self.topk),
+                self.d_out[ob:2 * ob].view(torch.int32).view(nq, self.topk), 2 * ob)
+
+    def results(self, nq: int) -> tuple[np.ndarray, np.ndarray]:
+        ob = 4 * nq * self.topk
+        h = self.h_out.numpy()
+        return (h[:ob].view(np.int32).reshape(nq, self.topk).copy(),
+                h[ob:2 * ob].view(np.uint32).reshape(nq, self.topk).copy())
 
 
 class GpuExecutor:
     """One CUDA stream and one set of preallocated buffers per slot: the batch
     is written into the slot's page-locked buffers, copied to the device, queried
-    (fused schedule) and the results copied back, all on the slot's stream."""
+    and the results copied back, all on the slot's stream.  The query runs the
+    given schedule (mode, threads), or the index's default one when mode is None
+    (the schedule slash_autotune picked, if it ran)."""
 
-    def __init__(self, ix, topk: int, slots: int, threads: int = 0, queries: int = 1 << 12, nnz: int = 1 << 18):
+    def __init__(self, ix, topk: int, slots: int, threads: int = 0, queries: int = 1 << 12, nnz: int = 1 << 18,
+                 mode: str | None = "fused"):
         import torch
         self.torch = torch
         self.ix, self.topk, self.threads = ix, topk, threads
+        self.sched = {} if mode is None else {"mode": mode, "threads": threads}
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.bufs = [_SlotBuffers(torch, topk, queries, nnz) for _ in range(slots)]
         self.events = [torch.cuda.Event(enable_timing=True) for _ in range(slots)]
@@ -195,16 +222,14 @@ class GpuExecutor:
         st, b = self.streams[slot], self.bufs[slot]
         nq, nnz = sum(r.nq for r in reqs), sum(len(r.cols) for r in reqs)
         b.ensure(nq, nnz)
+        h_offs, h_cols, d_offs, d_cols, nin, d_ids, d_sc, nout = b.views(nq, nnz)
         # the slot's previous batch has completed (the loop only reuses a free
         # slot), so its host buffers can be overwritten
-        concat_csr(reqs, b.h_offs.numpy().view(np.uint64), b.h_cols.numpy().view(np.uint32))
+        concat_csr(reqs, h_offs.numpy().view(np.uint64), h_cols.numpy().view(np.uint32))
         with torch.cuda.stream(st):
-            b.d_offs[:nq + 1].copy_(b.h_offs[:nq + 1], non_blocking=True)
-            b.d_cols[:nnz].copy_(b.h_cols[:nnz], non_blocking=True)
-            self.ix.query(b.d_offs[:nq + 1], b.d_cols[:max(nnz, 1)], self.topk, st, d_ids_out=b.d_ids,
-                          d_scores_out=b.d_sc, mode="fused", threads=self.threads)
-            b.h_ids[:nq].copy_(b.d_ids[:nq], non_blocking=True)
-            b.h_sc[:nq].copy_(b.d_sc[:nq], non_blocking=True)
+            b.d_in[:nin].copy_(b.h_in[:nin], non_blocking=True)
+            self.ix.query(d_offs, d_cols, self.topk, st, d_ids_out=d_ids, d_scores_out=d_sc, **self.sched)
+            b.h_out[:nout].copy_(b.d_out[:nout], non_blocking=True)
             ev = self.events[slot]
             ev.record(st)
         return (ev, slot, nq)
@@ -220,8 +245,8 @@ class GpuExecutor:
         ev, slot, nq = h
         ev.synchronize()
         t_done = self.t_ref + self.ref.elapsed_time(ev) / 1e3
-        b = self.bufs[slot]
-        return b.h_ids[:nq].numpy().copy(), b.h_sc[:nq].numpy().view(np.uint32).copy(), t_done
+        ids, sc = self.bufs[slot].results(nq)
+        return ids, sc, t_done
 
 
 def serve(requests: list[Request], executor, *, topk: int, slots: int = 4, mem_budget: int = 16 << 30,
@@ -232,12 +257,14 @@ def serve(requests: list[Request], executor, *, topk: int, slots: int = 4, mem_b
     pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
     t0 = time.perf_counter()
     n_batches = 0
+    t_launch = t_collect = 0.0  # host seconds spent launching and collecting batches
     while pending or bat.busy():
         now = time.perf_counter() - t0 if realtime else math.inf
         while pending and pending[0].arrival <= now:
             bat.arrive(pending.popleft())
         for s, b in enumerate(bat.inflight):
             if b is not None and executor.done(b.handle):
+                tc = time.perf_counter()
                 ids, sc, t_done = executor.collect(b.handle)
                 bat.finish(s)
                 q = 0
@@ -246,6 +273,7 @@ def serve(requests: list[Request], executor, *, topk: int, slots: int = 4, mem_b
                     rr.ids, rr.scores = ids[q:q + r.nq], sc[q:q + r.nq]
                     rr.launched, rr.done = b.launched, t_done - t0
                     q += r.nq
+                t_collect += time.perf_counter() - tc
         if realtime:
             for r in bat.expire(time.perf_counter() - t0):
                 res[r.rid].status = SLASH_ETIMEOUT
@@ -253,12 +281,14 @@ def serve(requests: list[Request], executor, *, topk: int, slots: int = 4, mem_b
             b = bat.next_batch(s)
             if b is None:
                 break
-            b.launched = time.perf_counter() - t0
+            tl = time.perf_counter()
+            b.launched = tl - t0
             if hasattr(executor, "launch_reqs"):
                 b.handle = executor.launch_reqs(s, b.reqs)
             else:
                 offs, cols = concat_csr(b.reqs)
                 b.handle = executor.launch(s, offs, cols)
+            t_launch += time.perf_counter() - tl
             n_batches += 1
         if not bat.queue and pending and realtime:
             wait = pending[0].arrival - (time.perf_counter() - t0)
@@ -271,6 +301,8 @@ def serve(requests: list[Request], executor, *, topk: int, slots: int = 4, mem_b
     nq = sum(q.nq for q in requests if res[q.rid].status == 0)
     span = max(r.done for r in done) - min(r.arrival for r in done) if done else 1.0
     p99 = float(np.percentile(lat, 99))
+    size = {q.rid: q.nq for q in requests}
+    small = np.array([r.latency for r in done if size[r.rid] <= 64])
     tail = [r for r in done if r.latency >= p99] or done
     summary = {"requests": len(done), "refused": len(bat.refused),
                "cancelled": sum(1 for r in res.values() if r.status == SLASH_ETIMEOUT),
@@ -281,7 +313,14 @@ def serve(requests: list[Request], executor, *, topk: int, slots: int = 4, mem_b
                # where the slowest 1% spent their time: queued on the host before
                # launch, and from launch to completion on the device
                "p99_queued_ms": 1e3 * float(np.mean([r.launched - r.arrival for r in tail])) if tail else 0.0,
-               "p99_device_ms": 1e3 * float(np.mean([r.done - r.launched for r in tail])) if tail else 0.0}
+               "p99_device_ms": 1e3 * float(np.mean([r.done - r.launched for r in tail])) if tail else 0.0,
+               # the tail of small requests alone (sizes are log-uniform: the slowest 1%
+               # overall are mostly the largest requests)
+               "p50_small_ms": 1e3 * float(np.percentile(small, 50)) if len(small) else 0.0,
+               "p99_small_ms": 1e3 * float(np.percentile(small, 99)) if len(small) else 0.0,
+               # host cost per batch of the loop's two calls into the executor
+               "host_launch_us_per_batch": 1e6 * t_launch / max(1, n_batches),
+               "host_collect_us_per_batch": 1e6 * t_collect / max(1, n_batches)}
     return list(res.values()), summary
 
 
