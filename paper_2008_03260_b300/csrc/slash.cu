@@ -1184,12 +1184,14 @@ k_query_fused(const __grid_constant__ Geo g, const QueryLayout lay, const uint64
 // most kStagedMaxBuckets buckets per query); query_core stays the general one.
 // A team of threads answers one query at a time (Algorithm 2, local and
 // cross-partition merge):
-//   - its warp 0 issues one bulk copy per non-empty bucket (cp.async.bulk,
-//     completed on an mbarrier), moving the bucket's ids into a shared-memory
-//     buffer; a bucket's run is rounded up to 4 ids, which is safe because the
-//     slots past a bucket's fill hold 0xFFFFFFFF.  With the plain schedule the
-//     keys and fills of the next query are already in the warp's registers:
-//     they were loaded while the previous query was counted;
+//   - its warp 0 lays the query's non-empty buckets out in a shared-memory id
+//     buffer (each run rounded up to 4 ids, which is safe because the slots
+//     past a bucket's fill hold 0xFFFFFFFF); then every warp of the team copies
+//     whole buckets in 16-byte cp.async pieces (or, with async16 = 0, warp 0
+//     issues one cp.async.bulk per bucket, completed on an mbarrier).  With the
+//     plain schedule the keys and fills of the next query are already in warp
+//     0's registers (loaded while this query was counted) and its bucket runs
+//     are prefetched into L2 while this query's pool is ranked;
 //   - every thread counts its share of the buffer into the packed sketch.  With
 //     four rows each thread keeps the 16 cells of its 4-id groups in its lane
 //     of tensor memory (TMEM), so the estimates need no second hashing;
@@ -1459,16 +1461,6 @@ struct Prefetch {
   uint32_t q = 0xFFFFFFFFu;    // the next query (every lane)
   uint32_t key[kPer], f[kPer];
 };
-
-// 64-bit warp minimum
-__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const uint64_t u = __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    v = u < v ? u : v;
-  }
-  return v;
-}
 
 // The count-min rows of the packed sketch.  kD > 0 fixes the number of rows at
 // compile time (the loops unroll and the row seeds sit in registers); kD = 0
