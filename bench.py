@@ -365,9 +365,9 @@ def main():
     ap.add_argument("--schedule", default="", help="query schedule without autotuning, e.g. plain:1024")
     ap.add_argument("--serve-seconds", type=float, default=30.0)
     ap.add_argument("--serve-max-requests", type=int, default=100_000)
-    ap.add_argument("--serve-slots", type=int, default=4)
-    ap.add_argument("--serve-max-batch", type=int, default=8192)
-    ap.add_argument("--serve-rates", default="1000,10000,100000")
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-max-batch", type=int, default=4096)
+    ap.add_argument("--serve-rates", default="1000,10000,30000")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--probe", action="store_true", help="print the shared-memory microbenchmark line and exit")
     args = ap.parse_args()
@@ -669,7 +669,7 @@ def bench_uneven(args, w: workloads.Workload) -> dict:
 def bench_serving(args, w: workloads.Workload) -> dict:
     """Poisson request streams against an 8-shard resident index: p50/p99 latency."""
     torch, slash = _gpu_setup(w)
-    from paper_2008_03260_b300.serve import GpuExecutor, poisson_requests, serve
+    from paper_2008_03260_b300.serve import GpuExecutor, poisson_requests, serve, serve_native
     g = datagen.Generator(dim_bits=w.dim_bits)
     offs, cols = g.rows(w.seed, 0, w.n_rows)
     qo, qc, _ = g.queries(w.seed, w.qseed, 2_000_000, w.n_rows, **w.query_kwargs())
@@ -702,16 +702,21 @@ def bench_serving(args, w: workloads.Workload) -> dict:
     for rate in rates:
         n_req = int(min(args.serve_seconds * rate, args.serve_max_requests))
         reqs = poisson_requests(float(rate), n_req, qo, qc, seed=rate)
-        ex = GpuExecutor(ix, topk=w.topk, slots=args.serve_slots, mode=sched["mode"], threads=sched["threads"])
-        with Clocks(0) as clk:
-            _, summ = serve(reqs, ex, topk=w.topk, slots=args.serve_slots, mem_budget=16 << 30,
-                            max_batch_queries=args.serve_max_batch)
+        with Clocks(0) as clk:  # the library's native loop
+            _, summ = serve_native(reqs, ix, topk=w.topk, slots=args.serve_slots,
+                                   max_batch_queries=args.serve_max_batch, mode=sched["mode"])
         summ["clocks"] = clk.summary()
+        ex = GpuExecutor(ix, topk=w.topk, slots=args.serve_slots, mode=sched["mode"], threads=sched["threads"])
+        with Clocks(0) as clk:  # the same stream through the Python loop, for comparison
+            _, py = serve(reqs, ex, topk=w.topk, slots=args.serve_slots, mem_budget=16 << 30,
+                          max_batch_queries=args.serve_max_batch)
+        py["clocks"] = clk.summary()
+        summ["python_loop"] = py
         per_rate[str(rate)] = summ
         log(f"[bench] serving {rate} req/s: {summ}")
     ix.close()
     top = per_rate[str(rates[-1])]
-    return {"metric": "serving p50/p99 ms and sustained queries/s (continuous batching, 8 shards)",
+    return {"metric": "serving p50/p99 ms and sustained queries/s (native continuous batching, 8 shards)",
             "value": top["queries_per_s"], "unit": "queries/s", "n_gpus": 1, "steps": len(rates),
             "warmup": 0, "ms_per_step": top["p50_ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": config_of(w, args),

@@ -1,0 +1,71 @@
+/*
+ * slash_serve.h -- C ABI of the native serving loop over a SLASH index.
+ *
+ * The paper answers query batches (Algorithm 2); serving a stream of requests
+ * has no counterpart in it.  This loop is the host runtime around that query:
+ * requests arrive in real time, are admitted in arrival order, grouped into
+ * batches of whole requests, and each batch is copied to the device, queried
+ * and copied back on one of several CUDA streams ("slots"), while the host
+ * keeps forming the next batches.  Its purpose is to keep the host cost per
+ * batch far below a batch's device time, so that the queueing delay of a
+ * request reflects the device, not the loop.
+ *
+ * Conventions are those of slash.h (return codes, h_* = caller-owned host
+ * memory).  The call runs the whole request stream and returns when every
+ * request is answered, cancelled or refused.
+ */
+#ifndef SLASH_SERVE_H
+#define SLASH_SERVE_H
+
+#include <stdint.h>
+
+#include "slash.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  uint32_t slots;              /* batches in flight at once, one CUDA stream each (1..16)           */
+  uint32_t max_batch_queries;  /* queries of one batch at most (>= 1); a request with more is      */
+                               /* refused (SLASH_EBUSY)                                           */
+  uint32_t topk;               /* k of every query (1..SLASH_MAX_TOPK)                              */
+  uint32_t mode;               /* query schedule: SLASH_QUERY_FUSED or SLASH_QUERY_WARP_FUSED (the  */
+                               /* schedules that may run on several streams at once)                */
+  uint32_t threads;            /* threads per CTA of the schedule (0 = the index's default)         */
+  uint32_t reserved;           /* must be 0                                                         */
+  double timeout_s;            /* a request still waiting for a batch this long after its arrival   */
+                               /* is cancelled (SLASH_ETIMEOUT); <= 0: no deadline                  */
+} slash_serve_opts;
+
+/* Serve n_requests requests in real time.  Request i arrives h_arrival_s[i]
+ * seconds after the call starts (non-decreasing) and carries the queries
+ * [h_req_q[i], h_req_q[i+1]) of one query CSR: query j's feature ids are
+ * h_cols[h_offs[j] .. h_offs[j+1]) (h_req_q[0] = 0; h_offs[0] need not be 0).
+ * A batch is formed, whenever a slot is free, from the waiting requests in
+ * arrival order while its queries stay within max_batch_queries.
+ *
+ * Outputs (row-major [total queries][topk], as slash_query): h_ids_out int32,
+ * h_scores_out uint32 of every query of an answered request; per request
+ * h_launched_s[i] (when its batch was issued) and h_done_s[i] (when the batch's
+ * results were back in host memory, from the slot's completion event), both in
+ * seconds since the call started (NaN if not answered), and h_status[i]: 0,
+ * SLASH_ETIMEOUT (cancelled before launch) or SLASH_EBUSY (refused).
+ *
+ * All host and device buffers are sized before the first arrival (pinned host
+ * and device buffers per slot for the largest batch the stream can form); the
+ * loop allocates nothing.  Between arrivals with nothing in flight the thread
+ * sleeps; otherwise it polls the slots' events.
+ *
+ * Errors: SLASH_EINVAL (NULL, opts out of range, decreasing arrivals or
+ * offsets), SLASH_ENOMEM (the buffers), SLASH_ECUDA; and any error a query
+ * returns, which stops the loop (requests not yet answered keep NaN times). */
+int slash_serve(slash_index *ix, const slash_serve_opts *opts, uint32_t n_requests, const double *h_arrival_s,
+                const uint64_t *h_req_q, const uint64_t *h_offs, const uint32_t *h_cols, int32_t *h_ids_out,
+                uint32_t *h_scores_out, double *h_launched_s, double *h_done_s, int32_t *h_status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLASH_SERVE_H */

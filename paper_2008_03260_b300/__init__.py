@@ -63,6 +63,12 @@ class slash_query_opts(ctypes.Structure):
         return f"slash_query_opts({m}, threads={self.threads}, ctas_per_sm={self.ctas_per_sm})"
 
 
+class slash_serve_opts(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint32), ("max_batch_queries", ctypes.c_uint32), ("topk", ctypes.c_uint32),
+                ("mode", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("timeout_s", ctypes.c_double)]
+
+
 class slash_params(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_uint32), ("K", ctypes.c_uint32), ("L", ctypes.c_uint32),
                 ("log2_buckets", ctypes.c_uint32), ("reservoir", ctypes.c_uint32),
@@ -111,6 +117,7 @@ def _load() -> ctypes.CDLL:
         "slash_query_ex": (i32, [vp, vp, vp, u32, u32, vp, vp, P(slash_query_opts), vp]),
         "slash_autotune": (i32, [vp, vp, vp, u32, u32, vp, vp, vp, P(slash_query_opts), P(ctypes.c_float)]),
         "slash_query_static": (i32, [vp, vp, vp, u32, u32, vp, vp, vp]),
+        "slash_serve": (i32, [vp, P(slash_serve_opts), u32, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         "slash_profile": (i32, [vp, i32]),
         "slash_profile_read": (i32, [vp, u32, vp, vp, vp, P(u32), P(u64)]),
         "slash_tk_build": (i32, [P(slash_tk_params), vp, P(vp)]),
@@ -273,6 +280,34 @@ def slash_autotune(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, topk: in
                                ids.data_ptr(), sc.data_ptr(), _stream(stream), ctypes.byref(best),
                                ctypes.byref(ms)), "slash_autotune")
     return best, float(ms.value)
+
+
+def slash_serve(ix: int, arrival_s, req_q, offs, cols, topk: int, *, slots: int = 4,
+                max_batch_queries: int = 8192, mode="fused", threads: int = 0, timeout_s: float = 0.0):
+    """The native serving loop (include/slash_serve.h) over host arrays:
+    arrival_s float64 [n], req_q uint64 [n+1] (request i = queries
+    [req_q[i], req_q[i+1])), the queries' CSR offs uint64 / cols uint32.
+    Returns (ids int32 [Q][topk], scores uint32 [Q][topk], launched_s, done_s,
+    status int32), one time and status per request."""
+    import numpy as np
+    arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+    rq = np.ascontiguousarray(req_q, dtype=np.uint64)
+    of = np.ascontiguousarray(offs, dtype=np.uint64)
+    co = np.ascontiguousarray(cols, dtype=np.uint32)
+    n = arr.size
+    if rq.size != n + 1:
+        raise ValueError("req_q needs n_requests + 1 entries")
+    nq = int(rq[-1]) if n else 0
+    ids = np.empty((nq, topk), dtype=np.int32)
+    sc = np.empty((nq, topk), dtype=np.uint32)
+    launched = np.empty(n, dtype=np.float64)
+    done = np.empty(n, dtype=np.float64)
+    status = np.empty(n, dtype=np.int32)
+    o = slash_serve_opts(slots, max_batch_queries, topk, _MODES.get(mode, mode), threads, 0, timeout_s)
+    ptr = lambda a: a.ctypes.data if a.size else None
+    _check(_lib.slash_serve(ix, ctypes.byref(o), n, ptr(arr), rq.ctypes.data, of.ctypes.data, ptr(co), ptr(ids),
+                            ptr(sc), ptr(launched), ptr(done), ptr(status)), "slash_serve")
+    return ids, sc, launched, done, status
 
 
 def slash_free(ix: int) -> None:
@@ -463,6 +498,9 @@ class Index:
 
     def autotune(self, d_offs, d_cols, topk: int, stream=None):
         return slash_autotune(self.h, d_offs, d_cols, topk, stream)
+
+    def serve(self, arrival_s, req_q, offs, cols, topk: int, **kw):
+        return slash_serve(self.h, arrival_s, req_q, offs, cols, topk, **kw)
 
     def sync(self, stream=None) -> None:
         _check(slash_sync(self.h, stream), "slash_sync")

@@ -15,9 +15,9 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libslash.so")
 SOURCES = [os.path.join(CSRC, "slash.cu"), os.path.join(CSRC, "slash_topkapi.cu"),
-           os.path.join(CSRC, "slash_probe.cu")]
+           os.path.join(CSRC, "slash_probe.cu"), os.path.join(CSRC, "slash_serve.cu")]
 DEPS = SOURCES + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))] + [
-    os.path.join(INCLUDE, "slash.h"), os.path.join(INCLUDE, "slash_topkapi.h")]
+    os.path.join(INCLUDE, "slash.h"), os.path.join(INCLUDE, "slash_topkapi.h"), os.path.join(INCLUDE, "slash_serve.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "-shared", "-I", INCLUDE, "-I", CSRC]

@@ -1,0 +1,203 @@
+// Native serving loop over a SLASH index (include/slash_serve.h): real-time
+// admission, batching of whole requests in arrival order, and one CUDA stream
+// per slot carrying a batch's copy in, query (Algorithm 2) and copy back.
+// Host code only; the query is the library's own slash_query_ex.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "slash.h"
+#include "slash_serve.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// Byte offset of a batch's features in the slot's input buffer: after its
+// nq + 1 offsets, rounded up to 16 bytes.
+inline size_t cols_at(uint64_t nq) { return (8u * (nq + 1u) + 15u) & ~size_t(15); }
+
+struct Slot {
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev = nullptr;
+  unsigned char* h_in = nullptr;   // page-locked: offsets, then features
+  unsigned char* d_in = nullptr;
+  unsigned char* h_out = nullptr;  // page-locked: ids [nq][k], then scores [nq][k]
+  unsigned char* d_out = nullptr;
+  bool busy = false;
+  uint32_t r0 = 0, r1 = 0;  // the batch's requests [r0, r1)
+  uint64_t q0 = 0, nq = 0;  // and its queries [q0, q0 + nq)
+};
+
+struct Slots {
+  std::vector<Slot> s;
+  cudaEvent_t ref = nullptr;
+  ~Slots() {
+    for (Slot& x : s)
+      if (x.st) cudaStreamSynchronize(x.st);
+    for (Slot& x : s) {
+      if (x.h_in) cudaFreeHost(x.h_in);
+      if (x.h_out) cudaFreeHost(x.h_out);
+      if (x.d_in) cudaFree(x.d_in);
+      if (x.d_out) cudaFree(x.d_out);
+      if (x.ev) cudaEventDestroy(x.ev);
+      if (x.st) cudaStreamDestroy(x.st);
+    }
+    if (ref) cudaEventDestroy(ref);
+  }
+};
+
+}  // namespace
+
+extern "C" int slash_serve(slash_index* ix, const slash_serve_opts* o, uint32_t n, const double* arrival,
+                           const uint64_t* req_q, const uint64_t* offs, const uint32_t* cols, int32_t* ids_out,
+                           uint32_t* scores_out, double* launched_s, double* done_s, int32_t* status) {
+  if (!ix || !o) return SLASH_EINVAL;
+  if (o->slots < 1u || o->slots > 16u || o->max_batch_queries < 1u || o->topk < 1u || o->topk > SLASH_MAX_TOPK ||
+      (o->mode != SLASH_QUERY_FUSED && o->mode != SLASH_QUERY_WARP_FUSED) || o->reserved != 0u)
+    return SLASH_EINVAL;
+  if (n == 0u) return SLASH_OK;
+  if (!arrival || !req_q || !offs || !ids_out || !scores_out || !launched_s || !done_s || !status)
+    return SLASH_EINVAL;
+  if (req_q[0] != 0u) return SLASH_EINVAL;
+  for (uint32_t i = 0; i < n; ++i) {
+    if (req_q[i + 1] < req_q[i] || !(arrival[i] >= 0.0) || (i && arrival[i] < arrival[i - 1])) return SLASH_EINVAL;
+  }
+  const uint64_t total_q = req_q[n];
+  for (uint64_t j = 0; j < total_q; ++j)
+    if (offs[j + 1] < offs[j]) return SLASH_EINVAL;
+  if (offs[total_q] > offs[0] && !cols) return SLASH_EINVAL;
+  const uint64_t cap = o->max_batch_queries, k = o->topk;
+  auto req_nq = [&](uint32_t i) { return req_q[i + 1] - req_q[i]; };
+  auto nnz_of = [&](uint64_t q0, uint64_t q1) { return offs[q1] - offs[q0]; };
+
+  // The largest batch the stream can form: a run of consecutive admitted
+  // requests (a refused one ends a run) of at most `cap` queries.
+  uint64_t most_q = 0, most_nnz = 0;
+  for (uint32_t i = 0, j = 0; i < n; ++i) {
+    if (req_nq(i) > cap) { j = i + 1; continue; }
+    if (j < i + 1) j = i + 1;
+    while (j < n && req_nq(j) <= cap && req_q[j + 1] - req_q[i] <= cap) ++j;
+    most_q = std::max(most_q, req_q[j] - req_q[i]);
+    most_nnz = std::max(most_nnz, nnz_of(req_q[i], req_q[j]));
+  }
+  const size_t in_bytes = cols_at(most_q) + 4u * std::max<uint64_t>(most_nnz, 1u);
+  const size_t out_bytes = 8u * std::max<uint64_t>(most_q, 1u) * k;
+
+  Slots sl;
+  sl.s.resize(o->slots);
+  for (Slot& x : sl.s) {
+    if (cudaStreamCreateWithFlags(&x.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&x.ev) != cudaSuccess) {
+      cudaGetLastError();
+      return SLASH_ECUDA;
+    }
+    if (cudaMallocHost(reinterpret_cast<void**>(&x.h_in), in_bytes) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&x.h_out), out_bytes) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&x.d_in), in_bytes) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&x.d_out), out_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return SLASH_ENOMEM;
+    }
+  }
+  if (cudaEventCreate(&sl.ref) != cudaSuccess) return SLASH_ECUDA;
+  for (uint32_t i = 0; i < n; ++i) {
+    launched_s[i] = done_s[i] = NAN;
+    status[i] = 0;
+  }
+  const slash_query_opts qo{o->mode, o->threads, 0u};
+
+  // time zero: a reference event on the GPU's clock, then the host's
+  if (cudaEventRecord(sl.ref, sl.s[0].st) != cudaSuccess || cudaEventSynchronize(sl.ref) != cudaSuccess)
+    return SLASH_ECUDA;
+  const Clock::time_point t0 = Clock::now();
+  auto now_s = [&]() { return std::chrono::duration<double>(Clock::now() - t0).count(); };
+
+  uint32_t next = 0;  // requests [0, next) have arrived
+  uint32_t head = 0;  // requests [head, next) wait for a batch
+  for (;;) {
+    const double now = now_s();
+    while (next < n && arrival[next] <= now) ++next;
+    bool busy = false;
+    for (Slot& x : sl.s) {  // batches that are back
+      if (!x.busy) continue;
+      const cudaError_t e = cudaEventQuery(x.ev);
+      if (e == cudaErrorNotReady) {
+        busy = true;
+        continue;
+      }
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SLASH_ECUDA;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, sl.ref, x.ev);
+      std::memcpy(ids_out + x.q0 * k, x.h_out, 4u * x.nq * k);
+      std::memcpy(scores_out + x.q0 * k, x.h_out + 4u * x.nq * k, 4u * x.nq * k);
+      for (uint32_t r = x.r0; r < x.r1; ++r) done_s[r] = 1e-3 * ms;
+      x.busy = false;
+    }
+    // the head of the queue: refused (too large for any batch) or past its deadline
+    while (head < next) {
+      if (req_nq(head) > cap) status[head] = SLASH_EBUSY;
+      else if (o->timeout_s > 0.0 && now - arrival[head] > o->timeout_s) status[head] = SLASH_ETIMEOUT;
+      else break;
+      ++head;
+    }
+    for (Slot& x : sl.s) {  // a batch for every free slot while requests wait
+      if (x.busy || head >= next) continue;
+      uint32_t r1 = head;
+      while (r1 < next && req_nq(r1) <= cap && req_q[r1 + 1] - req_q[head] <= cap &&
+             !(o->timeout_s > 0.0 && now - arrival[r1] > o->timeout_s))
+        ++r1;
+      const uint64_t q0 = req_q[head], nq = req_q[r1] - q0;
+      for (uint32_t r = head; r < r1; ++r) launched_s[r] = now;
+      if (nq == 0u) {  // requests without queries are answered at once
+        for (uint32_t r = head; r < r1; ++r) done_s[r] = now;
+        head = r1;
+        continue;
+      }
+      const uint64_t base = offs[q0], nnz = offs[q0 + nq] - base;
+      uint64_t* ho = reinterpret_cast<uint64_t*>(x.h_in);
+      for (uint64_t j = 0; j <= nq; ++j) ho[j] = offs[q0 + j] - base;
+      const size_t c0 = cols_at(nq);
+      if (nnz) std::memcpy(x.h_in + c0, cols + base, 4u * nnz);
+      const uint64_t ob = 4u * nq * k;
+      if (cudaMemcpyAsync(x.d_in, x.h_in, c0 + 4u * nnz, cudaMemcpyHostToDevice, x.st) != cudaSuccess) {
+        cudaGetLastError();
+        return SLASH_ECUDA;
+      }
+      const int rc = slash_query_ex(ix, reinterpret_cast<const uint64_t*>(x.d_in),
+                                    reinterpret_cast<const uint32_t*>(x.d_in + c0), (uint32_t)nq, (uint32_t)k,
+                                    reinterpret_cast<int32_t*>(x.d_out), reinterpret_cast<uint32_t*>(x.d_out + ob),
+                                    &qo, x.st);
+      if (rc != SLASH_OK) return rc;
+      if (cudaMemcpyAsync(x.h_out, x.d_out, 2u * ob, cudaMemcpyDeviceToHost, x.st) != cudaSuccess ||
+          cudaEventRecord(x.ev, x.st) != cudaSuccess) {
+        cudaGetLastError();
+        return SLASH_ECUDA;
+      }
+      x.busy = true;
+      x.r0 = head;
+      x.r1 = r1;
+      x.q0 = q0;
+      x.nq = nq;
+      busy = true;
+      head = r1;
+    }
+    if (!busy && head >= n) break;
+    if (!busy && head >= next && next < n) {  // idle until the next arrival
+      const double wait = arrival[next] - now_s();
+      if (wait > 2e-4) std::this_thread::sleep_for(std::chrono::duration<double>(wait - 1e-4));
+    } else {
+      std::this_thread::yield();
+    }
+  }
+  return SLASH_OK;
+}

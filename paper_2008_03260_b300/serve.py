@@ -249,6 +249,58 @@ class GpuExecutor:
         return ids, sc, t_done
 
 
+def summarize(requests: list[Request], res: dict, n_batches: int) -> dict:
+    """Latency percentiles and throughput of a served request stream."""
+    done = [r for r in res.values() if r.status == 0]
+    lat = np.array([r.latency for r in done]) if done else np.zeros(1)
+    nq = sum(q.nq for q in requests if res[q.rid].status == 0)
+    span = max(r.done for r in done) - min(r.arrival for r in done) if done else 1.0
+    p99 = float(np.percentile(lat, 99))
+    size = {q.rid: q.nq for q in requests}
+    small = np.array([r.latency for r in done if size[r.rid] <= 64])
+    tail = [r for r in done if r.latency >= p99] or done
+    return {"requests": len(done),
+            "refused": sum(1 for r in res.values() if r.status == SLASH_EBUSY),
+            "cancelled": sum(1 for r in res.values() if r.status == SLASH_ETIMEOUT),
+            "queries": nq, "batches": n_batches,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * p99,
+            "mean_ms": 1e3 * float(lat.mean()), "queries_per_s": nq / span if span > 0 else float("nan"),
+            "span_s": span,
+            # where the slowest 1% spent their time: queued on the host before
+            # launch, and from launch to completion on the device
+            "p99_queued_ms": 1e3 * float(np.mean([r.launched - r.arrival for r in tail])) if tail else 0.0,
+            "p99_device_ms": 1e3 * float(np.mean([r.done - r.launched for r in tail])) if tail else 0.0,
+            # the tail of small requests alone (sizes are log-uniform: the slowest 1%
+            # overall are mostly the largest requests)
+            "p50_small_ms": 1e3 * float(np.percentile(small, 50)) if len(small) else 0.0,
+            "p99_small_ms": 1e3 * float(np.percentile(small, 99)) if len(small) else 0.0}
+
+
+def serve_native(requests: list[Request], ix, *, topk: int, slots: int = 4, max_batch_queries: int = 8192,
+                 mode: str = "fused", threads: int = 0, timeout_s: float = 0.0) -> tuple[list[Result], dict]:
+    """The same request stream through the library's native loop (slash_serve):
+    admission, batching and the slots' streams run in C++; this function only
+    lays the requests out as arrays and reads the answers back."""
+    reqs = sorted(requests, key=lambda r: r.arrival)
+    arrival = np.array([r.arrival for r in reqs], dtype=np.float64)
+    req_q = np.zeros(len(reqs) + 1, dtype=np.uint64)
+    np.cumsum([r.nq for r in reqs], out=req_q[1:])
+    offs, cols = concat_csr(reqs)
+    ids, sc, launched, done, status = ix.serve(arrival, req_q, offs, cols, topk, slots=slots,
+                                               max_batch_queries=max_batch_queries, mode=mode, threads=threads,
+                                               timeout_s=timeout_s)
+    res = {}
+    for i, r in enumerate(reqs):
+        q0, q1 = int(req_q[i]), int(req_q[i + 1])
+        rr = Result(r.rid, r.arrival, float(launched[i]), float(done[i]), status=int(status[i]))
+        if rr.status == 0:
+            rr.ids, rr.scores = ids[q0:q1], sc[q0:q1]
+        res[r.rid] = rr
+    # batches issued at distinct instants (batches formed in the same pass of the loop count once)
+    n_batches = len({float(t) for t, st in zip(launched, status) if st == 0})
+    return list(res.values()), summarize(reqs, res, n_batches)
+
+
 def serve(requests: list[Request], executor, *, topk: int, slots: int = 4, mem_budget: int = 16 << 30,
           max_batch_queries: int = 1 << 16, realtime: bool = True) -> tuple[list[Result], dict]:
     """Run the request stream through the executor; returns per-request results and a summary."""
@@ -296,31 +348,10 @@ def serve(requests: list[Request], executor, *, topk: int, slots: int = 4, mem_b
                 time.sleep(wait - 1e-4)
     for r in bat.refused:
         res[r.rid].status = SLASH_EBUSY
-    done = [r for r in res.values() if r.status == 0]
-    lat = np.array([r.latency for r in done]) if done else np.zeros(1)
-    nq = sum(q.nq for q in requests if res[q.rid].status == 0)
-    span = max(r.done for r in done) - min(r.arrival for r in done) if done else 1.0
-    p99 = float(np.percentile(lat, 99))
-    size = {q.rid: q.nq for q in requests}
-    small = np.array([r.latency for r in done if size[r.rid] <= 64])
-    tail = [r for r in done if r.latency >= p99] or done
-    summary = {"requests": len(done), "refused": len(bat.refused),
-               "cancelled": sum(1 for r in res.values() if r.status == SLASH_ETIMEOUT),
-               "queries": nq, "batches": n_batches,
-               "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * p99,
-               "mean_ms": 1e3 * float(lat.mean()), "queries_per_s": nq / span if span > 0 else float("nan"),
-               "span_s": span,
-               # where the slowest 1% spent their time: queued on the host before
-               # launch, and from launch to completion on the device
-               "p99_queued_ms": 1e3 * float(np.mean([r.launched - r.arrival for r in tail])) if tail else 0.0,
-               "p99_device_ms": 1e3 * float(np.mean([r.done - r.launched for r in tail])) if tail else 0.0,
-               # the tail of small requests alone (sizes are log-uniform: the slowest 1%
-               # overall are mostly the largest requests)
-               "p50_small_ms": 1e3 * float(np.percentile(small, 50)) if len(small) else 0.0,
-               "p99_small_ms": 1e3 * float(np.percentile(small, 99)) if len(small) else 0.0,
-               # host cost per batch of the loop's two calls into the executor
-               "host_launch_us_per_batch": 1e6 * t_launch / max(1, n_batches),
-               "host_collect_us_per_batch": 1e6 * t_collect / max(1, n_batches)}
+    summary = summarize(requests, res, n_batches)
+    # host cost per batch of the loop's two calls into the executor
+    summary["host_launch_us_per_batch"] = 1e6 * t_launch / max(1, n_batches)
+    summary["host_collect_us_per_batch"] = 1e6 * t_collect / max(1, n_batches)
     return list(res.values()), summary
 
 

@@ -1,5 +1,6 @@
 """Serving loop: admission/batching host logic on CPU (fake executor), and the
 GPU loop's results equal to each request answered alone (tolerance zero)."""
+import dataclasses
 import time
 
 import numpy as np
@@ -148,3 +149,81 @@ def test_queued_requests_past_their_deadline_are_cancelled():
     assert all(by[i].status == 0 for i in range(12) if i not in late)
     assert summ["cancelled"] == len(late) and summ["requests"] == 12 - len(late)
     assert summ["p99_queued_ms"] >= 0 and summ["p99_device_ms"] >= 0
+
+
+def test_native_serve_validates_before_touching_the_gpu():
+    """slash_serve checks its options and arrays before any CUDA call (the
+    index handle is never dereferenced on these paths)."""
+    import ctypes
+
+    import paper_2008_03260_b300 as s
+    fake = ctypes.c_void_p(1)
+    arr = np.array([0.0, 0.1], dtype=np.float64)
+    rq = np.array([0, 1, 2], dtype=np.uint64)
+    offs = np.array([0, 2, 3], dtype=np.uint64)
+    cols = np.array([1, 2, 3], dtype=np.uint32)
+    out = [np.empty(20, np.int32), np.empty(20, np.uint32), np.empty(2), np.empty(2), np.empty(2, np.int32)]
+
+    def call(o, arrival=arr, req_q=rq, offsets=offs, n=2):
+        return s._lib.slash_serve(fake, ctypes.byref(o), n, arrival.ctypes.data, req_q.ctypes.data,
+                                  offsets.ctypes.data, cols.ctypes.data, *[a.ctypes.data for a in out])
+
+    ok = dict(slots=2, max_batch_queries=8, topk=10, mode=s.SLASH_QUERY_FUSED, threads=0, reserved=0,
+              timeout_s=0.0)
+    for bad in (dict(slots=0), dict(slots=17), dict(max_batch_queries=0), dict(topk=0), dict(topk=257),
+                dict(mode=s.SLASH_QUERY_PLAIN), dict(mode=s.SLASH_QUERY_WARP_PLAIN), dict(reserved=1)):
+        assert call(s.slash_serve_opts(**{**ok, **bad})) == s.SLASH_EINVAL, bad
+    o = s.slash_serve_opts(**ok)
+    assert call(o, arrival=np.array([0.2, 0.1])) == s.SLASH_EINVAL            # arrivals go back in time
+    assert call(o, arrival=np.array([-1.0, 0.1])) == s.SLASH_EINVAL
+    assert call(o, req_q=np.array([1, 1, 2], dtype=np.uint64)) == s.SLASH_EINVAL  # must start at query 0
+    assert call(o, req_q=np.array([0, 2, 1], dtype=np.uint64)) == s.SLASH_EINVAL
+    assert call(o, offsets=np.array([0, 3, 2], dtype=np.uint64)) == s.SLASH_EINVAL
+    assert call(o, n=0) == s.SLASH_OK                                             # nothing to serve
+
+
+@pytest.mark.gpu
+def test_native_serving_equals_oracle_refuses_and_cancels():
+    """The native loop's answers equal the oracle's for every answered request;
+    requests larger than a batch are refused; a deadline that has always passed
+    cancels every request."""
+    import torch
+
+    import oracle
+    import paper_2008_03260_b300 as s
+    from paper_2008_03260_b300.serve import SLASH_EBUSY, SLASH_ETIMEOUT, poisson_requests, serve_native
+    g = datagen.Generator()
+    n = 30_000
+    offs, cols = g.rows(0, 0, n)
+    qo, qc, _ = g.queries(0, 3, 20_000, n, planted_frac=0.3, p_perturb=0.2)
+    p = s.Params(K=4, L=16, log2_buckets=12, reservoir=32, cm_rows=4, cm_width=8192, shards=8, capacity=n)
+    dev = lambda a: torch.from_numpy(a.view(np.int64 if a.dtype == np.uint64 else np.int32)).cuda()
+    oix = oracle.Index(K=4, L=16, log2_buckets=12, reservoir=32, cm_rows=4, cm_width=8192, shards=8,
+                       capacity=n)
+    oix.insert(offs, cols)
+    with s.Index(p) as ix:
+        ix.insert(dev(offs), dev(cols))
+        ix.sync()
+        reqs = poisson_requests(50_000.0, 400, qo, qc, seed=7, max_size=512)
+        want = {q.rid: oix.query(q.offs, q.cols, 10) for q in reqs if q.nq <= 300}
+        for mode in ("fused", "warp_fused"):
+            res, summ = serve_native(reqs, ix, topk=10, slots=4, max_batch_queries=300, mode=mode)
+            by = {r.rid: r for r in res}
+            big = [q for q in reqs if q.nq > 300]
+            assert big and all(by[q.rid].status == SLASH_EBUSY for q in big)
+            assert summ["refused"] == len(big) and summ["requests"] == len(reqs) - len(big)
+            for q in reqs:
+                r = by[q.rid]
+                if q.nq > 300:
+                    continue
+                assert r.status == 0 and r.arrival <= r.launched <= r.done
+                want_ids, want_sc = want[q.rid]
+                assert np.array_equal(r.ids, want_ids), (mode, q.rid)
+                assert np.array_equal(r.scores, want_sc), (mode, q.rid)
+        # every request arrives at time 0 and may wait 1 ns: by the loop's first look
+        # (tens of ns after its start) every deadline has passed
+        at0 = [dataclasses.replace(q, arrival=0.0) for q in reqs]
+        res, summ = serve_native(at0, ix, topk=10, slots=2, max_batch_queries=4096, timeout_s=1e-9)
+        assert all(r.status == SLASH_ETIMEOUT and r.ids is None for r in res)
+        assert summ["cancelled"] == len(reqs)
+        ix.sync()
