@@ -170,15 +170,14 @@ int slash_autotune(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_co
 
 /* Allocation-free query (this entry point has no counterpart in the paper).
  * Same results and errors as slash_query_ex with {SLASH_QUERY_PLAIN, 512, 0},
- * for callers that cannot call cudaMalloc at query time -- code running while
- * a CUDA graph is being captured (allocation is not a capturable operation)
- * and hosts that hand out all device memory from their own pool at start-up.
+ * for callers that cannot call cudaMalloc at query time, such as hosts that
+ * hand out all device memory from their own pool at start-up.
  * Its only scratch, the batch's table addresses, lives in a fixed 16 MiB
  * array inside the library's device image (held by every GPU that loads the
  * library, until the process exits), so n_queries * L must be <= 4194304
  * (else SLASH_EINVAL, nothing launched).  The index's device must be current
  * (else SLASH_EINVAL).  The first call on a device looks up the array's device
- * address (no allocation); make that first call before any stream capture.
+ * address (no allocation).
  * Every call shares the array and nothing in it needs clearing: calls whose
  * work overlaps on the GPU (other streams, or without ordering) race on it. */
 int slash_query_static(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n_queries,

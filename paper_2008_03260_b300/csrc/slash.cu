@@ -2571,7 +2571,7 @@ int insert_tail(slash_index* ix, uint32_t n, uint64_t id0, cudaStream_t st) {
 }
 
 // Resident CTAs per SM of a query kernel, looked up once per index and schedule
-// (later calls, e.g. under stream capture, make no occupancy query).
+// (later calls make no occupancy query).
 int cached_bps(int& cached, const void* fn, uint32_t thr, size_t smem, int* out) {
   if (cached == 0) {
     int b = 0;
@@ -3032,7 +3032,7 @@ int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
     fn = thr == 256 ? (const void*)k_query_fused<256>
                     : thr == 512 ? (const void*)k_query_fused<512> : (const void*)k_query_fused<1024>;
   // resident CTAs per SM for this schedule, looked up once per index (so that
-  // later calls, e.g. under stream capture, make no occupancy query)
+  // later calls make no occupancy query)
   const int ti = thr == 256 ? 0 : thr == 512 ? 1 : 2;
   int bps = 0;
   SLASH_CK_RC(cached_bps(ix->qbps[o.mode == SLASH_QUERY_PLAIN ? 1 : 0][ti], fn, thr, lay.bytes, &bps));
@@ -3319,10 +3319,9 @@ int slash_debug_buckets(slash_index* ix, const uint32_t* h_shard, const uint32_t
 // slash_query_static: the plain query path (k_hash, then k_query) with its one
 // piece of scratch -- the queries' table addresses -- in a fixed array that is
 // part of this library's device image, so the call never allocates.  For
-// callers that cannot call cudaMalloc: code running while a CUDA graph is being
-// captured (allocation is not a capturable operation), and hosts whose device
-// memory is handed out once at start-up by their own pool, where a later
-// allocation would fail or stall the process.
+// callers that cannot call cudaMalloc, such as hosts whose device memory is
+// handed out once at start-up by their own pool, where a later allocation would
+// fail or stall the process.
 namespace {
 
 constexpr uint64_t kStaticQbktWords = 1ull << 22;  // 16 MiB: n_queries * L per call, at most

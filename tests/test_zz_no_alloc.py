@@ -1,7 +1,7 @@
 """The allocation-free query entry point (collected last on purpose).
 
 slash_query_static serves callers that cannot allocate device memory when they
-query (CUDA graph capture, pre-sized memory pools): its scratch is a fixed
+query (hosts with pre-sized memory pools): its scratch is a fixed
 array inside the library.  Called through the C ABI, it must give exactly the
 plain query path's results, on consecutive calls that reuse that array.
 """
