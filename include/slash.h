@@ -41,6 +41,7 @@
 #ifndef SLASH_H
 #define SLASH_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -225,6 +226,26 @@ int slash_query_cells(slash_index *ix, const uint64_t *d_offs, const uint32_t *d
 int slash_rank_candidates(uint32_t world, uint32_t n_queries, uint32_t m, uint32_t d, const int32_t *d_counts,
                           const int32_t *d_ids, const uint32_t *d_cells, uint32_t topk, int32_t *d_ids_out,
                           uint32_t *d_scores_out, void *cuda_stream);
+
+/* Allocator hook (no counterpart in the paper): the index's workspace -- the
+ * insert buffers (addresses, staged ids, merge lists), the plain-query
+ * addresses and the host-fed insert's device staging -- comes from
+ * alloc(bytes, ctx), which returns device memory on the index's device (at
+ * least 256-byte aligned) or NULL when it has none, and goes back through
+ * release(ptr, ctx).  Lets a host's caching allocator (for example PyTorch's)
+ * supply and account that memory.  The index's own arrays (buckets, fills,
+ * counters) stay where slash_build_index put them.  Workspace is taken when a
+ * call first needs it or needs more, and released when it grows, when the
+ * allocator changes and at slash_free; before each release the library waits
+ * for the device, so released memory is idle.  alloc = release = NULL restores
+ * cudaMalloc/cudaFree.  A NULL from alloc makes the call that needed the
+ * memory return SLASH_ENOMEM with the index unchanged.  Setting it releases
+ * the current workspace with the allocator that made it.  Synchronises the
+ * device.  Errors: SLASH_EINVAL (NULL index, or only one of alloc / release),
+ * SLASH_ECUDA. */
+typedef void *(*slash_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*slash_free_fn)(void *ptr, void *ctx);
+int slash_set_allocator(slash_index *ix, slash_alloc_fn alloc, slash_free_fn release, void *ctx);
 
 /* Checkpoint (no counterpart in the paper, whose index lives only for one run):
  * write the whole index state -- parameters, the next id, fill counts and

@@ -63,6 +63,11 @@ class slash_query_opts(ctypes.Structure):
         return f"slash_query_opts({m}, threads={self.threads}, ctas_per_sm={self.ctas_per_sm})"
 
 
+# the allocator hook's callback types (include/slash.h)
+SLASH_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+SLASH_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class slash_serve_opts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_uint32), ("max_batch_queries", ctypes.c_uint32), ("topk", ctypes.c_uint32),
                 ("mode", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
@@ -118,6 +123,7 @@ def _load() -> ctypes.CDLL:
         "slash_autotune": (i32, [vp, vp, vp, u32, u32, vp, vp, vp, P(slash_query_opts), P(ctypes.c_float)]),
         "slash_query_static": (i32, [vp, vp, vp, u32, u32, vp, vp, vp]),
         "slash_serve": (i32, [vp, P(slash_serve_opts), u32, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "slash_set_allocator": (i32, [vp, SLASH_ALLOC_FN, SLASH_FREE_FN, vp]),
         "slash_profile": (i32, [vp, i32]),
         "slash_profile_read": (i32, [vp, u32, vp, vp, vp, P(u32), P(u64)]),
         "slash_tk_build": (i32, [P(slash_tk_params), vp, P(vp)]),
@@ -308,6 +314,37 @@ def slash_serve(ix: int, arrival_s, req_q, offs, cols, topk: int, *, slots: int 
     _check(_lib.slash_serve(ix, ctypes.byref(o), n, ptr(arr), rq.ctypes.data, of.ctypes.data, ptr(co), ptr(ids),
                             ptr(sc), ptr(launched), ptr(done), ptr(status)), "slash_serve")
     return ids, sc, launched, done, status
+
+
+def slash_set_allocator(ix: int, alloc=None, release=None) -> None:
+    """Route the index's workspace through alloc(bytes) -> device pointer (0 or
+    None when out of memory) and release(ptr); both None restores cudaMalloc.
+    Keep the returned callback objects alive as long as the index uses them."""
+    if (alloc is None) != (release is None):
+        raise ValueError("give both alloc and release, or neither")
+    if alloc is None:
+        _check(_lib.slash_set_allocator(ix, SLASH_ALLOC_FN(), SLASH_FREE_FN(), None), "slash_set_allocator")
+        return None
+
+    def _a(n, ctx):
+        try:
+            return alloc(int(n)) or None
+        except Exception:  # an exception cannot cross the C boundary: report no memory
+            return None
+
+    def _f(ptr, ctx):
+        release(int(ptr))
+
+    cbs = (SLASH_ALLOC_FN(_a), SLASH_FREE_FN(_f))
+    _check(_lib.slash_set_allocator(ix, cbs[0], cbs[1], None), "slash_set_allocator")
+    return cbs
+
+
+def torch_allocator():
+    """(alloc, release) over PyTorch's caching allocator on the current device
+    and stream, for slash_set_allocator / Index.set_allocator."""
+    import torch
+    return (lambda n: torch.cuda.caching_allocator_alloc(n), lambda p: torch.cuda.caching_allocator_delete(p))
 
 
 def slash_free(ix: int) -> None:
@@ -527,10 +564,16 @@ class Index:
     def profile_read(self) -> tuple[dict, int]:
         return slash_profile_read(self.h)
 
+    def set_allocator(self, alloc=None, release=None) -> None:
+        """The index's workspace from alloc / release (see slash_set_allocator);
+        Index.set_allocator(*torch_allocator()) uses PyTorch's caching allocator."""
+        self._alloc_cbs = slash_set_allocator(self.h, alloc, release)
+
     def close(self) -> None:
         h, self.h = self.h, None
         if h:
             slash_free(h)
+        self._alloc_cbs = None
 
     def __enter__(self):
         return self

@@ -2283,6 +2283,10 @@ struct slash_index {
   uint64_t* h2d_offs[2] = {nullptr, nullptr};
   uint32_t* h2d_cols[2] = {nullptr, nullptr};
   uint64_t h2d_rows = 0, h2d_nnz = 0;
+  // the caller's allocator for the workspace (slash_set_allocator); null = cudaMalloc
+  slash_alloc_fn alloc_fn = nullptr;
+  slash_free_fn free_fn = nullptr;
+  void* alloc_ctx = nullptr;
   // query workspace (grow-only)
   uint64_t qws = 0;
   uint32_t* qbkt = nullptr;
@@ -2372,7 +2376,41 @@ cudaError_t ws_malloc(slash_index* ix, void** p, size_t bytes) {
     *p = nullptr;
     return cudaErrorMemoryAllocation;
   }
+  if (ix->alloc_fn) {
+    *p = ix->alloc_fn(bytes, ix->alloc_ctx);
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+  }
   return cudaMalloc(p, bytes);
+}
+
+// Workspace release.  cudaFree waits for the device; a caller's allocator may
+// hand the memory out again at once, so the device is drained first (workspace
+// is released only when it grows, when the allocator changes, and at slash_free).
+void ws_free(slash_index* ix, void* p) {
+  if (!p) return;
+  if (ix->free_fn) {
+    cudaDeviceSynchronize();
+    ix->free_fn(p, ix->alloc_ctx);
+  } else {
+    cudaFree(p);
+  }
+}
+
+// All workspace back to its allocator; the sizes start again from zero.
+void ws_release_all(slash_index* ix) {
+  ws_free(ix, ix->bkt); ws_free(ix, ix->stage); ws_free(ix, ix->big);
+  ws_free(ix, ix->fb); ws_free(ix, ix->fboff); ws_free(ix, ix->fbcur);
+  ix->bkt = ix->stage = ix->big = ix->fb = ix->fboff = ix->fbcur = nullptr;
+  ix->ws_rows = 0;
+  ix->big_cap = ix->fb_cap = 0;
+  ws_free(ix, ix->qbkt);
+  ix->qbkt = nullptr;
+  ix->qws = 0;
+  for (int i = 0; i < 2; ++i) {
+    ws_free(ix, ix->h2d_offs[i]); ws_free(ix, ix->h2d_cols[i]);
+    ix->h2d_offs[i] = nullptr; ix->h2d_cols[i] = nullptr;
+  }
+  ix->h2d_rows = ix->h2d_nnz = 0;
 }
 
 uint64_t insert_chunk_rows(const slash_index* ix) {
@@ -2403,11 +2441,11 @@ int grow_insert_ws(slash_index* ix, uint64_t rows) {
   if (e == cudaSuccess) e = ws_malloc(ix, (void**)&fbcur, sizeof(uint32_t) * fb_cap);
   if (e != cudaSuccess) {
     cudaGetLastError();
-    cudaFree(bkt); cudaFree(stage); cudaFree(big); cudaFree(fb); cudaFree(fboff); cudaFree(fbcur);
+    ws_free(ix, bkt); ws_free(ix, stage); ws_free(ix, big); ws_free(ix, fb); ws_free(ix, fboff); ws_free(ix, fbcur);
     return SLASH_ENOMEM;
   }
-  cudaFree(ix->bkt); cudaFree(ix->stage); cudaFree(ix->big); cudaFree(ix->fb); cudaFree(ix->fboff);
-  cudaFree(ix->fbcur);
+  ws_free(ix, ix->bkt); ws_free(ix, ix->stage); ws_free(ix, ix->big); ws_free(ix, ix->fb); ws_free(ix, ix->fboff);
+  ws_free(ix, ix->fbcur);
   ix->bkt = bkt; ix->stage = stage; ix->big = big; ix->fb = fb; ix->fboff = fboff; ix->fbcur = fbcur;
   ix->big_cap = big_cap;
   ix->fb_cap = fb_cap;
@@ -2419,7 +2457,7 @@ int grow_query_ws(slash_index* ix, uint64_t nq) {
   if (nq <= ix->qws) return SLASH_OK;
   uint32_t* q = nullptr;
   if (ws_malloc(ix, (void**)&q, sizeof(uint32_t) * ix->p.L * nq) != cudaSuccess) { cudaGetLastError(); return SLASH_ENOMEM; }
-  cudaFree(ix->qbkt);
+  ws_free(ix, ix->qbkt);
   ix->qbkt = q;
   ix->qws = nq;
   return SLASH_OK;
@@ -2922,7 +2960,7 @@ int slash_insert_host(slash_index* ix, const uint64_t* h_offs, const uint32_t* h
     SLASH_CK(cudaStreamSynchronize(st));
     SLASH_CK(cudaStreamSynchronize(ix->copy_st));
     for (int i = 0; i < 2; ++i) {
-      cudaFree(ix->h2d_offs[i]); cudaFree(ix->h2d_cols[i]);
+      ws_free(ix, ix->h2d_offs[i]); ws_free(ix, ix->h2d_cols[i]);
       ix->h2d_offs[i] = nullptr; ix->h2d_cols[i] = nullptr;
     }
     ix->h2d_rows = ix->h2d_nnz = 0;
@@ -3124,13 +3162,13 @@ int slash_autotune(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
 int slash_free(slash_index* ix) {
   if (!ix) return SLASH_OK;
   cudaDeviceSynchronize();
+  ws_release_all(ix);
   cudaFree(ix->slots); cudaFree(ix->fill); cudaFree(ix->err);
-  cudaFree(ix->bkt); cudaFree(ix->stage); cudaFree(ix->cnt);
-  cudaFree(ix->blocksum); cudaFree(ix->meta); cudaFree(ix->big);
-  cudaFree(ix->fb); cudaFree(ix->fboff); cudaFree(ix->fbcur); cudaFree(ix->ctr); cudaFree(ix->qbkt);
+  cudaFree(ix->cnt);
+  cudaFree(ix->blocksum); cudaFree(ix->meta);
+  cudaFree(ix->ctr);
   cudaFree(ix->work);
   for (int i = 0; i < 2; ++i) {
-    cudaFree(ix->h2d_offs[i]); cudaFree(ix->h2d_cols[i]);
     if (ix->ev_copied[i]) cudaEventDestroy(ix->ev_copied[i]);
     if (ix->ev_free[i]) cudaEventDestroy(ix->ev_free[i]);
   }
@@ -3139,6 +3177,16 @@ int slash_free(slash_index* ix) {
   for (auto e : ix->prof_pool) cudaEventDestroy(e);
   delete ix;
   return cudaGetLastError() == cudaSuccess ? SLASH_OK : SLASH_ECUDA;
+}
+
+int slash_set_allocator(slash_index* ix, slash_alloc_fn alloc, slash_free_fn release, void* ctx) {
+  if (!ix || (alloc == nullptr) != (release == nullptr)) return SLASH_EINVAL;
+  SLASH_CK(cudaDeviceSynchronize());
+  ws_release_all(ix);  // with the allocator that made it
+  ix->alloc_fn = alloc;
+  ix->free_fn = release;
+  ix->alloc_ctx = ctx;
+  return SLASH_OK;
 }
 
 int slash_sync(slash_index* ix, void* cuda_stream) {

@@ -70,3 +70,15 @@ def test_checkpoint_file_errors_without_gpu(tmp_path):
     assert lib.slash_load(str(junk).encode(), None, ctypes.byref(out)) == -1   # SLASH_EINVAL
     assert lib.slash_tk_load(str(junk).encode(), None, ctypes.byref(out)) == -1
     assert out.value is None
+
+
+def test_set_allocator_validates_without_gpu():
+    import ctypes
+
+    import paper_2008_03260_b300 as s
+    none_a, none_f = s.SLASH_ALLOC_FN(), s.SLASH_FREE_FN()
+    assert s._lib.slash_set_allocator(None, none_a, none_f, None) == s.SLASH_EINVAL      # no index
+    only_alloc = s.SLASH_ALLOC_FN(lambda n, c: None)
+    assert s._lib.slash_set_allocator(ctypes.c_void_p(1), only_alloc, none_f, None) == s.SLASH_EINVAL
+    only_free = s.SLASH_FREE_FN(lambda p, c: None)
+    assert s._lib.slash_set_allocator(ctypes.c_void_p(1), none_a, only_free, None) == s.SLASH_EINVAL
