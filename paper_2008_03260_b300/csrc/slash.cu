@@ -52,6 +52,7 @@
 #include <atomic>
 #include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include <nvtx3/nvToolsExt.h>
@@ -2251,6 +2252,13 @@ int launch_hash(const Geo& g, const ShardMap& sm, const uint64_t* offs, const ui
 
 }  // namespace slash
 
+// Host-fed insert: pieces of at most kH2dPiece rows are copied into a ring of
+// kH2dSlots device staging slots; the copy stream runs up to kH2dSlots pieces
+// ahead of the hashing, so it keeps copying while a chunk's tail (plan, scan,
+// scatter, merges) runs.
+constexpr int kH2dSlots = 4;
+constexpr uint64_t kH2dPiece = 1ull << 21;
+
 struct slash_index {
   slash_params p{};
   Geo geo{};
@@ -2277,11 +2285,11 @@ struct slash_index {
   uint32_t* ctr = nullptr;       // [0] big entries, [1] fallback entries
   uint64_t big_cap = 0, fb_cap = 0;
   float sigma = 8.0f;            // filter margin in binomial standard deviations
-  // host-fed insert: two device staging slots for CSR pieces, an internal copy stream
+  // host-fed insert: a ring of device staging slots for CSR pieces, an internal copy stream
   cudaStream_t copy_st = nullptr;
-  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
-  uint64_t* h2d_offs[2] = {nullptr, nullptr};
-  uint32_t* h2d_cols[2] = {nullptr, nullptr};
+  cudaEvent_t ev_copied[kH2dSlots] = {}, ev_free[kH2dSlots] = {};
+  uint64_t* h2d_offs[kH2dSlots] = {};
+  uint32_t* h2d_cols[kH2dSlots] = {};
   uint64_t h2d_rows = 0, h2d_nnz = 0;
   // the caller's allocator for the workspace (slash_set_allocator); null = cudaMalloc
   slash_alloc_fn alloc_fn = nullptr;
@@ -2406,11 +2414,34 @@ void ws_release_all(slash_index* ix) {
   ws_free(ix, ix->qbkt);
   ix->qbkt = nullptr;
   ix->qws = 0;
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kH2dSlots; ++i) {
     ws_free(ix, ix->h2d_offs[i]); ws_free(ix, ix->h2d_cols[i]);
     ix->h2d_offs[i] = nullptr; ix->h2d_cols[i] = nullptr;
   }
   ix->h2d_rows = ix->h2d_nnz = 0;
+}
+
+// h_offs[0..n] non-decreasing?  Large arrays are checked by several host
+// threads (the check precedes the first copy of a host-fed insert, so it is on
+// that call's critical path).
+bool offsets_ascending(const uint64_t* h_offs, uint64_t n) {
+  auto run = [h_offs](uint64_t a, uint64_t b) {  // rows [a, b)
+    uint64_t bad = 0;
+    for (uint64_t i = a; i < b; ++i) bad |= (uint64_t)(h_offs[i + 1] < h_offs[i]);
+    return bad == 0;
+  };
+  const unsigned hw = std::thread::hardware_concurrency();
+  const uint64_t T = std::min<uint64_t>(std::max(1u, hw), 16u);
+  if (n < (1ull << 22) || T < 2) return run(0, n);
+  std::vector<char> ok(T, 1);
+  std::vector<std::thread> th;
+  const uint64_t per = (n + T - 1) / T;
+  for (uint64_t t = 0; t < T; ++t)
+    th.emplace_back([&, t]() { ok[t] = run(std::min(n, t * per), std::min(n, (t + 1) * per)) ? 1 : 0; });
+  for (auto& x : th) x.join();
+  for (char c : ok)
+    if (!c) return false;
+  return true;
 }
 
 uint64_t insert_chunk_rows(const slash_index* ix) {
@@ -2936,22 +2967,27 @@ int slash_insert_host(slash_index* ix, const uint64_t* h_offs, const uint32_t* h
   }
   if (!h_offs || !h_cols) return SLASH_EINVAL;
   if (ix->next_id + n_rows > ix->p.capacity) return SLASH_EFULL;
-  for (uint64_t i = 0; i < n_rows; ++i)
-    if (h_offs[i + 1] < h_offs[i]) return SLASH_EINVAL;  // host offsets are checked here
+  if (!offsets_ascending(h_offs, n_rows)) return SLASH_EINVAL;  // host offsets are checked here
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  const uint64_t chunk = std::min<uint64_t>(insert_chunk_rows(ix), n_rows);
+  // The copies are the bound of this call.  A large batch goes in four chunks,
+  // so that the tail of every chunk but the last runs while the copy stream
+  // fills the ring for the next chunk; buckets keep the same contents however
+  // the rows are chunked (bottom-R is order-free).
+  const uint64_t chunk = std::min<uint64_t>(
+      std::min<uint64_t>(insert_chunk_rows(ix), std::max<uint64_t>(4 * kH2dPiece, (n_rows + 3) / 4)), n_rows);
   int rc = grow_insert_ws(ix, chunk);
   if (rc) return rc;
-  // pieces of at most 2M rows are copied while the previous piece is hashed
-  const uint64_t piece = std::min<uint64_t>(chunk, 1ull << 21);
+  // pieces of at most kH2dPiece rows, laid out chunk by chunk exactly as the copy loop takes them
+  const uint64_t piece = std::min<uint64_t>(chunk, kH2dPiece);
   uint64_t most_nnz = 0;
-  for (uint64_t r0 = 0; r0 < n_rows; r0 += piece) {
-    const uint64_t r1 = std::min<uint64_t>(n_rows, r0 + piece);
-    most_nnz = std::max<uint64_t>(most_nnz, h_offs[r1] - h_offs[r0]);
+  for (uint64_t c0 = 0; c0 < n_rows; c0 += chunk) {
+    const uint64_t c1 = std::min<uint64_t>(n_rows, c0 + chunk);
+    for (uint64_t r0 = c0; r0 < c1; r0 += piece)
+      most_nnz = std::max<uint64_t>(most_nnz, h_offs[std::min<uint64_t>(c1, r0 + piece)] - h_offs[r0]);
   }
   if (!ix->copy_st) {
     SLASH_CK(cudaStreamCreateWithFlags(&ix->copy_st, cudaStreamNonBlocking));
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kH2dSlots; ++i) {
       SLASH_CK(cudaEventCreateWithFlags(&ix->ev_copied[i], cudaEventDisableTiming));
       SLASH_CK(cudaEventCreateWithFlags(&ix->ev_free[i], cudaEventDisableTiming));
     }
@@ -2959,12 +2995,12 @@ int slash_insert_host(slash_index* ix, const uint64_t* h_offs, const uint32_t* h
   if (piece > ix->h2d_rows || most_nnz > ix->h2d_nnz) {
     SLASH_CK(cudaStreamSynchronize(st));
     SLASH_CK(cudaStreamSynchronize(ix->copy_st));
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kH2dSlots; ++i) {
       ws_free(ix, ix->h2d_offs[i]); ws_free(ix, ix->h2d_cols[i]);
       ix->h2d_offs[i] = nullptr; ix->h2d_cols[i] = nullptr;
     }
     ix->h2d_rows = ix->h2d_nnz = 0;
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kH2dSlots; ++i) {
       SLASH_CK(ws_malloc(ix, (void**)&ix->h2d_offs[i], sizeof(uint64_t) * (piece + 1)));
       SLASH_CK(ws_malloc(ix, (void**)&ix->h2d_cols[i], sizeof(uint32_t) * std::max<uint64_t>(most_nnz, 1)));
     }
@@ -2973,8 +3009,7 @@ int slash_insert_host(slash_index* ix, const uint64_t* h_offs, const uint32_t* h
   }
   const uint64_t first = ix->next_id;
   // the copy stream starts after the work already queued on the caller's stream
-  SLASH_CK(cudaEventRecord(ix->ev_free[0], st));
-  SLASH_CK(cudaEventRecord(ix->ev_free[1], st));
+  for (int i = 0; i < kH2dSlots; ++i) SLASH_CK(cudaEventRecord(ix->ev_free[i], st));
   uint32_t slot = 0;
   for (uint64_t c0 = 0; c0 < n_rows; c0 += chunk) {
     const uint32_t n = (uint32_t)std::min<uint64_t>(chunk, n_rows - c0);
@@ -2997,7 +3032,7 @@ int slash_insert_host(slash_index* ix, const uint64_t* h_offs, const uint32_t* h
                     ix->bkt + (r0 - c0), n, nullptr, true, st);
       if (rc) return rc;
       SLASH_CK(cudaEventRecord(ix->ev_free[slot], st));
-      slot ^= 1u;
+      slot = (slot + 1u) % kH2dSlots;
     }
     rc = insert_tail(ix, n, first + c0, st);
     if (rc) return rc;
@@ -3168,7 +3203,7 @@ int slash_free(slash_index* ix) {
   cudaFree(ix->blocksum); cudaFree(ix->meta);
   cudaFree(ix->ctr);
   cudaFree(ix->work);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < kH2dSlots; ++i) {
     if (ix->ev_copied[i]) cudaEventDestroy(ix->ev_copied[i]);
     if (ix->ev_free[i]) cudaEventDestroy(ix->ev_free[i]);
   }

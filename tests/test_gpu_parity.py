@@ -401,6 +401,47 @@ def test_streamed_device_rows_top100_bit_exact():
     assert np.mean((ids.cpu().numpy() == src[:, None]).any(axis=1)) > 0.9  # planted rows are found
 
 
+def test_insert_from_host_memory_chunks_not_aligned_to_pieces(monkeypatch):
+    """5M host rows in 3M-row chunks: the copy pieces (2^21 rows) restart at each
+    chunk, so the second chunk's pieces straddle the first chunk's grid.  The
+    host-fed index equals the device-fed one array for array, and sampled
+    buckets equal the oracle's."""
+    import oracle as orc
+    monkeypatch.setenv("SLASH_INSERT_CHUNK_ROWS", "3000000")
+    s = _slash()
+    g = datagen.Generator()
+    n = 5_000_000
+    offs, cols = g.rows(18, 0, n)
+    p = s.Params(K=4, L=16, log2_buckets=14, reservoir=16, cm_rows=4, cm_width=4096, capacity=n, seed=18)
+    h_offs = torch.from_numpy(offs.view(np.int64)).pin_memory()
+    h_cols = torch.from_numpy(cols.view(np.int32)).pin_memory()
+    with s.Index(p) as ix:
+        bad = h_offs.clone()
+        bad[4_500_000] = bad[4_500_001] + 1                  # one decreasing step, deep in the array
+        with pytest.raises(s.SlashError) as e:
+            ix.insert_host(bad, h_cols)
+        assert e.value.code == s.SLASH_EINVAL and ix.size == 0
+        assert ix.insert_host(h_offs, h_cols) == 0
+        ix.sync()
+        h_slots, h_fill = ix.export()
+    with s.Index(p) as ix:
+        ix.insert(_dev(offs), _dev(cols))
+        ix.sync()
+        d_slots, d_fill = ix.export()
+    assert np.array_equal(h_fill, d_fill) and np.array_equal(h_slots, d_slots)
+    rng = np.random.default_rng(18)
+    rt = rng.integers(0, p.L, 1500).astype(np.uint32)
+    rb = rng.integers(0, 1 << p.log2_buckets, 1500).astype(np.uint32)
+    oix = orc.Index(K=4, L=16, log2_buckets=14, reservoir=16, cm_rows=4, cm_width=4096, seed=18, capacity=n,
+                    partial=(rt, rb))
+    oix.insert(offs, cols, threads=datagen.default_threads())
+    fill2 = h_fill.reshape(p.L, 1 << p.log2_buckets)
+    slots2 = h_slots.reshape(p.L, 1 << p.log2_buckets, p.reservoir)
+    for t, b in zip(rt, rb):
+        want, wf = oix.bucket(int(t), int(b))
+        assert fill2[t, b] == wf and np.array_equal(slots2[t, b], want), (int(t), int(b))
+
+
 @pytest.mark.parametrize("chunk_rows", ["7000", "0"])
 def test_insert_from_host_memory_bit_exact(chunk_rows, monkeypatch):
     """slash_insert_host (pinned host CSR, copies overlapped with hashing, many
