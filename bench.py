@@ -384,9 +384,9 @@ def main():
     if args.impl == "reference":
         run_reference(args, w)
         return
-    if w.name in ("uneven", "serving", "stream", "topkapi", "sweep"):
+    if w.name in ("uneven", "serving", "stream", "topkapi", "sweep", "exchange"):
         fn = {"uneven": bench_uneven, "serving": bench_serving, "stream": bench_stream,
-              "topkapi": bench_topkapi, "sweep": bench_sweep}[w.name]
+              "topkapi": bench_topkapi, "sweep": bench_sweep, "exchange": bench_exchange}[w.name]
         print(json.dumps(fn(args, w)), flush=True)
         return
 
@@ -723,6 +723,82 @@ def bench_serving(args, w: workloads.Workload) -> dict:
             "schedule": sched, "schedule_ms_per_65536_queries": timings, "slots": args.serve_slots,
             "max_batch_queries": args.serve_max_batch,
             "rates": per_rate}
+
+
+def bench_exchange(args, w: workloads.Workload) -> dict:
+    """The candidate exchange (one logical index over row partitions) on one GPU:
+    the criteo rows in W partitions, one index each with the shared seed; the
+    query batch answered by candidates -> all-gather -> cells -> all-reduce ->
+    rank, the collectives done as local stacking and sums (every call of this
+    build uses one GPU).  Against one index whose W shards are the partitions:
+    the answers must be identical."""
+    torch, slash = _gpu_setup(w)
+    from paper_2008_03260_b300.multi import GpuPart, exchange_query_loopback, partition
+    W = w.extra["partitions"]
+    offs, cols, qo, qc, _ = make_inputs(w, 0, w.n_rows, w.n_queries)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64 if a.dtype == np.uint64 else np.int32)).cuda()
+    ixs, parts = [], []
+    for r in range(W):
+        lo, cnt = partition(r, W, w.n_rows)
+        ix = slash.Index(slash.Params(**w.params()))
+        ix.set_next_id(lo)
+        o = offs[lo:lo + cnt + 1]
+        ix.insert(dev(o - o[0]), dev(cols[int(o[0]):int(o[-1])]))
+        ix.sync()
+        ixs.append(ix)
+        parts.append(GpuPart(ix))
+    one = slash.Index(slash.Params(**w.params(shards=W)))
+    one.insert(dev(offs), dev(cols))
+    one.sync()
+    d_qo, d_qc = dev(qo), dev(qc)
+    st = torch.cuda.current_stream()
+
+    def timed(fn):
+        out, res = [], None
+        for i in range(args.warmup + args.steps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            res = fn()
+            b.record(st)
+            b.synchronize()
+            if i >= args.warmup:
+                out.append(a.elapsed_time(b) / 1e3)
+        return statistics.mean(out), res
+
+    chunk = 4096
+    with Clocks(0) as clk:
+        t_ex, (ex_ids, ex_sc) = timed(lambda: exchange_query_loopback(parts, d_qo, d_qc, w.topk, chunk=chunk))
+        t_one, (one_ids, one_sc) = timed(lambda: one.query(d_qo, d_qc, w.topk))
+    equal = bool(torch.equal(ex_ids, one_ids) and torch.equal(ex_sc, one_sc))
+    # where the exchange's time goes: the partitions' kernels (library events),
+    # the rest being the ranking and the local collectives
+    for ix in ixs:
+        ix.profile(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    exchange_query_loopback(parts, d_qo, d_qc, w.topk, chunk=chunk)
+    b.record(st)
+    b.synchronize()
+    stages = {}
+    for ix in ixs:
+        for name, (ms, n) in ix.profile_read()[0].items():
+            stages[name] = stages.get(name, 0.0) + ms
+        ix.profile(False)
+    stages["rank and local collectives"] = max(0.0, a.elapsed_time(b) - sum(stages.values()))
+    for ix in ixs:
+        ix.sync()
+        ix.close()
+    one.close()
+    m = w.L * w.reservoir  # candidate ids one partition can send per query
+    return {"metric": "queries/s of one logical index over row partitions (candidate exchange) on 1 B300",
+            "value": w.n_queries / t_ex, "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_ex, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded Criteo-shaped generator)",
+            "config": dict(config_of(w, args), partitions=W, chunk_queries=chunk,
+                           collectives="local stacking and sums on one GPU"),
+            "one_index_queries_per_s": w.n_queries / t_one, "answers_identical": equal,
+            "stage_ms": stages,
+            "exchanged_bytes_per_query_per_rank_at_most": W * (4 + 4 * m + 4 * w.cm_rows * m), "clocks": clk.summary()}
 
 
 def bench_stream(args, w: workloads.Workload) -> dict:

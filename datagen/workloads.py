@@ -17,6 +17,9 @@ per row, power-law feature popularity), reduced to what one device holds:
   topkapi    rows and queries of `criteo`, TopKAPI sketch buckets of 4 rows x
              32 cells (512 B per bucket, the size of an R=128 reservoir;
              ~8.6 GB), top-10
+  exchange   rows and queries of `criteo` split into 2 row partitions (one index
+             each, shared seed), answered as one index through the candidate
+             exchange
   sweep      quality sweep of Sec. 6 (K = 4; L = 16, 24, 32): 1M rows, 2^16
              buckets, R=32 (side-rule or optimal densification) or TopKAPI
              4x8 (same bytes), 10k planted queries (20% resampled), S@1, S@64
@@ -79,10 +82,13 @@ STREAM = Workload("stream", 1_000_000_000, 8, 32, 20, 256, 4, 8192, 1_000_000, 1
 TOPKAPI = Workload("topkapi", 50_000_000, 6, 64, 18, 0, 0, 0, 100_000, 10, p_perturb=0.1,
                    extra={"tk_rows": 4, "tk_cells": 32})
 
+EXCHANGE = Workload("exchange", 50_000_000, 6, 64, 18, 128, 4, 8192, 100_000, 10, p_perturb=0.1,
+                    extra={"partitions": 2})
+
 SWEEP = Workload("sweep", 1_000_000, 4, 32, 16, 32, 4, 8192, 10_000, 64, p_perturb=0.2,
                  extra={"L_values": (16, 24, 32), "tk_rows_sweep": 4, "tk_cells_sweep": 8})
 
-ALL = {w.name: w for w in (TINY, CRITEO, UNEVEN, SERVING, STREAM, TOPKAPI, SWEEP)}
+ALL = {w.name: w for w in (TINY, CRITEO, UNEVEN, SERVING, STREAM, TOPKAPI, EXCHANGE, SWEEP)}
 
 LOGNORMAL_MU = math.log(40.0)
 LOGNORMAL_SIGMA = 1.0

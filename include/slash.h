@@ -200,8 +200,9 @@ int slash_query_static(slash_index *ix, const uint64_t *d_offs, const uint32_t *
 int slash_set_next_id(slash_index *ix, uint64_t next_id);
 
 /* Each query's distinct candidates in this index (the ids of its S*L buckets):
- * d_counts int32 [n_queries], d_ids int32 [n_queries][m] in ascending order, -1
- * past the count; m >= S*L*R.  Uses the plain-query workspace (SLASH_ENOMEM
+ * d_counts int32 [n_queries], d_ids int32 [n_queries][m] in the order of their
+ * first occurrence in the query's buckets (shard-major, then table, then slot),
+ * -1 past the count; m >= S*L*R.  Uses the plain-query workspace (SLASH_ENOMEM
  * if it cannot grow).  Errors: SLASH_EINVAL (m too small, NULL, or S*L*R too
  * large for one CTA's shared memory), SLASH_ENOMEM, SLASH_ECUDA. */
 int slash_query_candidates(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n_queries,
@@ -211,8 +212,11 @@ int slash_query_candidates(slash_index *ix, const uint64_t *d_offs, const uint32
  * world, query q and j < m, d_cells[((w*n_queries + q)*m + j)*d + r] = this
  * index's sketch count in row r (d = cm_rows) at the cell of d_ids[(w*n_queries
  * + q)*m + j], the sketch being the one query q builds from its own buckets;
- * 0 for j >= d_counts[w*n_queries + q].  Errors as slash_query_candidates
- * (world 1..64). */
+ * entries with j >= d_counts[w*n_queries + q] are not written (the ranking
+ * reads only those below the count).  Here m is the row length of the gathered
+ * ids (>= 1; rows may be cut to the largest count, and counts above m are
+ * read as m).  d_cells must be 16-byte aligned.  Errors: SLASH_EINVAL (world
+ * 1..64, m = 0, NULL, misaligned d_cells), SLASH_ENOMEM, SLASH_ECUDA. */
 int slash_query_cells(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols, uint32_t n_queries,
                       uint32_t world, uint32_t m, const int32_t *d_counts, const int32_t *d_ids, uint32_t *d_cells,
                       void *cuda_stream);

@@ -3472,9 +3472,10 @@ extern "C" int slash_query_static(slash_index* ix, const uint64_t* d_offs, const
 // ----------------------------------------------------------------------------- candidate exchange
 // The local steps of one process of a multi-process index (Sec. 3 partitions,
 // Algorithm 2's merge across machines done as one exchange of candidates):
-//   k_candidates   each query's distinct local candidate ids, ascending;
+//   k_candidates   each query's distinct local candidate ids, in bucket order;
 //   k_cells        this partition's count-min cells of every gathered id;
-//   k_rank         top-k from the summed cells (estimate = the smallest cell).
+//   k_rank         top-k from the summed cells (estimate = the smallest cell): a
+//                  histogram cut-off, then one sort of the candidates at or above it.
 // The collectives between them (all-gather of the ids, sum of the cells) are
 // the caller's.  Each kernel takes one CTA per query (grid-stride).
 namespace {
@@ -3518,7 +3519,11 @@ __device__ uint32_t ex_gather(const Geo& g, const uint32_t* __restrict__ qbkt, u
   return bo[nbk];
 }
 
-// Each query's distinct local candidates, ascending: counts[q], out[q*m .. q*m + m) (-1 past the count).
+// Each query's distinct local candidates, in the order of their first
+// occurrence in its buckets (shard-major, then table, then slot): counts[q],
+// out[q*m .. q*m + m) (-1 past the count).  Repeats are found with a
+// shared-memory table of buffer indices (open addressing, 2*n2 slots): a slot
+// keeps the smallest index of its id, and a position is kept when it holds it.
 __global__ void __launch_bounds__(kExThreads)
 k_candidates(const __grid_constant__ Geo g, const uint32_t* __restrict__ qbkt, uint64_t ldq, uint32_t nq, uint32_t m,
              const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill, int32_t* __restrict__ counts,
@@ -3527,25 +3532,49 @@ k_candidates(const __grid_constant__ Geo g, const uint32_t* __restrict__ qbkt, u
   const uint32_t nbk = g.S * g.L, maxm = nbk * g.R;
   uint32_t n2 = 2;
   while (n2 < maxm) n2 <<= 1;
+  const uint32_t T = 2u * n2, tmask = T - 1u;
   uint32_t* ids = exs;                 // [n2]
-  uint32_t* bk = ids + n2;             // [nbk]
+  uint32_t* tab = ids + n2;            // [2 * n2] buffer indices, kEmpty = free
+  uint32_t* bk = tab + T;              // [nbk]
   uint32_t* bf = bk + nbk;             // [nbk]
   uint32_t* bo = bf + nbk;             // [nbk + 1]
   uint32_t* tmp = bo + nbk + 1;        // [nbk / 32 + 1]
   uint32_t* wcnt = tmp + nbk / 32 + 1; // [33]
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, NW = blockDim.x >> 5;
   for (uint32_t q = blockIdx.x; q < nq; q += gridDim.x) {
+    for (uint32_t i = threadIdx.x; i < T; i += blockDim.x) tab[i] = kEmpty;  // ordered by the gather's barrier
     const uint32_t n = ex_gather(g, qbkt, ldq, q, slots, fill, ids, bk, bf, bo, tmp);
-    uint32_t p2 = 2;
-    while (p2 < n) p2 <<= 1;
-    for (uint32_t i = n + threadIdx.x; i < p2; i += blockDim.x) ids[i] = kEmpty;
+    // every position enters its id's slot, which keeps the smallest position
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint32_t id = ids[i];
+      for (uint32_t sl = mix32(id) & tmask, probe = 0; probe < T; ++probe, sl = (sl + 1u) & tmask) {
+        uint32_t t = tab[sl];
+        if (t == kEmpty) {
+          t = atomicCAS(&tab[sl], kEmpty, i);
+          if (t == kEmpty) break;  // claimed
+        }
+        if (ids[t] == id) {
+          atomicMin(&tab[sl], i);
+          break;
+        }
+      }
+    }
     __syncthreads();
-    block_bitonic_u32(ids, p2);
-    // keep the first of each run of equal ids, compacted in order
+    // keep the positions their slot names, compacted in buffer order
     uint32_t base = 0;
     for (uint32_t i0 = 0; i0 < n; i0 += blockDim.x) {
       const uint32_t i = i0 + threadIdx.x;
-      const bool fresh = i < n && (i == 0 || ids[i - 1] != ids[i]);
+      bool fresh = false;
+      if (i < n) {
+        // the id's slot: on its probe path every slot before it is taken (slots only fill)
+        const uint32_t id = ids[i];
+        uint32_t sl = mix32(id) & tmask, t = tab[sl];
+        for (uint32_t probe = 0; probe < T && t != kEmpty && ids[t] != id; ++probe) {
+          sl = (sl + 1u) & tmask;
+          t = tab[sl];
+        }
+        fresh = t == i;
+      }
       const uint32_t bal = __ballot_sync(0xFFFFFFFFu, fresh);
       if (lane == 0) wcnt[warp] = __popc(bal);
       __syncthreads();
@@ -3572,8 +3601,8 @@ k_candidates(const __grid_constant__ Geo g, const uint32_t* __restrict__ qbkt, u
 }
 
 // This partition's sketch cells of every gathered id: for rank w < W and
-// j < m, cells[((w*nq + q)*m + j)*d + r] = the partition's count in row r at
-// the id's cell (0 for j >= counts[w*nq + q]).
+// j < counts[w*nq + q], cells[((w*nq + q)*m + j)*d + r] = the partition's count
+// in row r at the id's cell (entries past the count are not written).
 __global__ void __launch_bounds__(kExThreads)
 k_cells(const __grid_constant__ Geo g, const uint32_t* __restrict__ qbkt, uint64_t ldq, uint32_t nq, uint32_t W,
         uint32_t m, const int32_t* __restrict__ counts, const int32_t* __restrict__ gids,
@@ -3592,13 +3621,21 @@ k_cells(const __grid_constant__ Geo g, const uint32_t* __restrict__ qbkt, uint64
     for (uint32_t i = threadIdx.x; i < n; i += blockDim.x)
       for (uint32_t r = 0; r < g.d; ++r) cm_add(cmw, r * g.w + cm_cell(ids[i], g.sc[r], wmask));
     __syncthreads();
-    for (uint32_t w = 0; w < W; ++w) {
+    for (uint32_t w = 0; w < W; ++w) {  // entries past a rank's count are left as they are
       const uint64_t row = (uint64_t)w * nq + q;
-      const uint32_t c = (uint32_t)max(0, counts[row]);
-      for (uint32_t j = threadIdx.x; j < m; j += blockDim.x) {
+      const uint32_t c = min((uint32_t)max(0, counts[row]), m);
+      for (uint32_t j = threadIdx.x; j < c; j += blockDim.x) {
         const uint32_t id = (uint32_t)gids[row * m + j];
-        for (uint32_t r = 0; r < g.d; ++r)
-          cells[(row * m + j) * g.d + r] = j < c ? cm_get(cmw, r * g.w + cm_cell(id, g.sc[r], wmask)) : 0u;
+        if (g.d == 4u) {  // one 16-byte store
+          uint4 v;
+          v.x = cm_get(cmw, 0u * g.w + cm_cell(id, g.sc[0], wmask));
+          v.y = cm_get(cmw, 1u * g.w + cm_cell(id, g.sc[1], wmask));
+          v.z = cm_get(cmw, 2u * g.w + cm_cell(id, g.sc[2], wmask));
+          v.w = cm_get(cmw, 3u * g.w + cm_cell(id, g.sc[3], wmask));
+          reinterpret_cast<uint4*>(cells)[row * m + j] = v;
+        } else {
+          for (uint32_t r = 0; r < g.d; ++r) cells[(row * m + j) * g.d + r] = cm_get(cmw, r * g.w + cm_cell(id, g.sc[r], wmask));
+        }
       }
     }
     __syncthreads();
@@ -3613,55 +3650,113 @@ k_rank(uint32_t W, uint32_t nq, uint32_t m, uint32_t d, const int32_t* __restric
        uint32_t* __restrict__ scores_out) {
   extern __shared__ __align__(16) uint64_t exk[];
   uint64_t* A = exk;              // [kExChunk] keys of one chunk
-  uint64_t* S = A + kExChunk;     // [kExChunk] survivors: each chunk's first k
+  uint64_t* S = A + kExChunk;     // [kExChunk] survivors: each chunk's first k, or the cut-off pool
   __shared__ uint32_t pre[65];    // prefix of the ranks' counts (W <= 64)
+  __shared__ uint32_t hist[256];  // estimates (255 = at least 255)
+  __shared__ uint32_t elo, npool;
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  // estimate and key of gathered candidate e of query q
+  auto key_of = [&](uint32_t q, uint32_t e, uint32_t& est) -> uint64_t {
+    uint32_t w = 0;
+    while (pre[w + 1] <= e) ++w;
+    const uint64_t row = (uint64_t)w * nq + q;
+    const uint32_t j = e - pre[w];
+    est = 0xFFFFFFFFu;
+    for (uint32_t r = 0; r < d; ++r) est = min(est, cells[(row * m + j) * d + r]);
+    return ((uint64_t)(0xFFFFFFFFu - est) << 32) | (uint32_t)gids[row * m + j];
+  };
   for (uint32_t q = blockIdx.x; q < nq; q += gridDim.x) {
     if (threadIdx.x == 0) {
       uint32_t run = 0;
       for (uint32_t w = 0; w < W; ++w) { pre[w] = run; run += (uint32_t)max(0, counts[(uint64_t)w * nq + q]); }
       pre[W] = run;
+      npool = 0;
     }
+    for (uint32_t i = threadIdx.x; i < 256u; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
     const uint32_t E = pre[W];
-    uint32_t sn = 0;
-    for (uint32_t e0 = 0; e0 < E; e0 += kExChunk) {
-      const uint32_t ne = min(kExChunk, E - e0);
-      uint32_t p2 = 2;
-      while (p2 < ne) p2 <<= 1;
-      for (uint32_t i = threadIdx.x; i < p2; i += blockDim.x) {
-        uint64_t key = ~0ull;
-        if (i < ne) {
-          const uint32_t e = e0 + i;
-          uint32_t w = 0;
-          while (pre[w + 1] <= e) ++w;
-          const uint64_t row = (uint64_t)w * nq + q;
-          const uint32_t j = e - pre[w];
-          uint32_t est = 0xFFFFFFFFu;
-          for (uint32_t r = 0; r < d; ++r) est = min(est, cells[(row * m + j) * d + r]);
-          key = ((uint64_t)(0xFFFFFFFFu - est) << 32) | (uint32_t)gids[row * m + j];
-        }
-        A[i] = key;
-      }
-      __syncthreads();
-      block_bitonic(A, p2);
-      const uint32_t keep = min(k, ne);
-      if (sn + keep > kExChunk) {  // fold the survivors to their first k
-        uint32_t s2 = 2;
-        while (s2 < sn) s2 <<= 1;
-        for (uint32_t i = sn + threadIdx.x; i < s2; i += blockDim.x) S[i] = ~0ull;
-        __syncthreads();
-        block_bitonic(S, s2);
-        sn = min(sn, k);
-      }
-      for (uint32_t i = threadIdx.x; i < keep; i += blockDim.x) S[sn + i] = A[i];
-      sn += keep;
-      __syncthreads();
+    // -- cut-off: the largest estimate bin whose bins at or above it hold min(k, E)
+    //    candidates; candidates are distinct (partitions hold disjoint ids), so the
+    //    top k lie in the pool of those at or above it
+    for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
+      uint32_t est;
+      key_of(q, e, est);
+      atomicAdd(&hist[min(est, 255u)], 1u);
     }
-    uint32_t s2 = 2;
-    while (s2 < sn) s2 <<= 1;
-    for (uint32_t i = sn + threadIdx.x; i < s2; i += blockDim.x) S[i] = ~0ull;
     __syncthreads();
-    block_bitonic(S, s2);
+    if (warp == 0) {
+      const uint32_t need = min(k, E);
+      uint32_t v[8], sum = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) { v[i] = hist[255u - (lane * 8u + i)]; sum += v[i]; }
+      uint32_t inc = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= (uint32_t)o) inc += u;
+      }
+      if (need == 0u && lane == 0) elo = 0u;
+      const uint32_t ex = inc - sum;
+      if (need > 0u && ex < need && need <= inc) {
+        uint32_t cum = ex;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          cum += v[i];
+          if (cum >= need) { elo = 255u - (lane * 8u + i); break; }
+        }
+      }
+    }
+    __syncthreads();
+    const uint32_t lo = elo;
+    for (uint32_t e = threadIdx.x; e < E; e += blockDim.x) {
+      uint32_t est;
+      const uint64_t key = key_of(q, e, est);
+      if (min(est, 255u) >= lo) {
+        const uint32_t pos = atomicAdd(&npool, 1u);
+        if (pos < kExChunk) S[pos] = key;
+      }
+    }
+    __syncthreads();
+    const uint32_t P = npool;
+    uint32_t sn;
+    if (P <= kExChunk) {  // the usual case: sort the pool
+      uint32_t p2 = 2;
+      while (p2 < P) p2 <<= 1;
+      for (uint32_t i = P + threadIdx.x; i < p2; i += blockDim.x) S[i] = ~0ull;
+      __syncthreads();
+      block_bitonic(S, p2);
+      sn = P;
+    } else {  // a pool too large for one sort: every candidate, chunk by chunk
+      sn = 0;
+      for (uint32_t e0 = 0; e0 < E; e0 += kExChunk) {
+        const uint32_t ne = min(kExChunk, E - e0);
+        uint32_t p2 = 2;
+        while (p2 < ne) p2 <<= 1;
+        for (uint32_t i = threadIdx.x; i < p2; i += blockDim.x) {
+          uint32_t est;
+          A[i] = i < ne ? key_of(q, e0 + i, est) : ~0ull;
+        }
+        __syncthreads();
+        block_bitonic(A, p2);
+        const uint32_t keep = min(k, ne);
+        if (sn + keep > kExChunk) {  // fold the survivors to their first k
+          uint32_t s2 = 2;
+          while (s2 < sn) s2 <<= 1;
+          for (uint32_t i = sn + threadIdx.x; i < s2; i += blockDim.x) S[i] = ~0ull;
+          __syncthreads();
+          block_bitonic(S, s2);
+          sn = min(sn, k);
+        }
+        for (uint32_t i = threadIdx.x; i < keep; i += blockDim.x) S[sn + i] = A[i];
+        sn += keep;
+        __syncthreads();
+      }
+      uint32_t s2 = 2;
+      while (s2 < sn) s2 <<= 1;
+      for (uint32_t i = sn + threadIdx.x; i < s2; i += blockDim.x) S[i] = ~0ull;
+      __syncthreads();
+      block_bitonic(S, s2);
+    }
     for (uint32_t j = threadIdx.x; j < k; j += blockDim.x) {
       const bool have = j < sn;
       ids_out[(uint64_t)q * k + j] = have ? (int32_t)(uint32_t)S[j] : -1;
@@ -3702,14 +3797,16 @@ int slash_query_candidates(slash_index* ix, const uint64_t* d_offs, const uint32
   if (!d_offs || !d_cols || !d_counts || !d_ids) return SLASH_EINVAL;
   uint32_t n2 = 2;
   while (n2 < maxm) n2 <<= 1;
-  const size_t smem = sizeof(uint32_t) * (n2 + 33) + ex_gather_smem(ix->p);
+  const size_t smem = sizeof(uint32_t) * (3 * (size_t)n2 + 33) + ex_gather_smem(ix->p);  // ids, table, counts
   if (smem > ix->smem_optin) return SLASH_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   ApiRange api("slash_query_candidates");
   int rc = ex_addresses(ix, d_offs, d_cols, n_queries, st);
   if (rc) return rc;
   cudaFuncSetAttribute(k_candidates, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const uint32_t grid = (uint32_t)std::min<uint64_t>(n_queries, (uint64_t)ix->num_sms * 2);
+  int bps = 0;  // every CTA the SMs hold: each sorts its own query's ids
+  SLASH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_candidates, kExThreads, smem));
+  const uint32_t grid = (uint32_t)std::min<uint64_t>(n_queries, (uint64_t)ix->num_sms * std::max(bps, 1));
   Launch l(ix, "k_candidates", st);
   k_candidates<<<grid, kExThreads, smem, st>>>(ix->geo, ix->qbkt, n_queries, n_queries, m, ix->slots, ix->fill,
                                                 d_counts, d_ids);
@@ -3720,11 +3817,11 @@ int slash_query_candidates(slash_index* ix, const uint64_t* d_offs, const uint32
 int slash_query_cells(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_cols, uint32_t n_queries,
                       uint32_t world, uint32_t m, const int32_t* d_counts, const int32_t* d_ids, uint32_t* d_cells,
                       void* cuda_stream) {
-  if (!ix || world == 0 || world > 64) return SLASH_EINVAL;
+  if (!ix || world == 0 || world > 64 || m == 0) return SLASH_EINVAL;
   const uint64_t maxm = (uint64_t)ix->p.shards * ix->p.L * ix->p.reservoir;
-  if (m < maxm) return SLASH_EINVAL;
   if (n_queries == 0) return SLASH_OK;
-  if (!d_offs || !d_cols || !d_counts || !d_ids || !d_cells) return SLASH_EINVAL;
+  if (!d_offs || !d_cols || !d_counts || !d_ids || !d_cells || (reinterpret_cast<uintptr_t>(d_cells) & 15u))
+    return SLASH_EINVAL;
   const size_t smem = sizeof(uint32_t) * ((size_t)ix->p.cm_rows * ix->p.cm_width / 2 + maxm) + ex_gather_smem(ix->p);
   if (smem > ix->smem_optin) return SLASH_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -3732,7 +3829,9 @@ int slash_query_cells(slash_index* ix, const uint64_t* d_offs, const uint32_t* d
   int rc = ex_addresses(ix, d_offs, d_cols, n_queries, st);
   if (rc) return rc;
   cudaFuncSetAttribute(k_cells, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const uint32_t grid = (uint32_t)std::min<uint64_t>(n_queries, (uint64_t)ix->num_sms * 2);
+  int bps = 0;
+  SLASH_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_cells, kExThreads, smem));
+  const uint32_t grid = (uint32_t)std::min<uint64_t>(n_queries, (uint64_t)ix->num_sms * std::max(bps, 1));
   Launch l(ix, "k_cells", st);
   k_cells<<<grid, kExThreads, smem, st>>>(ix->geo, ix->qbkt, n_queries, n_queries, world, m, d_counts, d_ids,
                                            ix->slots, ix->fill, d_cells);

@@ -81,11 +81,12 @@ def exchange_query(local, comm, offs, cols, k: int, chunk: int = 4096):
     """Top-k of a query batch over every rank's partition (one logical index).
 
     ``local`` does the three local steps of one rank (``GpuPart`` on a device):
-      candidates(offs, cols)           -> counts [nq], ids [nq, m] (distinct, ascending, -1 past the count)
+      candidates(offs, cols)           -> counts [nq], ids [nq, m] (distinct, -1 past the count)
       cells(offs, cols, ids, counts)   -> [W, nq, m, d] this rank's sketch cells of every gathered id
       rank(ids, counts, cells, k)      -> ids [nq, k], scores [nq, k] from the summed cells
     ``offs`` (nq+1 offsets into ``cols``) and ``cols`` are the same batch on every
-    rank.  Queries go in chunks of ``chunk`` to bound the exchanged bytes.
+    rank.  Queries go in chunks of ``chunk`` to bound the exchanged bytes; the
+    id rows are cut to the chunk's largest count before they are exchanged.
     """
     import torch
     nq = len(offs) - 1
@@ -95,7 +96,8 @@ def exchange_query(local, comm, offs, cols, k: int, chunk: int = 4096):
         o = offs[q0:q1 + 1]
         cnt, ids = local.candidates(o, cols)
         all_cnt = comm.all_gather(cnt)
-        all_ids = comm.all_gather(ids)
+        mc = max(1, int(all_cnt.max()))           # the same on every rank
+        all_ids = comm.all_gather(ids[:, :mc].contiguous())
         cells = comm.all_reduce_sum(local.cells(o, cols, all_ids, all_cnt))
         i, s = local.rank(all_ids, all_cnt, cells, k)
         out_ids.append(i)
@@ -115,7 +117,8 @@ def exchange_query_loopback(parts: list, offs, cols, k: int, chunk: int = 4096):
         o = offs[q0:q1 + 1]
         cand = [p.candidates(o, cols) for p in parts]
         all_cnt = torch.stack([c[0] for c in cand])
-        all_ids = torch.stack([c[1] for c in cand])
+        mc = max(1, int(all_cnt.max()))
+        all_ids = torch.stack([c[1][:, :mc] for c in cand])
         cells = parts[0].cells(o, cols, all_ids, all_cnt)
         for p in parts[1:]:
             cells = cells + p.cells(o, cols, all_ids, all_cnt)
