@@ -343,6 +343,16 @@ int slash_debug_fail_alloc(slash_index *ix, uint32_t count);
  * index the staged engine does not serve). */
 int slash_debug_stall_copies(slash_index *ix, int enable);
 
+/* Test support -- checked builds.  The library built with -DSLASH_CHECKS
+ * (libslash_checked.so, the same entry points) tests every bucket key and
+ * staging offset its kernels derive from the data before using it; one out of
+ * range raises a device-wide flag and the access is skipped.  This call reports
+ * *checked_out = 1 in such a build (0 otherwise) and *errors_out = the flag
+ * (nonzero: some kernel found an index out of range since the last call),
+ * then clears it.  Synchronises the device in a checked build.
+ * Errors: SLASH_EINVAL (NULL), SLASH_ECUDA. */
+int slash_debug_bounds(uint32_t *checked_out, uint32_t *errors_out);
+
 /* Test support -- copy the whole index to host memory: h_slots uint32
  * [S][L][2^B][R], h_fill uint32 [S][L][2^B].  Synchronises.  Either pointer
  * may be NULL.  Errors: SLASH_ECUDA. */

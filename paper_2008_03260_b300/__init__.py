@@ -24,7 +24,9 @@ from dataclasses import dataclass
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-_LIB_PATH = os.path.join(_PKG, "libslash.so")
+# SLASH_CHECKED=1 loads the checked build (bounds-tested indices; slower)
+_CHECKED = os.environ.get("SLASH_CHECKED", "") == "1"
+_LIB_PATH = os.path.join(_PKG, "libslash_checked.so" if _CHECKED else "libslash.so")
 
 SLASH_OK = 0
 SLASH_EINVAL = -1
@@ -91,8 +93,8 @@ class slash_tk_params(ctypes.Structure):
 
 def _load() -> ctypes.CDLL:
     from . import build as _build
-    if _build.needs_build():  # compile the CUDA library in place (nvcc); no fallback if that fails
-        _build.build()
+    if _build.needs_build(_CHECKED):  # compile the CUDA library in place (nvcc); no fallback if that fails
+        _build.build(checked=_CHECKED)
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"libslash.so not built ({_LIB_PATH}); run python -m paper_2008_03260_b300.build")
     lib = ctypes.CDLL(_LIB_PATH)
@@ -124,6 +126,7 @@ def _load() -> ctypes.CDLL:
         "slash_query_static": (i32, [vp, vp, vp, u32, u32, vp, vp, vp]),
         "slash_serve": (i32, [vp, P(slash_serve_opts), u32, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         "slash_set_allocator": (i32, [vp, SLASH_ALLOC_FN, SLASH_FREE_FN, vp]),
+        "slash_debug_bounds": (i32, [P(u32), P(u32)]),
         "slash_profile": (i32, [vp, i32]),
         "slash_profile_read": (i32, [vp, u32, vp, vp, vp, P(u32), P(u64)]),
         "slash_tk_build": (i32, [P(slash_tk_params), vp, P(vp)]),
@@ -338,6 +341,13 @@ def slash_set_allocator(ix: int, alloc=None, release=None) -> None:
     cbs = (SLASH_ALLOC_FN(_a), SLASH_FREE_FN(_f))
     _check(_lib.slash_set_allocator(ix, cbs[0], cbs[1], None), "slash_set_allocator")
     return cbs
+
+
+def slash_debug_bounds() -> tuple[bool, int]:
+    """(is this the checked build, its out-of-range flag since the last call); clears the flag."""
+    c, e = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(_lib.slash_debug_bounds(ctypes.byref(c), ctypes.byref(e)), "slash_debug_bounds")
+    return bool(c.value), int(e.value)
 
 
 def torch_allocator():

@@ -63,6 +63,21 @@
 
 using namespace slash;
 
+// Checked builds (-DSLASH_CHECKS, libslash_checked.so): every bucket key and
+// staging offset derived from the data is tested before it is used; one out of
+// range raises g_bounds_err and the access is skipped (no trap).  In the
+// service build SLASH_BOUND(c) is `true` and the tests compile away.
+#ifdef SLASH_CHECKS
+__device__ uint32_t g_bounds_err = 0u;
+__device__ __forceinline__ bool slash_bound(bool ok) {
+  if (!ok) atomicOr(&g_bounds_err, 1u);
+  return ok;
+}
+#define SLASH_BOUND(c) slash_bound(c)
+#else
+#define SLASH_BOUND(c) true
+#endif
+
 // ----------------------------------------------------------------------------- k_hash
 namespace {
 
@@ -107,7 +122,8 @@ k_hash(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
       uint32_t out = b;
       if (kCount) {
         // the count's old value is this pair's rank in its bucket: kept in the low bits
-        const uint32_t rank = atomic_add_keep(&cnt[(((uint64_t)s * g.L + t) << g.B) | b], 1u, keep);
+        const uint64_t ci = (((uint64_t)s * g.L + t) << g.B) | b;
+        const uint32_t rank = SLASH_BOUND(ci < ((uint64_t)g.S * g.L << g.B)) ? atomic_add_keep(&cnt[ci], 1u, keep) : 0u;
         if (g.rbits) out = (b << g.rbits) | min(rank, (1u << g.rbits) - 1u);
       }
       tile[t * kTileStride + lr] = out;
@@ -229,7 +245,8 @@ k_hash_reg(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
       uint32_t out = b;
       if (kCount) {
         // the count's old value is this pair's rank in its bucket: kept in the low bits
-        const uint32_t rank = atomic_add_keep(&cnt[(((uint64_t)s * g.L + t) << g.B) | b], 1u, keep);
+        const uint64_t ci = (((uint64_t)s * g.L + t) << g.B) | b;
+        const uint32_t rank = SLASH_BOUND(ci < ((uint64_t)g.S * g.L << g.B)) ? atomic_add_keep(&cnt[ci], 1u, keep) : 0u;
         if (g.rbits) out = (b << g.rbits) | min(rank, (1u << g.rbits) - 1u);
       }
       tile[t * kTileStride + lr] = out;
@@ -405,9 +422,10 @@ k_scatter(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
     const uint64_t id = id0 + i;
     const uint32_t s = shard_of(sm, g.S, id);
     const uint64_t key = (((uint64_t)s * g.L + t) << g.B) | b;
+    if (!SLASH_BOUND(key < ((uint64_t)g.S * g.L << g.B))) continue;
     const uint4 m = meta[key];
     if (g.rbits && m.x == kNoFilter) {  // unfiltered bucket: every pair staged at its rank
-      stage[(uint64_t)m.z + (v & ((1u << g.rbits) - 1u))] = (uint32_t)id;
+      if (SLASH_BOUND((v & ((1u << g.rbits) - 1u)) < m.y)) stage[(uint64_t)m.z + (v & ((1u << g.rbits) - 1u))] = (uint32_t)id;
       continue;
     }
     if (priority((uint32_t)id, sp) >= m.x) continue;
@@ -612,6 +630,7 @@ k_fb_collect(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
       const uint64_t id = id0 + i;
       const uint32_t s = shard_of(sm, g.S, id);
       const uint64_t key = (((uint64_t)s * g.L + t) << g.B) | b;
+      if (!SLASH_BOUND(key < ((uint64_t)g.S * g.L << g.B))) continue;
       const uint4 m = meta[key];
       if (m.y != kFallback) continue;
       stage[(uint64_t)fboff[m.w] + atomicAdd(&fbcur[m.w], 1u)] = (uint32_t)id;
@@ -815,7 +834,8 @@ __device__ void query_core(const Geo& g, const QueryLayout& lay, unsigned char* 
     for (uint32_t i = threadIdx.x; i < cmwords / 4; i += T) cm4[i] = make_uint4(0, 0, 0, 0);
   }
   if (threadIdx.x < C_Q) ctrl[threadIdx.x] = 0u;
-  for (uint32_t i = threadIdx.x; i < nbk; i += T) bfill[i] = fill[bkey[i]];
+  for (uint32_t i = threadIdx.x; i < nbk; i += T)
+    bfill[i] = SLASH_BOUND(bkey[i] < ((uint64_t)g.S * g.L << g.B)) ? fill[bkey[i]] : 0u;
   __syncthreads();
   uint32_t* cnts = reinterpret_cast<uint32_t*>(pool);  // scratch: 32-id chunks per bucket
   for (uint32_t i = threadIdx.x; i < nbk; i += T) cnts[i] = (bfill[i] + 31u) >> 5;
@@ -1395,7 +1415,8 @@ __device__ __forceinline__ void staged_prefetch_l2(const Geo& g, const StagedLay
 __device__ __forceinline__ void staged_fills(const Geo& g, const StagedLayout& lay, const uint32_t* __restrict__ fill,
                                              uint32_t lane, const uint32_t (&key)[kPer], uint32_t (&f)[kPer]) {
 #pragma unroll
-  for (int j = 0; j < kPer; ++j) f[j] = lane * kPer + j < lay.nbk ? __ldg(fill + key[j]) : 0u;
+  for (int j = 0; j < kPer; ++j)
+    f[j] = lane * kPer + j < lay.nbk && SLASH_BOUND(key[j] < ((uint64_t)g.S * g.L << g.B)) ? __ldg(fill + key[j]) : 0u;
 }
 
 // Issuing warp: lay the buckets' runs out in the id buffer (bucket order, each
@@ -1545,7 +1566,7 @@ __device__ bool staged_answer(const Geo& g, const StagedLayout& lay, unsigned ch
     const uint32_t* boff = reinterpret_cast<const uint32_t*>(qsm + lay.off_boff);
     const uint32_t ids_s = smem_u32(qsm + lay.off_ids);
     for (uint32_t b = warp; b < lay.nbk; b += (T >> 5)) {
-      const uint32_t o = boff[b], n4 = (boff[b + 1] - o) >> 2;
+      const uint32_t o = boff[b], n4 = SLASH_BOUND(boff[b + 1] <= lay.idcap) ? (boff[b + 1] - o) >> 2 : 0u;
       const uint32_t* src = slots + (uint64_t)bkey[b] * g.R;
       for (uint32_t c = lane; c < n4; c += 32) cp_async16(ids_s + 16u * c + 4u * o, src + 4u * c);
     }
@@ -2022,7 +2043,7 @@ k_query_warp(const __grid_constant__ Geo g, const WarpLayout lay, const uint32_t
       if (i < nbk) {
         const uint32_t t = i % g.L;
         key = (i << g.B) | (kFused ? table_address(g, m, t) : __ldg(qbkt + t * ldq + q));
-        f = min(__ldg(fill + key), g.R);
+        f = SLASH_BOUND(key < ((uint64_t)g.S * g.L << g.B)) ? min(__ldg(fill + key), g.R) : 0u;
       }
       uint32_t inc = f;
 #pragma unroll
@@ -3214,6 +3235,22 @@ int slash_free(slash_index* ix) {
   return cudaGetLastError() == cudaSuccess ? SLASH_OK : SLASH_ECUDA;
 }
 
+int slash_debug_bounds(uint32_t* checked_out, uint32_t* errors_out) {
+  if (!checked_out || !errors_out) return SLASH_EINVAL;
+#ifdef SLASH_CHECKS
+  *checked_out = 1u;
+  uint32_t e = 0u;
+  SLASH_CK(cudaMemcpyFromSymbol(&e, g_bounds_err, sizeof(uint32_t)));
+  const uint32_t z = 0u;
+  SLASH_CK(cudaMemcpyToSymbol(g_bounds_err, &z, sizeof(uint32_t)));
+  *errors_out = e;
+#else
+  *checked_out = 0u;
+  *errors_out = 0u;
+#endif
+  return SLASH_OK;
+}
+
 int slash_set_allocator(slash_index* ix, slash_alloc_fn alloc, slash_free_fn release, void* ctx) {
   if (!ix || (alloc == nullptr) != (release == nullptr)) return SLASH_EINVAL;
   SLASH_CK(cudaDeviceSynchronize());
@@ -3509,7 +3546,7 @@ __device__ uint32_t ex_gather(const Geo& g, const uint32_t* __restrict__ qbkt, u
     const uint32_t s = it / g.L, t = it - s * g.L;
     const uint32_t key = ((s * g.L + t) << g.B) | qbkt[t * ldq + q];
     bk[it] = key;
-    bf[it] = min(fill[key], g.R);
+    bf[it] = SLASH_BOUND(key < ((uint64_t)g.S * g.L << g.B)) ? min(fill[key], g.R) : 0u;
   }
   __syncthreads();
   block_scan_small(bf, bo, nbk, tmp);
