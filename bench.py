@@ -302,9 +302,9 @@ def config_of(w, args) -> dict:
 # the id write), so a full-size launch's traffic is the per-unit figure times
 # its units.
 TRAFFIC_PER_UNIT = {
-    "k_hash_insert": ((347228416 + 457842176) / 2_000_000, "row",
-                      "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_hash_reg<12, 6, 1> on 2M criteo-shaped "
-                      "rows (2^14 buckets), 402.5 B/row, scaled by the rows of the launch"),
+    "k_hash_insert": ((346640384 + 458050304) / 2_000_000, "row",
+                      "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_hash_reg<12, 6, 1, 0> on 2M criteo-shaped "
+                      "rows (2^14 buckets), 402.3 B/row, scaled by the rows of the launch"),
     "k_scatter": ((562054400 + 367997952) / 128_000_000, "pair",
                   "ncu dram__bytes_read.sum + dram__bytes_write.sum of k_scatter on 2M criteo-shaped rows x 64 tables "
                   "(2^14 buckets), 7.27 B/pair, scaled by the (row, table) pairs of the launch"),
@@ -312,7 +312,7 @@ TRAFFIC_PER_UNIT = {
 TRAFFIC_SHAPE = {"K": 6, "L": 64, "reservoir": 128}
 # Warp instructions per row of the insert hash (smsp__inst_executed.sum of a
 # 2M-row ncu capture / 2M; the count per row does not depend on the table size).
-HASH_WARP_INST_PER_ROW = (1094409036 / 2_000_000, "ncu smsp__inst_executed.sum of k_hash_reg<12, 6, 1> on 2M "
+HASH_WARP_INST_PER_ROW = (1094409036 / 2_000_000, "ncu smsp__inst_executed.sum of k_hash_reg<12, 6, 1, 0> on 2M "
                                                    "criteo-shaped rows (2^14 buckets) / 2M")
 
 ALGO_BYTES_DOC = {

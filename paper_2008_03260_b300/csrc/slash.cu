@@ -91,12 +91,12 @@ constexpr int kTileStride = kHashRows + 1;
 
 // Rows [blockIdx.x*32, +32): addresses -> bkt[t*ldb + row] (table-major),
 // optional codes [n][nb], optional per-bucket counts (insert).
-template <bool kCount>
+template <bool kCount, bool kPart>
 __global__ void __launch_bounds__(kHashWarps * 32)
 k_hash(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
        const uint64_t* __restrict__ offs, const uint32_t* __restrict__ cols, uint32_t n, uint64_t id0,
        uint32_t* __restrict__ bkt, uint64_t ldb, uint32_t* __restrict__ codes,
-       uint32_t* __restrict__ cnt, uint32_t* __restrict__ err) {
+       uint32_t* __restrict__ cnt, uint32_t* __restrict__ err, uint32_t t0, uint32_t t1) {
   extern __shared__ uint32_t smem[];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const uint32_t per_warp = (g.nb + g.nw + 3u) & ~3u;  // 16-byte aligned per warp
@@ -117,7 +117,7 @@ k_hash(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
     doph_row(g, cols, b0, b1, m, mask, err, lane);
     uint32_t s = 0;
     if (kCount) s = shard_of(sm, g.S, id0 + r);
-    for (uint32_t t = lane; t < g.L; t += 32) {
+    for (uint32_t t = (kPart ? t0 : 0u) + lane; t < (kPart ? t1 : g.L); t += 32) {
       const uint32_t b = table_address(g, m, t);
       uint32_t out = b;
       if (kCount) {
@@ -133,7 +133,8 @@ k_hash(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
     __syncwarp();
   }
   __syncthreads();
-  for (uint32_t idx = threadIdx.x; idx < g.L * kHashRows; idx += blockDim.x) {
+  for (uint32_t idx = (kPart ? t0 : 0u) * kHashRows + threadIdx.x; idx < (kPart ? t1 : g.L) * kHashRows;
+       idx += blockDim.x) {
     const uint32_t t = idx / kHashRows, lr = idx - t * kHashRows;
     const uint64_t r = row0 + lr;
     if (r < n) __stcs(&bkt[t * ldb + r], tile[t * kTileStride + lr]);
@@ -146,12 +147,12 @@ k_hash(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
 // padded smem row (bin j at j + j/C): with C+1 odd, the 32 lanes' chunk reads
 // hit 32 different banks.  Non-empty bins are recognised by value; the one
 // feature whose hash is 0xFFFFFFFF (it lands in bin nb-1) is flagged apart.
-template <int C, int K, bool kCount>
+template <int C, int K, bool kCount, bool kPart>
 __global__ void __launch_bounds__(kHashWarps * 32, 5)  // five CTAs per SM: 51 registers
 k_hash_reg(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
            const uint64_t* __restrict__ offs, const uint32_t* __restrict__ cols, uint32_t n, uint64_t id0,
            uint32_t* __restrict__ bkt, uint64_t ldb, uint32_t* __restrict__ codes,
-           uint32_t* __restrict__ cnt, uint32_t* __restrict__ err) {
+           uint32_t* __restrict__ cnt, uint32_t* __restrict__ err, uint32_t t0, uint32_t t1) {
   constexpr uint32_t NB = 32u * C, TPL = C / K, ROW = ((NB + 32u + 1u) + 3u) & ~3u;  // padded row + flag
   extern __shared__ uint32_t smem[];
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
@@ -238,6 +239,7 @@ k_hash_reg(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
 #pragma unroll
     for (int tt = 0; tt < TPL; ++tt) {
       const uint32_t t = lane * TPL + tt;
+      if (kPart && (t < t0 || t >= t1)) continue;  // another pass's table
       uint32_t acc = g.st[t];
 #pragma unroll
       for (int j = 0; j < K; ++j) acc = (acc ^ code[tt * K + j]) * kGold32;
@@ -258,7 +260,8 @@ k_hash_reg(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
     __syncwarp();
   }
   __syncthreads();
-  for (uint32_t idx = threadIdx.x; idx < g.L * kHashRows; idx += blockDim.x) {
+  for (uint32_t idx = (kPart ? t0 : 0u) * kHashRows + threadIdx.x; idx < (kPart ? t1 : g.L) * kHashRows;
+       idx += blockDim.x) {
     const uint32_t t = idx / kHashRows, lr = idx - t * kHashRows;
     const uint64_t r = row0 + lr;
     if (r < n) __stcs(&bkt[t * ldb + r], tile[t * kTileStride + lr]);
@@ -2306,14 +2309,21 @@ size_t hash_smem_bytes(const Geo& g) {
 
 void init_hash_kernels(int smem_optin) {
   const int so = smem_optin;
-  cudaFuncSetAttribute(k_hash<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
-  cudaFuncSetAttribute(k_hash<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_hash<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_hash<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_hash<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
 #define SLASH_HATTR(CC, KK)                                                                              \
-  cudaFuncSetAttribute(k_hash_reg<CC, KK, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);    \
-  cudaFuncSetAttribute(k_hash_reg<CC, KK, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
+  cudaFuncSetAttribute(k_hash_reg<CC, KK, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);    \
+  cudaFuncSetAttribute(k_hash_reg<CC, KK, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);     \
+  cudaFuncSetAttribute(k_hash_reg<CC, KK, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, so);
   SLASH_HATTR(12, 6) SLASH_HATTR(12, 4) SLASH_HATTR(8, 8) SLASH_HATTR(8, 4) SLASH_HATTR(4, 4) SLASH_HATTR(16, 8)
 #undef SLASH_HATTR
 }
+
+// The insert's per-bucket counts are updated once per (row, table) and live in
+// L2 under an evict-last hint; when the count array is larger than this, the
+// tables are split into passes whose counts fit (each pass hashes the rows again).
+constexpr uint64_t kCountL2Budget = 72ull << 20;
 
 int launch_hash(const Geo& g, const ShardMap& sm, const uint64_t* offs, const uint32_t* cols, uint32_t n,
                 uint64_t id0, uint32_t* bkt, uint64_t ldb, uint32_t* codes, uint32_t* cnt, uint32_t* err,
@@ -2322,33 +2332,52 @@ int launch_hash(const Geo& g, const ShardMap& sm, const uint64_t* offs, const ui
   const dim3 grid((n + kHashRows - 1) / kHashRows);
   const bool count = cnt != nullptr;
   const uint32_t nb = g.nb, K = g.K;
+  const uint64_t count_bytes = sizeof(uint32_t) * ((uint64_t)g.S * g.L << g.B);
+  const uint32_t passes = count ? (uint32_t)std::min<uint64_t>(g.L, (count_bytes + kCountL2Budget - 1) / kCountL2Budget)
+                                : 1u;
   // register-chunk kernels hold the side rule only
   const uint32_t C = nb % 32u == 0u && !g.densify ? nb / 32u : 0u;
   const size_t rsmem = sizeof(uint32_t) * ((size_t)kHashWarps * (((nb + 33u) + 3u) & ~3u) +
                                            (size_t)g.L * kTileStride);
-#define SLASH_HREG(CC, KK)                                                                                  \
-  if (C == CC && K == KK) {                                                                              \
-    if (count)                                                                                           \
-      k_hash_reg<CC, KK, true><<<grid, kHashWarps * 32, rsmem, st>>>(g, sm, offs, cols, n, id0, bkt, ldb,  \
-                                                                   codes, cnt, err);                     \
-    else                                                                                                 \
-      k_hash_reg<CC, KK, false><<<grid, kHashWarps * 32, rsmem, st>>>(g, sm, offs, cols, n, id0, bkt, ldb, \
-                                                                    codes, nullptr, err);                \
-    return cudaGetLastError() == cudaSuccess ? SLASH_OK : SLASH_ECUDA;                                   \
-  }
-  SLASH_HREG(12, 6)
-  SLASH_HREG(12, 4)
-  SLASH_HREG(8, 8)
-  SLASH_HREG(8, 4)
-  SLASH_HREG(4, 4)
-  SLASH_HREG(16, 8)
-#undef SLASH_HREG
   const size_t smem = hash_smem_bytes(g);
-  if (count)
-    k_hash<true><<<grid, kHashWarps * 32, smem, st>>>(g, sm, offs, cols, n, id0, bkt, ldb, codes, cnt, err);
-  else
-    k_hash<false><<<grid, kHashWarps * 32, smem, st>>>(g, sm, offs, cols, n, id0, bkt, ldb, codes, nullptr, err);
-  return cudaGetLastError() == cudaSuccess ? SLASH_OK : SLASH_ECUDA;
+  for (uint32_t pass = 0; pass < passes; ++pass) {
+    const uint32_t t0 = (uint32_t)((uint64_t)g.L * pass / passes), t1 = (uint32_t)((uint64_t)g.L * (pass + 1) / passes);
+    uint32_t* cd = pass == 0 ? codes : nullptr;  // the codes do not depend on the pass
+    bool done = false;
+#define SLASH_HREG(CC, KK)                                                                                  \
+  if (!done && C == CC && K == KK) {                                                                     \
+    if (count && passes > 1)                                                                             \
+      k_hash_reg<CC, KK, true, true><<<grid, kHashWarps * 32, rsmem, st>>>(g, sm, offs, cols, n, id0, bkt, ldb, \
+                                                                         cd, cnt, err, t0, t1);         \
+    else if (count)                                                                                      \
+      k_hash_reg<CC, KK, true, false><<<grid, kHashWarps * 32, rsmem, st>>>(g, sm, offs, cols, n, id0, bkt,    \
+                                                                          ldb, cd, cnt, err, t0, t1);   \
+    else                                                                                                 \
+      k_hash_reg<CC, KK, false, false><<<grid, kHashWarps * 32, rsmem, st>>>(g, sm, offs, cols, n, id0, bkt,   \
+                                                                           ldb, cd, nullptr, err, t0, t1); \
+    done = true;                                                                                         \
+  }
+    SLASH_HREG(12, 6)
+    SLASH_HREG(12, 4)
+    SLASH_HREG(8, 8)
+    SLASH_HREG(8, 4)
+    SLASH_HREG(4, 4)
+    SLASH_HREG(16, 8)
+#undef SLASH_HREG
+    if (!done) {
+      if (count && passes > 1)
+        k_hash<true, true><<<grid, kHashWarps * 32, smem, st>>>(g, sm, offs, cols, n, id0, bkt, ldb, cd, cnt, err, t0,
+                                                                t1);
+      else if (count)
+        k_hash<true, false><<<grid, kHashWarps * 32, smem, st>>>(g, sm, offs, cols, n, id0, bkt, ldb, cd, cnt, err, t0,
+                                                                 t1);
+      else
+        k_hash<false, false><<<grid, kHashWarps * 32, smem, st>>>(g, sm, offs, cols, n, id0, bkt, ldb, cd, nullptr, err,
+                                                                  t0, t1);
+    }
+    if (cudaGetLastError() != cudaSuccess) return SLASH_ECUDA;
+  }
+  return SLASH_OK;
 }
 
 }  // namespace slash
