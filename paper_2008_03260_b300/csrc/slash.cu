@@ -616,10 +616,21 @@ k_merge_small(const __grid_constant__ Geo g, uint64_t nk, uint32_t cap_c, uint32
         const uint32_t base = (nb - 1u) * step + 1u, c2 = base + lane;
         f = base + __popc(__ballot_sync(0xFFFFFFFFu, lane + 1u < step && c2 < g.R && priority(bs[c2], sp) < pmin));
       }
-      for (uint32_t c = f + lane; c < g.R; c += 32) {
-        const uint32_t id = bs[c];
-        b[c] = id;
-        a[c] = priority(id, sp);  // ascending: the slots are kept in priority order
+      for (uint32_t c0 = f; c0 < g.R; c0 += 128u) {  // four loads in flight per lane
+        uint32_t idv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t c = c0 + lane + 32u * i;
+          idv[i] = c < g.R ? bs[c] : 0u;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t c = c0 + lane + 32u * i;
+          if (c < g.R) {
+            b[c] = idv[i];
+            a[c] = priority(idv[i], sp);  // ascending: the slots are kept in priority order
+          }
+        }
       }
       __syncwarp();
       for (uint32_t c0 = f; c0 < g.R; c0 += 32) {
