@@ -440,6 +440,7 @@ k_scatter(const __grid_constant__ Geo g, const __grid_constant__ ShardMap sm,
 // ----------------------------------------------------------------------------- insert: merge
 constexpr int kMergeWarps = 16;
 constexpr uint32_t kSmallMax = 1024;  // most candidates a warp merges in smem (buffer size is per index)
+constexpr uint32_t kBigMinNew = 64;   // a bucket merged by a CTA has more than this many new ids
 constexpr uint32_t kInvMul2 = 0x7ED1B41Du;  // 0xC2B2AE35^-1 mod 2^31
 constexpr uint32_t kInvMul1 = 0x25CB9243u;  // 0x85EBCA6B^-1 mod 2^31
 
@@ -2602,7 +2603,7 @@ uint64_t insert_chunk_rows(const slash_index* ix) {
 int grow_insert_ws(slash_index* ix, uint64_t rows) {
   if (rows <= ix->ws_rows) return SLASH_OK;
   const uint64_t L = ix->p.L;
-  const uint64_t big_cap = (L * rows) / (kSmallMax / 2) + 1;  // > 512 survivors per big bucket
+  const uint64_t big_cap = (L * rows) / kBigMinNew + 1;  // a big bucket stages > kBigMinNew ids
   const uint64_t fb_cap = std::min<uint64_t>(ix->nk, L * rows);
   uint32_t *bkt = nullptr, *stage = nullptr, *big = nullptr, *fb = nullptr, *fboff = nullptr, *fbcur = nullptr;
   cudaError_t e = ws_malloc(ix, (void**)&bkt, sizeof(uint32_t) * L * rows);
@@ -2749,10 +2750,20 @@ int insert_tail(slash_index* ix, uint32_t n, uint64_t id0, cudaStream_t st) {
   }
   SLASH_CK(cudaMemsetAsync(ix->ctr, 0, 2 * sizeof(uint32_t), st));
   const uint64_t mblocks = std::min<uint64_t>((nk + kMergeWarps - 1) / kMergeWarps, (uint64_t)ix->num_sms * 16);
-  const size_t msmem = sizeof(uint32_t) * ((size_t)kMergeWarps * 2 * ix->merge_cap + kMergeWarps * 32);
+  // The warps' buffers are sized for this chunk: R old ids plus the new ids a
+  // bucket gets beyond its mean by a wide margin (a bucket above it takes the
+  // CTA merge, which needs more than kBigMinNew new ids: the big list's bound).
+  // Smaller buffers keep more merge warps resident on each SM.
+  uint32_t cap = 64;
+  {
+    const double mu_c = (double)n / ((double)ix->p.shards * (double)(1ull << ix->p.log2_buckets));
+    const double want = (double)ix->p.reservoir + mu_c + 8.0 * std::sqrt(mu_c) + 17.0;
+    while ((cap < want || cap < ix->p.reservoir + kBigMinNew + 1u) && cap < ix->merge_cap) cap <<= 1;
+  }
+  const size_t msmem = sizeof(uint32_t) * ((size_t)kMergeWarps * 2 * cap + kMergeWarps * 32);
   {
     Launch l(ix, "k_merge_small", st);
-    k_merge_small<<<(uint32_t)mblocks, kMergeWarps * 32, msmem, st>>>(ix->geo, nk, ix->merge_cap, ix->cnt, ix->meta,
+    k_merge_small<<<(uint32_t)mblocks, kMergeWarps * 32, msmem, st>>>(ix->geo, nk, cap, ix->cnt, ix->meta,
                                                                       ix->stage, ix->slots, ix->fill, ix->big,
                                                                       ix->ctr, ix->fb, ix->ctr + 1);
   }
