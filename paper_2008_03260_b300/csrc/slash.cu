@@ -585,82 +585,6 @@ k_merge_small(const __grid_constant__ Geo g, uint64_t nk, uint32_t cap_c, uint32
     }
     if (lane == 0) meta[key].w = 0u;
     if (got == 0) continue;  // nothing below the threshold: the bucket is unchanged
-    if (fold == g.R && got <= 32u && g.R <= cap_c) {
-      // A full bucket taking a few new ids (the usual case of later inserts): the
-      // new ids, one per lane, are sorted by priority; each old id moves up by the
-      // new ids below it (leaving past R), each new id lands after the old ids
-      // below it.  Only the slots that change are written; the fill stays R.
-      uint32_t nid = kEmpty, np = 0xFFFFFFFFu;  // priorities are < 2^31: empty lanes sort last
-      if (lane < got) {
-        nid = stage[lo + lane];
-        np = priority(nid, sp);
-      }
-#pragma unroll
-      for (uint32_t k2 = 2; k2 <= 32u; k2 <<= 1)
-#pragma unroll
-        for (uint32_t j = k2 >> 1; j > 0; j >>= 1) {
-          const uint32_t op = __shfl_xor_sync(0xFFFFFFFFu, np, j), oi = __shfl_xor_sync(0xFFFFFFFFu, nid, j);
-          const bool take_min = ((lane & j) == 0u) == ((lane & k2) == 0u);
-          if (take_min ? op < np : op > np) {
-            np = op;
-            nid = oi;
-          }
-        }
-      // f = old slots below the smallest new priority (they stay): one sample per
-      // lane every `step` slots, then the one segment that holds the boundary
-      const uint32_t pmin = __shfl_sync(0xFFFFFFFFu, np, 0);
-      const uint32_t step = (g.R + 31u) >> 5;
-      const uint32_t cs = lane * step;
-      const uint32_t nb = __popc(__ballot_sync(0xFFFFFFFFu, cs < g.R && priority(bs[cs], sp) < pmin));
-      uint32_t f = 0;
-      if (nb > 0u) {
-        const uint32_t base = (nb - 1u) * step + 1u, c2 = base + lane;
-        f = base + __popc(__ballot_sync(0xFFFFFFFFu, lane + 1u < step && c2 < g.R && priority(bs[c2], sp) < pmin));
-      }
-      for (uint32_t c0 = f; c0 < g.R; c0 += 128u) {  // four loads in flight per lane
-        uint32_t idv[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const uint32_t c = c0 + lane + 32u * i;
-          idv[i] = c < g.R ? bs[c] : 0u;
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const uint32_t c = c0 + lane + 32u * i;
-          if (c < g.R) {
-            b[c] = idv[i];
-            a[c] = priority(idv[i], sp);  // ascending: the slots are kept in priority order
-          }
-        }
-      }
-      __syncwarp();
-      for (uint32_t c0 = f; c0 < g.R; c0 += 32) {
-        const uint32_t c = c0 + lane;
-        const uint32_t op = c < g.R ? a[c] : 0xFFFFFFFFu;
-        uint32_t l0 = 0, h0 = got;  // new priorities below op (lanes 0..got-1, ascending)
-#pragma unroll
-        for (int it = 0; it < 6; ++it) {
-          const uint32_t mid = (l0 + h0) >> 1;
-          const uint32_t v = __shfl_sync(0xFFFFFFFFu, np, mid & 31u);
-          if (l0 < h0) {
-            if (v < op) l0 = mid + 1u;
-            else h0 = mid;
-          }
-        }
-        if (c < g.R && l0 > 0u && c + l0 < g.R) bs[c + l0] = b[c];
-      }
-      if (lane < got) {
-        uint32_t l0 = f, h0 = g.R;  // old priorities below np (all of [0, f) are)
-        while (l0 < h0) {
-          const uint32_t mid = (l0 + h0) >> 1;
-          if (a[mid] < np) l0 = mid + 1u;
-          else h0 = mid;
-        }
-        if (lane + l0 < g.R) bs[lane + l0] = nid;
-      }
-      __syncwarp();
-      continue;
-    }
     const uint32_t tot = fold + got;
     if (tot > cap_c) {
       if (lane == 0) {
