@@ -367,7 +367,13 @@ def main():
     ap.add_argument("--serve-max-requests", type=int, default=100_000)
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-max-batch", type=int, default=4096)
-    ap.add_argument("--serve-rates", default="1000,10000,30000")
+    ap.add_argument("--serve-rates", default="1000,10000,30000,100000")
+    ap.add_argument("--serve-reserve-sms", type=int, default=0,
+                    help="SMs the native loop's large batches leave to batches of few queries")
+    ap.add_argument("--serve-small-queries", type=int, default=0,
+                    help="largest batch the native loop runs on its high-priority streams")
+    ap.add_argument("--no-serve-python", action="store_true",
+                    help="serve through the native loop only (skip the Python loop's comparison run)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--probe", action="store_true", help="print the shared-memory microbenchmark line and exit")
     args = ap.parse_args()
@@ -704,25 +710,34 @@ def bench_serving(args, w: workloads.Workload) -> dict:
         reqs = poisson_requests(float(rate), n_req, qo, qc, seed=rate)
         with Clocks(0) as clk:  # the library's native loop
             _, summ = serve_native(reqs, ix, topk=w.topk, slots=args.serve_slots,
-                                   max_batch_queries=args.serve_max_batch, mode=sched["mode"])
+                                   max_batch_queries=args.serve_max_batch, mode=sched["mode"],
+                                   reserve_sms=args.serve_reserve_sms, small_queries=args.serve_small_queries)
         summ["clocks"] = clk.summary()
-        ex = GpuExecutor(ix, topk=w.topk, slots=args.serve_slots, mode=sched["mode"], threads=sched["threads"])
-        with Clocks(0) as clk:  # the same stream through the Python loop, for comparison
-            _, py = serve(reqs, ex, topk=w.topk, slots=args.serve_slots, mem_budget=16 << 30,
-                          max_batch_queries=args.serve_max_batch)
-        py["clocks"] = clk.summary()
-        summ["python_loop"] = py
+        # the load offered: all queries over the arrival span (above the sustained rate = saturated)
+        summ["offered_queries_per_s"] = sum(r.nq for r in reqs) / max(r.arrival for r in reqs)
+        if not args.no_serve_python:
+            ex = GpuExecutor(ix, topk=w.topk, slots=args.serve_slots, mode=sched["mode"], threads=sched["threads"])
+            with Clocks(0) as clk:  # the same stream through the Python loop, for comparison
+                _, py = serve(reqs, ex, topk=w.topk, slots=args.serve_slots, mem_budget=16 << 30,
+                              max_batch_queries=args.serve_max_batch)
+            py["clocks"] = clk.summary()
+            summ["python_loop"] = py
         per_rate[str(rate)] = summ
         log(f"[bench] serving {rate} req/s: {summ}")
     ix.close()
-    top = per_rate[str(rates[-1])]
+    # value: the most queries/s sustained at any rate (at an offered load above it: the
+    # capacity); ms_per_step: the p50 at the highest rate the loop keeps up with
+    best = max(per_rate.values(), key=lambda v: v["queries_per_s"])
+    kept = [v for v in per_rate.values() if v["queries_per_s"] >= 0.95 * v["offered_queries_per_s"]]
+    top = kept[-1] if kept else per_rate[str(rates[0])]
     return {"metric": "serving p50/p99 ms and sustained queries/s (native continuous batching, 8 shards)",
-            "value": top["queries_per_s"], "unit": "queries/s", "n_gpus": 1, "steps": len(rates),
+            "value": best["queries_per_s"], "unit": "queries/s", "n_gpus": 1, "steps": len(rates),
             "warmup": 0, "ms_per_step": top["p50_ms"], "higher_is_better": True, "scaling": "weak",
+            "p50_p99_ms": {r: [round(v["p50_ms"], 4), round(v["p99_ms"], 4)] for r, v in per_rate.items()},
             "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": config_of(w, args),
             "schedule": sched, "schedule_ms_per_65536_queries": timings, "slots": args.serve_slots,
-            "max_batch_queries": args.serve_max_batch,
-            "rates": per_rate}
+            "max_batch_queries": args.serve_max_batch, "reserve_sms": args.serve_reserve_sms,
+            "small_queries": args.serve_small_queries, "rates": per_rate}
 
 
 def bench_exchange(args, w: workloads.Workload) -> dict:

@@ -149,6 +149,10 @@ typedef struct {
   uint32_t threads;      /* threads per CTA (team): 256, 512 or 1024 (0 = the index's default);
                             the warp schedules always run 8 warps per CTA                             */
   uint32_t ctas_per_sm;  /* cap on resident CTAs per SM (0 = as many as fit)                          */
+  uint32_t max_sms;      /* the launch's persistent CTAs fill at most this many SMs' worth of slots
+                            (grid <= max_sms x resident CTAs per SM), leaving the rest of the GPU to
+                            work on other streams; 0 or >= the SM count = the whole GPU.  The answers
+                            do not depend on it                                                       */
 } slash_query_opts;
 
 /* slash_query with an explicit schedule (opts == NULL: the index's default,

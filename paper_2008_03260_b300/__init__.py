@@ -58,11 +58,13 @@ _MODES = {"fused": SLASH_QUERY_FUSED, "plain": SLASH_QUERY_PLAIN, "warp_fused": 
 
 
 class slash_query_opts(ctypes.Structure):
-    _fields_ = [("mode", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
+    _fields_ = [("mode", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("max_sms", ctypes.c_uint32)]
 
     def __repr__(self):
         m = {v: k for k, v in _MODES.items()}.get(self.mode, str(self.mode))
-        return f"slash_query_opts({m}, threads={self.threads}, ctas_per_sm={self.ctas_per_sm})"
+        return (f"slash_query_opts({m}, threads={self.threads}, ctas_per_sm={self.ctas_per_sm}, "
+                f"max_sms={self.max_sms})")
 
 
 # the allocator hook's callback types (include/slash.h)
@@ -72,8 +74,8 @@ SLASH_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 class slash_serve_opts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_uint32), ("max_batch_queries", ctypes.c_uint32), ("topk", ctypes.c_uint32),
-                ("mode", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
-                ("timeout_s", ctypes.c_double)]
+                ("mode", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("reserve_sms", ctypes.c_uint32),
+                ("small_queries", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("timeout_s", ctypes.c_double)]
 
 
 class slash_params(ctypes.Structure):
@@ -124,7 +126,7 @@ def _load() -> ctypes.CDLL:
         "slash_query_ex": (i32, [vp, vp, vp, u32, u32, vp, vp, P(slash_query_opts), vp]),
         "slash_autotune": (i32, [vp, vp, vp, u32, u32, vp, vp, vp, P(slash_query_opts), P(ctypes.c_float)]),
         "slash_query_static": (i32, [vp, vp, vp, u32, u32, vp, vp, vp]),
-        "slash_serve": (i32, [vp, P(slash_serve_opts), u32, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "slash_serve": (i32, [vp, P(slash_serve_opts), u32, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         "slash_set_allocator": (i32, [vp, SLASH_ALLOC_FN, SLASH_FREE_FN, vp]),
         "slash_debug_bounds": (i32, [P(u32), P(u32)]),
         "slash_profile": (i32, [vp, i32]),
@@ -243,20 +245,20 @@ def slash_insert_host(ix: int, h_offs: torch.Tensor, h_cols: torch.Tensor, strea
     return int(first.value)
 
 
-def _opts(mode, threads, ctas_per_sm):
+def _opts(mode, threads, ctas_per_sm, max_sms=0):
     if mode is None:
         return None
     m = _MODES.get(mode, mode)
-    return slash_query_opts(int(m), int(threads or 0), int(ctas_per_sm or 0))
+    return slash_query_opts(int(m), int(threads or 0), int(ctas_per_sm or 0), int(max_sms or 0))
 
 
 def slash_query(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, topk: int,
                 d_ids_out: torch.Tensor | None = None, d_scores_out: torch.Tensor | None = None,
-                stream=None, mode=None, threads: int = 0, ctas_per_sm: int = 0
+                stream=None, mode=None, threads: int = 0, ctas_per_sm: int = 0, max_sms: int = 0
                 ) -> tuple[torch.Tensor, torch.Tensor]:
     """Algorithm 2 for a batch.  ``mode`` None = the index's default schedule,
     else "fused" / "plain" / "warp_fused" / "warp_plain" (with optional
-    ``threads`` and ``ctas_per_sm``)."""
+    ``threads``, ``ctas_per_sm`` and ``max_sms``)."""
     nq = d_offs.numel() - 1
     if nq < 0:
         raise ValueError("d_offs needs n+1 entries")
@@ -267,7 +269,7 @@ def slash_query(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, topk: int,
         d_scores_out = torch.empty((nq, topk), dtype=torch.int32, device=dev)
     if d_ids_out.numel() < nq * topk or d_scores_out.numel() < nq * topk:
         raise ValueError("output tensors too small")
-    o = _opts(mode, threads, ctas_per_sm)
+    o = _opts(mode, threads, ctas_per_sm, max_sms)
     args = (ix, _dev_ptr(d_offs, 8, "d_offs"), _dev_ptr(d_cols, 4, "d_cols"), nq, topk,
             _dev_ptr(d_ids_out, 4, "d_ids_out"), _dev_ptr(d_scores_out, 4, "d_scores_out"))
     if o is None:
@@ -292,12 +294,13 @@ def slash_autotune(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, topk: in
 
 
 def slash_serve(ix: int, arrival_s, req_q, offs, cols, topk: int, *, slots: int = 4,
-                max_batch_queries: int = 8192, mode="fused", threads: int = 0, timeout_s: float = 0.0):
+                max_batch_queries: int = 8192, mode="fused", threads: int = 0, timeout_s: float = 0.0,
+                reserve_sms: int = 0, small_queries: int = 0):
     """The native serving loop (include/slash_serve.h) over host arrays:
     arrival_s float64 [n], req_q uint64 [n+1] (request i = queries
     [req_q[i], req_q[i+1])), the queries' CSR offs uint64 / cols uint32.
     Returns (ids int32 [Q][topk], scores uint32 [Q][topk], launched_s, done_s,
-    status int32), one time and status per request."""
+    status int32, device_s), one time, status and batch device span per request."""
     import numpy as np
     arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
     rq = np.ascontiguousarray(req_q, dtype=np.uint64)
@@ -312,11 +315,13 @@ def slash_serve(ix: int, arrival_s, req_q, offs, cols, topk: int, *, slots: int 
     launched = np.empty(n, dtype=np.float64)
     done = np.empty(n, dtype=np.float64)
     status = np.empty(n, dtype=np.int32)
-    o = slash_serve_opts(slots, max_batch_queries, topk, _MODES.get(mode, mode), threads, 0, timeout_s)
+    device = np.empty(n, dtype=np.float64)
+    o = slash_serve_opts(slots, max_batch_queries, topk, _MODES.get(mode, mode), threads, reserve_sms,
+                         small_queries, 0, timeout_s)
     ptr = lambda a: a.ctypes.data if a.size else None
     _check(_lib.slash_serve(ix, ctypes.byref(o), n, ptr(arr), rq.ctypes.data, of.ctypes.data, ptr(co), ptr(ids),
-                            ptr(sc), ptr(launched), ptr(done), ptr(status)), "slash_serve")
-    return ids, sc, launched, done, status
+                            ptr(sc), ptr(launched), ptr(done), ptr(status), ptr(device)), "slash_serve")
+    return ids, sc, launched, done, status, device
 
 
 def slash_set_allocator(ix: int, alloc=None, release=None) -> None:

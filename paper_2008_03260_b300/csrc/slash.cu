@@ -2364,7 +2364,7 @@ struct slash_index {
   // query workspace (grow-only)
   uint64_t qws = 0;
   uint32_t* qbkt = nullptr;
-  slash_query_opts qdef{SLASH_QUERY_FUSED, 512, 0};  // default query schedule (autotuned)
+  slash_query_opts qdef{SLASH_QUERY_FUSED, 512, 0, 0};  // default query schedule (autotuned)
   uint32_t* work = nullptr;                          // ring of fused-kernel work counters
   int qbps[2][3] = {};                               // CTAs/SM per (mode, threads); -1 = does not fit
   int sbps[2][3] = {};                               // the same for the staged engine
@@ -2745,10 +2745,10 @@ const void* staged_fn(bool fused, uint32_t thr, uint32_t d) {
 
 // k_query_redo over a batch whose first output ids mark the queries left to it.
 int launch_redo(slash_index* ix, const uint64_t* offs, const uint32_t* cols, uint32_t n, uint32_t topk, int32_t* ids,
-                uint32_t* scores, cudaStream_t st) {
+                uint32_t* scores, uint32_t sms, cudaStream_t st) {
   const uint32_t rt = ix->redo_threads;
   const QueryLayout rl = make_query_layout(ix->p, rt);
-  const uint32_t rgrid = (uint32_t)std::min<uint64_t>((n + rt - 1) / rt, (uint64_t)ix->num_sms);
+  const uint32_t rgrid = (uint32_t)std::min<uint64_t>((n + rt - 1) / rt, (uint64_t)sms);
   {
     Launch lr(ix, "k_query_redo", st);
 #define SLASH_REDO(T) \
@@ -2781,9 +2781,9 @@ bool warp_ok(const slash_index* ix, uint32_t topk) {
 
 // The warp engine on n queries (rows offs[0..n] of cols), then k_query_redo for
 // the queries it left to the general kernel.
-int launch_warp(slash_index* ix, bool fused, uint32_t ctas_cap, const uint64_t* offs, const uint32_t* cols,
-                const uint32_t* qbkt, uint64_t ldq, uint32_t n, uint32_t topk, int32_t* ids, uint32_t* scores,
-                cudaStream_t st) {
+int launch_warp(slash_index* ix, bool fused, uint32_t ctas_cap, uint32_t sms, const uint64_t* offs,
+                const uint32_t* cols, const uint32_t* qbkt, uint64_t ldq, uint32_t n, uint32_t topk, int32_t* ids,
+                uint32_t* scores, cudaStream_t st) {
   const WarpLayout lay = make_warp_layout(ix->p);
   const size_t smem = (size_t)kWarpWarps * lay.per_warp * 4u;
   const void* fn = fused ? (const void*)k_query_warp<true> : (const void*)k_query_warp<false>;
@@ -2793,8 +2793,7 @@ int launch_warp(slash_index* ix, bool fused, uint32_t ctas_cap, const uint64_t* 
   if (bps < 1) return SLASH_EINVAL;
   if (ctas_cap) bps = std::min<int>(bps, (int)ctas_cap);
   const uint64_t blocks = ((uint64_t)n + 31u) / 32u;  // a warp takes 32 queries at a time
-  const uint32_t grid = (uint32_t)std::min<uint64_t>((blocks + kWarpWarps - 1) / kWarpWarps,
-                                                     (uint64_t)ix->num_sms * bps);
+  const uint32_t grid = (uint32_t)std::min<uint64_t>((blocks + kWarpWarps - 1) / kWarpWarps, (uint64_t)sms * bps);
   uint32_t* work = ix->work + (ix->work_next.fetch_add(1u) % kWorkRing);
   SLASH_CK(cudaMemsetAsync(work, 0, sizeof(uint32_t), st));
   {
@@ -2807,7 +2806,7 @@ int launch_warp(slash_index* ix, bool fused, uint32_t ctas_cap, const uint64_t* 
                                                               ix->slots, ix->fill, ids, scores, work, ix->err);
   }
   SLASH_CK(cudaGetLastError());
-  return launch_redo(ix, offs, cols, n, topk, ids, scores, st);
+  return launch_redo(ix, offs, cols, n, topk, ids, scores, sms, st);
 }
 
 // Teams of `thr` threads per staged CTA: one, or with a four-row sketch (one CTA
@@ -2821,7 +2820,7 @@ uint32_t staged_teams(const slash_index* ix, uint32_t thr, const StagedLayout& l
 // The staged engine on n queries (rows offs[0..n] of cols): fused (each CTA
 // hashes its queries) or plain (addresses qbkt[t*ldq + q] from the hash
 // kernel), then k_query_redo for the queries it left marked.
-int launch_staged(slash_index* ix, bool fused, uint32_t thr, uint32_t ctas_cap, const uint64_t* offs,
+int launch_staged(slash_index* ix, bool fused, uint32_t thr, uint32_t ctas_cap, uint32_t sms, const uint64_t* offs,
                   const uint32_t* cols, const uint32_t* qbkt, uint64_t ldq, uint32_t n, uint32_t topk, int32_t* ids,
                   uint32_t* scores, cudaStream_t st) {
   StagedLayout lay = make_staged_layout(ix->p);
@@ -2858,7 +2857,7 @@ int launch_staged(slash_index* ix, bool fused, uint32_t thr, uint32_t ctas_cap, 
   if (bps < 1) return SLASH_EINVAL;
   if (ctas_cap) bps = std::min<int>(bps, (int)ctas_cap);
   const uint64_t teams_needed = (n + 0ull + teams - 1) / teams;
-  const uint32_t grid = (uint32_t)std::min<uint64_t>(teams_needed, (uint64_t)ix->num_sms * bps);
+  const uint32_t grid = (uint32_t)std::min<uint64_t>(teams_needed, (uint64_t)sms * bps);
   const size_t smem = (size_t)teams * lay.bytes;
   // a private counter per launch: launches on different streams may overlap
   uint32_t* work = ix->work + (ix->work_next.fetch_add(1u) % kWorkRing);
@@ -2874,7 +2873,7 @@ int launch_staged(slash_index* ix, bool fused, uint32_t thr, uint32_t ctas_cap, 
                     (void*)&err};
     SLASH_CK(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, st));
   }
-  return launch_redo(ix, offs, cols, n, topk, ids, scores, st);
+  return launch_redo(ix, offs, cols, n, topk, ids, scores, sms, st);
 }
 
 bool params_ok(const slash_params* p) {
@@ -3138,9 +3137,11 @@ int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
   if (n_queries == 0) return SLASH_OK;
   if (!d_offs || !d_cols || !d_ids_out || !d_scores_out) return SLASH_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
+  // SMs the launch's persistent CTAs may fill (the rest stay free for other streams' work)
+  const uint32_t sms = o.max_sms && o.max_sms < ix->num_sms ? o.max_sms : ix->num_sms;
   if (warp_mode) {
     if (o.mode == SLASH_QUERY_WARP_FUSED)
-      return launch_warp(ix, true, o.ctas_per_sm, d_offs, d_cols, nullptr, 0, n_queries, topk, d_ids_out,
+      return launch_warp(ix, true, o.ctas_per_sm, sms, d_offs, d_cols, nullptr, 0, n_queries, topk, d_ids_out,
                          d_scores_out, st);
     const uint64_t chunk = std::min<uint64_t>(n_queries, 1ull << 22);
     int rc = grow_query_ws(ix, chunk);
@@ -3149,7 +3150,7 @@ int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
       const uint32_t n = (uint32_t)std::min<uint64_t>(chunk, n_queries - q0);
       rc = run_hash(ix, d_offs + q0, d_cols, n, 0, ix->qbkt, n, nullptr, false, st);
       if (rc) return rc;
-      rc = launch_warp(ix, false, o.ctas_per_sm, d_offs + q0, d_cols, ix->qbkt, n, n, topk, d_ids_out + q0 * topk,
+      rc = launch_warp(ix, false, o.ctas_per_sm, sms, d_offs + q0, d_cols, ix->qbkt, n, n, topk, d_ids_out + q0 * topk,
                        d_scores_out + q0 * topk, st);
       if (rc) return rc;
     }
@@ -3157,7 +3158,7 @@ int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
   }
   if (ix->staged && topk <= kLocalTop) {
     if (o.mode == SLASH_QUERY_FUSED)
-      return launch_staged(ix, true, thr, o.ctas_per_sm, d_offs, d_cols, nullptr, 0, n_queries, topk, d_ids_out,
+      return launch_staged(ix, true, thr, o.ctas_per_sm, sms, d_offs, d_cols, nullptr, 0, n_queries, topk, d_ids_out,
                            d_scores_out, st);
     const uint64_t chunk = std::min<uint64_t>(n_queries, 1ull << 22);
     int rc = grow_query_ws(ix, chunk);
@@ -3166,7 +3167,7 @@ int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
       const uint32_t n = (uint32_t)std::min<uint64_t>(chunk, n_queries - q0);
       rc = run_hash(ix, d_offs + q0, d_cols, n, 0, ix->qbkt, n, nullptr, false, st);
       if (rc) return rc;
-      rc = launch_staged(ix, false, thr, o.ctas_per_sm, d_offs + q0, d_cols, ix->qbkt, n, n, topk,
+      rc = launch_staged(ix, false, thr, o.ctas_per_sm, sms, d_offs + q0, d_cols, ix->qbkt, n, n, topk,
                          d_ids_out + q0 * topk, d_scores_out + q0 * topk, st);
       if (rc) return rc;
     }
@@ -3187,7 +3188,7 @@ int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
   SLASH_CK_RC(cached_bps(ix->qbps[o.mode == SLASH_QUERY_PLAIN ? 1 : 0][ti], fn, thr, lay.bytes, &bps));
   if (bps < 1) return SLASH_EINVAL;
   if (o.ctas_per_sm) bps = std::min<int>(bps, (int)o.ctas_per_sm);
-  const uint64_t slots_per_gpu = (uint64_t)ix->num_sms * bps;
+  const uint64_t slots_per_gpu = (uint64_t)sms * bps;
   if (o.mode == SLASH_QUERY_FUSED) {
     const uint32_t grid = (uint32_t)std::min<uint64_t>(n_queries, slots_per_gpu);
     // a private counter per launch: fused launches on different streams may overlap
@@ -3236,14 +3237,14 @@ int slash_autotune(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
   cudaEvent_t a, b;
   SLASH_CK(cudaEventCreate(&a));
   SLASH_CK(cudaEventCreate(&b));
-  slash_query_opts best{SLASH_QUERY_FUSED, 512, 0};
+  slash_query_opts best{SLASH_QUERY_FUSED, 512, 0, 0};
   float best_ms = 3.4e38f;
   int rc = SLASH_OK;
   for (uint32_t m : modes) {
     for (uint32_t t : threads) {
       if (m >= SLASH_QUERY_WARP_FUSED && t != 256u) continue;  // the warp schedules have one CTA shape
       for (uint32_t cps = 0; cps <= 1; ++cps) {  // 0 = as many CTAs per SM as fit, 1 = one
-        slash_query_opts o{m, t, cps};
+        slash_query_opts o{m, t, cps, 0u};
         float ms = 3.4e38f;
         for (int rep = 0; rep < 3 && rc == SLASH_OK; ++rep) {
           cudaEventRecord(a, st);
@@ -3542,7 +3543,7 @@ extern "C" int slash_query_static(slash_index* ix, const uint64_t* d_offs, const
   if (ix->staged && topk <= kLocalTop) {
     rc = run_hash(ix, d_offs, d_cols, n_queries, 0, qbkt, n_queries, nullptr, false, st);
     if (rc) return rc;
-    return launch_staged(ix, false, 512u, 0u, d_offs, d_cols, qbkt, n_queries, n_queries, topk, d_ids_out,
+    return launch_staged(ix, false, 512u, 0u, ix->num_sms, d_offs, d_cols, qbkt, n_queries, n_queries, topk, d_ids_out,
                          d_scores_out, st);
   }
   const QueryLayout lay = make_query_layout(ix->p, 512u);

@@ -1,7 +1,8 @@
 // Native serving loop over a SLASH index (include/slash_serve.h): real-time
-// admission, batching of whole requests in arrival order, and one CUDA stream
-// per slot carrying a batch's copy in, query (Algorithm 2) and copy back.
-// Host code only; the query is the library's own slash_query_ex.
+// admission, batching of whole requests in arrival order, and per slot two CUDA
+// streams (high priority for batches of few queries, low for the rest) carrying
+// a batch's copy in, query (Algorithm 2) and copy back.  Host code only; the
+// query is the library's own slash_query_ex.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,13 +20,24 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// One turn of a polling loop: a pause hint to the core (x86), no system call.
+inline void spin_pause() {
+#if defined(__x86_64__) && !defined(__CUDA_ARCH__)
+  __builtin_ia32_pause();
+#else
+  std::this_thread::yield();
+#endif
+}
+
 // Byte offset of a batch's features in the slot's input buffer: after its
 // nq + 1 offsets, rounded up to 16 bytes.
 inline size_t cols_at(uint64_t nq) { return (8u * (nq + 1u) + 15u) & ~size_t(15); }
 
 struct Slot {
-  cudaStream_t st = nullptr;
-  cudaEvent_t ev = nullptr;
+  cudaStream_t st = nullptr;     // low priority: batches of more than small_queries queries
+  cudaStream_t st_hi = nullptr;  // high priority: the small ones
+  cudaEvent_t ev0 = nullptr;  // before the batch's copy in
+  cudaEvent_t ev = nullptr;   // after its copy back
   unsigned char* h_in = nullptr;   // page-locked: offsets, then features
   unsigned char* d_in = nullptr;
   unsigned char* h_out = nullptr;  // page-locked: ids [nq][k], then scores [nq][k]
@@ -37,19 +49,34 @@ struct Slot {
 
 struct Slots {
   std::vector<Slot> s;
-  cudaEvent_t ref = nullptr;
+  std::vector<void*> pinned;  // caller arrays page-locked for the call
+  // Page-lock [p, p + bytes) of a caller's array for the call: its batches are
+  // then copied straight from (or into) it.  False (nothing locked) if CUDA declines.
+  bool pin(const void* p, size_t bytes) {
+    if (!p || bytes == 0) return false;
+    if (cudaHostRegister(const_cast<void*>(p), bytes, cudaHostRegisterDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    pinned.push_back(const_cast<void*>(p));
+    return true;
+  }
   ~Slots() {
-    for (Slot& x : s)
+    for (Slot& x : s) {
       if (x.st) cudaStreamSynchronize(x.st);
+      if (x.st_hi) cudaStreamSynchronize(x.st_hi);
+    }
     for (Slot& x : s) {
       if (x.h_in) cudaFreeHost(x.h_in);
       if (x.h_out) cudaFreeHost(x.h_out);
       if (x.d_in) cudaFree(x.d_in);
       if (x.d_out) cudaFree(x.d_out);
       if (x.ev) cudaEventDestroy(x.ev);
+      if (x.ev0) cudaEventDestroy(x.ev0);
       if (x.st) cudaStreamDestroy(x.st);
+      if (x.st_hi) cudaStreamDestroy(x.st_hi);
     }
-    if (ref) cudaEventDestroy(ref);
+    for (void* p : pinned) cudaHostUnregister(p);
   }
 };
 
@@ -57,10 +84,12 @@ struct Slots {
 
 extern "C" int slash_serve(slash_index* ix, const slash_serve_opts* o, uint32_t n, const double* arrival,
                            const uint64_t* req_q, const uint64_t* offs, const uint32_t* cols, int32_t* ids_out,
-                           uint32_t* scores_out, double* launched_s, double* done_s, int32_t* status) {
+                           uint32_t* scores_out, double* launched_s, double* done_s, int32_t* status,
+                           double* device_s) {
   if (!ix || !o) return SLASH_EINVAL;
   if (o->slots < 1u || o->slots > 16u || o->max_batch_queries < 1u || o->topk < 1u || o->topk > SLASH_MAX_TOPK ||
-      (o->mode != SLASH_QUERY_FUSED && o->mode != SLASH_QUERY_WARP_FUSED) || o->reserved != 0u)
+      (o->mode != SLASH_QUERY_FUSED && o->mode != SLASH_QUERY_WARP_FUSED) || o->reserved != 0u ||
+      (o->reserve_sms != 0u && o->small_queries == 0u))
     return SLASH_EINVAL;
   if (n == 0u) return SLASH_OK;
   if (!arrival || !req_q || !offs || !ids_out || !scores_out || !launched_s || !done_s || !status)
@@ -90,11 +119,21 @@ extern "C" int slash_serve(slash_index* ix, const slash_serve_opts* o, uint32_t 
   const size_t in_bytes = cols_at(most_q) + 4u * std::max<uint64_t>(most_nnz, 1u);
   const size_t out_bytes = 8u * std::max<uint64_t>(most_q, 1u) * k;
 
+  int dev = 0, num_sms = 0, prio_lo = 0, prio_hi = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) {
+    cudaGetLastError();
+    return SLASH_ECUDA;
+  }
+  if (o->reserve_sms >= (uint32_t)num_sms) return SLASH_EINVAL;
+
   Slots sl;
   sl.s.resize(o->slots);
   for (Slot& x : sl.s) {
-    if (cudaStreamCreateWithFlags(&x.st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreate(&x.ev) != cudaSuccess) {
+    if (cudaStreamCreateWithPriority(&x.st, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&x.st_hi, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+        cudaEventCreate(&x.ev0) != cudaSuccess || cudaEventCreate(&x.ev) != cudaSuccess) {
       cudaGetLastError();
       return SLASH_ECUDA;
     }
@@ -106,16 +145,23 @@ extern "C" int slash_serve(slash_index* ix, const slash_serve_opts* o, uint32_t 
       return SLASH_ENOMEM;
     }
   }
-  if (cudaEventCreate(&sl.ref) != cudaSuccess) return SLASH_ECUDA;
+  // The caller's feature and answer arrays, page-locked when CUDA allows: a
+  // batch's features are then copied to the device from where they lie and its
+  // answers straight into place (no host copies, no page faults on first touch
+  // of the answer arrays while serving); otherwise both go through the slot's
+  // page-locked buffers.
+  const bool direct_in = sl.pin(cols ? cols + offs[0] : nullptr, 4u * (offs[total_q] - offs[0]));
+  const bool direct_out = sl.pin(ids_out, 4u * total_q * k) && sl.pin(scores_out, 4u * total_q * k);
   for (uint32_t i = 0; i < n; ++i) {
     launched_s[i] = done_s[i] = NAN;
+    if (device_s) device_s[i] = NAN;
     status[i] = 0;
   }
-  const slash_query_opts qo{o->mode, o->threads, 0u};
+  // a batch of more than small_queries queries leaves reserve_sms SMs to the small ones
+  const slash_query_opts qo_small{o->mode, o->threads, 0u, 0u};
+  const slash_query_opts qo_big{o->mode, o->threads, 0u, o->reserve_sms ? (uint32_t)num_sms - o->reserve_sms : 0u};
 
-  // time zero: a reference event on the GPU's clock, then the host's
-  if (cudaEventRecord(sl.ref, sl.s[0].st) != cudaSuccess || cudaEventSynchronize(sl.ref) != cudaSuccess)
-    return SLASH_ECUDA;
+  // time zero; every time below is read from the host's clock
   const Clock::time_point t0 = Clock::now();
   auto now_s = [&]() { return std::chrono::duration<double>(Clock::now() - t0).count(); };
 
@@ -136,11 +182,20 @@ extern "C" int slash_serve(slash_index* ix, const slash_serve_opts* o, uint32_t 
         cudaGetLastError();
         return SLASH_ECUDA;
       }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, sl.ref, x.ev);
-      std::memcpy(ids_out + x.q0 * k, x.h_out, 4u * x.nq * k);
-      std::memcpy(scores_out + x.q0 * k, x.h_out + 4u * x.nq * k, 4u * x.nq * k);
-      for (uint32_t r = x.r0; r < x.r1; ++r) done_s[r] = 1e-3 * ms;
+      if (!direct_out) {
+        std::memcpy(ids_out + x.q0 * k, x.h_out, 4u * x.nq * k);
+        std::memcpy(scores_out + x.q0 * k, x.h_out + 4u * x.nq * k, 4u * x.nq * k);
+      }
+      const double t_done = now_s();  // the answers are in the caller's arrays
+      float ms = NAN;
+      if (device_s && cudaEventElapsedTime(&ms, x.ev0, x.ev) != cudaSuccess) {
+        cudaGetLastError();
+        ms = NAN;
+      }
+      for (uint32_t r = x.r0; r < x.r1; ++r) {
+        done_s[r] = t_done;
+        if (device_s) device_s[r] = 1e-3 * (double)ms;
+      }
       x.busy = false;
     }
     // the head of the queue: refused (too large for any batch) or past its deadline
@@ -167,19 +222,34 @@ extern "C" int slash_serve(slash_index* ix, const slash_serve_opts* o, uint32_t 
       uint64_t* ho = reinterpret_cast<uint64_t*>(x.h_in);
       for (uint64_t j = 0; j <= nq; ++j) ho[j] = offs[q0 + j] - base;
       const size_t c0 = cols_at(nq);
-      if (nnz) std::memcpy(x.h_in + c0, cols + base, 4u * nnz);
+      if (nnz && !direct_in) std::memcpy(x.h_in + c0, cols + base, 4u * nnz);
       const uint64_t ob = 4u * nq * k;
-      if (cudaMemcpyAsync(x.d_in, x.h_in, c0 + 4u * nnz, cudaMemcpyHostToDevice, x.st) != cudaSuccess) {
+      const bool small = o->small_queries != 0u && nq <= o->small_queries;
+      cudaStream_t st = small ? x.st_hi : x.st;
+      bool ok = cudaEventRecord(x.ev0, st) == cudaSuccess;
+      if (direct_in) {
+        ok = ok && cudaMemcpyAsync(x.d_in, x.h_in, 8u * (nq + 1u), cudaMemcpyHostToDevice, st) == cudaSuccess;
+        ok = ok && (nnz == 0u ||
+                    cudaMemcpyAsync(x.d_in + c0, cols + base, 4u * nnz, cudaMemcpyHostToDevice, st) == cudaSuccess);
+      } else {
+        ok = ok && cudaMemcpyAsync(x.d_in, x.h_in, c0 + 4u * nnz, cudaMemcpyHostToDevice, st) == cudaSuccess;
+      }
+      if (!ok) {
         cudaGetLastError();
         return SLASH_ECUDA;
       }
       const int rc = slash_query_ex(ix, reinterpret_cast<const uint64_t*>(x.d_in),
                                     reinterpret_cast<const uint32_t*>(x.d_in + c0), (uint32_t)nq, (uint32_t)k,
                                     reinterpret_cast<int32_t*>(x.d_out), reinterpret_cast<uint32_t*>(x.d_out + ob),
-                                    &qo, x.st);
+                                    small ? &qo_small : &qo_big, st);
       if (rc != SLASH_OK) return rc;
-      if (cudaMemcpyAsync(x.h_out, x.d_out, 2u * ob, cudaMemcpyDeviceToHost, x.st) != cudaSuccess ||
-          cudaEventRecord(x.ev, x.st) != cudaSuccess) {
+      if (direct_out) {
+        ok = cudaMemcpyAsync(ids_out + q0 * k, x.d_out, ob, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+             cudaMemcpyAsync(scores_out + q0 * k, x.d_out + ob, ob, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+      } else {
+        ok = cudaMemcpyAsync(x.h_out, x.d_out, 2u * ob, cudaMemcpyDeviceToHost, st) == cudaSuccess;
+      }
+      if (!ok || cudaEventRecord(x.ev, st) != cudaSuccess) {
         cudaGetLastError();
         return SLASH_ECUDA;
       }
@@ -193,10 +263,14 @@ extern "C" int slash_serve(slash_index* ix, const slash_serve_opts* o, uint32_t 
     }
     if (!busy && head >= n) break;
     if (!busy && head >= next && next < n) {  // idle until the next arrival
+      // a long wait is slept through but its last kSpinS are polled: a thread's
+      // wake-up can come late by far more than the sleep's own resolution
+      constexpr double kSpinS = 2e-3;
       const double wait = arrival[next] - now_s();
-      if (wait > 2e-4) std::this_thread::sleep_for(std::chrono::duration<double>(wait - 1e-4));
+      if (wait > 2.0 * kSpinS) std::this_thread::sleep_for(std::chrono::duration<double>(wait - kSpinS));
+      else spin_pause();
     } else {
-      std::this_thread::yield();
+      spin_pause();
     }
   }
   return SLASH_OK;

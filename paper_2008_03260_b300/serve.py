@@ -53,6 +53,7 @@ class Result:
     ids: np.ndarray | None = None
     scores: np.ndarray | None = None
     status: int = 0
+    device: float = math.nan  # the batch's device span (copy in to copy back), seconds
 
     @property
     def latency(self) -> float:
@@ -210,12 +211,8 @@ class GpuExecutor:
         self.sched = {} if mode is None else {"mode": mode, "threads": threads}
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.bufs = [_SlotBuffers(torch, topk, queries, nnz) for _ in range(slots)]
+        self.ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(slots)]
         self.events = [torch.cuda.Event(enable_timing=True) for _ in range(slots)]
-        self.ref = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        self.ref.record(torch.cuda.current_stream())
-        self.ref.synchronize()
-        self.t_ref = time.perf_counter()
 
     def launch_reqs(self, slot: int, reqs: list[Request]):
         torch = self.torch
@@ -227,6 +224,7 @@ class GpuExecutor:
         # slot), so its host buffers can be overwritten
         concat_csr(reqs, h_offs.numpy().view(np.uint64), h_cols.numpy().view(np.uint32))
         with torch.cuda.stream(st):
+            self.ev0[slot].record(st)
             b.d_in[:nin].copy_(b.h_in[:nin], non_blocking=True)
             self.ix.query(d_offs, d_cols, self.topk, st, d_ids_out=d_ids, d_scores_out=d_sc, **self.sched)
             b.h_out[:nout].copy_(b.d_out[:nout], non_blocking=True)
@@ -244,9 +242,13 @@ class GpuExecutor:
     def collect(self, h) -> tuple[np.ndarray, np.ndarray, float]:
         ev, slot, nq = h
         ev.synchronize()
-        t_done = self.t_ref + self.ref.elapsed_time(ev) / 1e3
         ids, sc = self.bufs[slot].results(nq)
-        return ids, sc, t_done
+        return ids, sc, time.perf_counter()  # the answers are in the caller's hands
+
+    def device_span(self, h) -> float:
+        """Seconds from the batch's copy in to the end of its copy back (completed batch)."""
+        ev, slot, _ = h
+        return self.ev0[slot].elapsed_time(ev) / 1e3
 
 
 def summarize(requests: list[Request], res: dict, n_batches: int) -> dict:
@@ -266,10 +268,12 @@ def summarize(requests: list[Request], res: dict, n_batches: int) -> dict:
             "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * p99,
             "mean_ms": 1e3 * float(lat.mean()), "queries_per_s": nq / span if span > 0 else float("nan"),
             "span_s": span,
-            # where the slowest 1% spent their time: queued on the host before
-            # launch, and from launch to completion on the device
+            # where the slowest 1% spent their time: queued before launch, from
+            # launch to answers in hand, and of that the batch's span on the device
             "p99_queued_ms": 1e3 * float(np.mean([r.launched - r.arrival for r in tail])) if tail else 0.0,
             "p99_device_ms": 1e3 * float(np.mean([r.done - r.launched for r in tail])) if tail else 0.0,
+            "p99_gpu_span_ms": 1e3 * float(np.nanmean([r.device for r in tail]))
+            if tail and not all(math.isnan(r.device) for r in tail) else float("nan"),
             # the tail of small requests alone (sizes are log-uniform: the slowest 1%
             # overall are mostly the largest requests)
             "p50_small_ms": 1e3 * float(np.percentile(small, 50)) if len(small) else 0.0,
@@ -277,7 +281,8 @@ def summarize(requests: list[Request], res: dict, n_batches: int) -> dict:
 
 
 def serve_native(requests: list[Request], ix, *, topk: int, slots: int = 4, max_batch_queries: int = 8192,
-                 mode: str = "fused", threads: int = 0, timeout_s: float = 0.0) -> tuple[list[Result], dict]:
+                 mode: str = "fused", threads: int = 0, timeout_s: float = 0.0, reserve_sms: int = 0,
+                 small_queries: int = 0) -> tuple[list[Result], dict]:
     """The same request stream through the library's native loop (slash_serve):
     admission, batching and the slots' streams run in C++; this function only
     lays the requests out as arrays and reads the answers back."""
@@ -286,13 +291,15 @@ def serve_native(requests: list[Request], ix, *, topk: int, slots: int = 4, max_
     req_q = np.zeros(len(reqs) + 1, dtype=np.uint64)
     np.cumsum([r.nq for r in reqs], out=req_q[1:])
     offs, cols = concat_csr(reqs)
-    ids, sc, launched, done, status = ix.serve(arrival, req_q, offs, cols, topk, slots=slots,
+    ids, sc, launched, done, status, device = ix.serve(arrival, req_q, offs, cols, topk, slots=slots,
                                                max_batch_queries=max_batch_queries, mode=mode, threads=threads,
-                                               timeout_s=timeout_s)
+                                               timeout_s=timeout_s, reserve_sms=reserve_sms,
+                                               small_queries=small_queries)
     res = {}
     for i, r in enumerate(reqs):
         q0, q1 = int(req_q[i]), int(req_q[i + 1])
-        rr = Result(r.rid, r.arrival, float(launched[i]), float(done[i]), status=int(status[i]))
+        rr = Result(r.rid, r.arrival, float(launched[i]), float(done[i]), status=int(status[i]),
+                    device=float(device[i]))
         if rr.status == 0:
             rr.ids, rr.scores = ids[q0:q1], sc[q0:q1]
         res[r.rid] = rr
@@ -318,12 +325,13 @@ def serve(requests: list[Request], executor, *, topk: int, slots: int = 4, mem_b
             if b is not None and executor.done(b.handle):
                 tc = time.perf_counter()
                 ids, sc, t_done = executor.collect(b.handle)
+                span = executor.device_span(b.handle) if hasattr(executor, "device_span") else math.nan
                 bat.finish(s)
                 q = 0
                 for r in b.reqs:
                     rr = res[r.rid]
                     rr.ids, rr.scores = ids[q:q + r.nq], sc[q:q + r.nq]
-                    rr.launched, rr.done = b.launched, t_done - t0
+                    rr.launched, rr.done, rr.device = b.launched, t_done - t0, span
                     q += r.nq
                 t_collect += time.perf_counter() - tc
         if realtime:

@@ -166,12 +166,13 @@ def test_native_serve_validates_before_touching_the_gpu():
 
     def call(o, arrival=arr, req_q=rq, offsets=offs, n=2):
         return s._lib.slash_serve(fake, ctypes.byref(o), n, arrival.ctypes.data, req_q.ctypes.data,
-                                  offsets.ctypes.data, cols.ctypes.data, *[a.ctypes.data for a in out])
+                                  offsets.ctypes.data, cols.ctypes.data, *[a.ctypes.data for a in out], None)
 
-    ok = dict(slots=2, max_batch_queries=8, topk=10, mode=s.SLASH_QUERY_FUSED, threads=0, reserved=0,
-              timeout_s=0.0)
+    ok = dict(slots=2, max_batch_queries=8, topk=10, mode=s.SLASH_QUERY_FUSED, threads=0, reserve_sms=0,
+              small_queries=0, reserved=0, timeout_s=0.0)
     for bad in (dict(slots=0), dict(slots=17), dict(max_batch_queries=0), dict(topk=0), dict(topk=257),
-                dict(mode=s.SLASH_QUERY_PLAIN), dict(mode=s.SLASH_QUERY_WARP_PLAIN), dict(reserved=1)):
+                dict(mode=s.SLASH_QUERY_PLAIN), dict(mode=s.SLASH_QUERY_WARP_PLAIN), dict(reserved=1),
+                dict(reserve_sms=8)):  # an SM reserve needs a small-batch size
         assert call(s.slash_serve_opts(**{**ok, **bad})) == s.SLASH_EINVAL, bad
     o = s.slash_serve_opts(**ok)
     assert call(o, arrival=np.array([0.2, 0.1])) == s.SLASH_EINVAL            # arrivals go back in time
@@ -206,8 +207,12 @@ def test_native_serving_equals_oracle_refuses_and_cancels():
         ix.sync()
         reqs = poisson_requests(50_000.0, 400, qo, qc, seed=7, max_size=512)
         want = {q.rid: oix.query(q.offs, q.cols, 10) for q in reqs if q.nq <= 300}
-        for mode in ("fused", "warp_fused"):
-            res, summ = serve_native(reqs, ix, topk=10, slots=4, max_batch_queries=300, mode=mode)
+        # (schedule, SMs left to small batches, small-batch size): one priority for all, then
+        # high-priority small batches beside large ones held to 48 and to 8 SMs
+        for mode, reserve, small in (("fused", 0, 0), ("warp_fused", 0, 0), ("fused", 100, 32),
+                                     ("warp_fused", 140, 64)):
+            res, summ = serve_native(reqs, ix, topk=10, slots=4, max_batch_queries=300, mode=mode,
+                                     reserve_sms=reserve, small_queries=small)
             by = {r.rid: r for r in res}
             big = [q for q in reqs if q.nq > 300]
             assert big and all(by[q.rid].status == SLASH_EBUSY for q in big)
@@ -218,8 +223,15 @@ def test_native_serving_equals_oracle_refuses_and_cancels():
                     continue
                 assert r.status == 0 and r.arrival <= r.launched <= r.done
                 want_ids, want_sc = want[q.rid]
-                assert np.array_equal(r.ids, want_ids), (mode, q.rid)
-                assert np.array_equal(r.scores, want_sc), (mode, q.rid)
+                assert np.array_equal(r.ids, want_ids), (mode, reserve, q.rid)
+                assert np.array_equal(r.scores, want_sc), (mode, reserve, q.rid)
+        # a launch held to a few SMs answers as one over the whole GPU
+        q1 = int(qo[2000])
+        d_qo, d_qc = dev((qo[:2001] - qo[0]).astype(np.uint64)), dev(np.ascontiguousarray(qc[int(qo[0]):q1]))
+        for mode in ("fused", "plain", "warp_fused", "warp_plain"):
+            a_ids, a_sc = ix.query(d_qo, d_qc, 10, mode=mode)
+            b_ids, b_sc = ix.query(d_qo, d_qc, 10, mode=mode, max_sms=3)
+            assert torch.equal(a_ids, b_ids) and torch.equal(a_sc, b_sc), mode
         # every request arrives at time 0 and may wait 1 ns: by the loop's first look
         # (tens of ns after its start) every deadline has passed
         at0 = [dataclasses.replace(q, arrival=0.0) for q in reqs]
