@@ -28,6 +28,10 @@
 extern "C" {
 #endif
 
+/* slash_serve_opts.flags: leave the caller's arrays pageable; every batch goes
+ * through the slots' pinned buffers (host copies in and out). */
+#define SLASH_SERVE_NO_PIN 1u
+
 typedef struct {
   uint32_t slots;              /* batches in flight at once, one CUDA stream each (1..16)           */
   uint32_t max_batch_queries;  /* queries of one batch at most (>= 1); a request with more is      */
@@ -41,7 +45,7 @@ typedef struct {
                                /* needs small_queries >= 1 and < the SM count                        */
   uint32_t small_queries;      /* batches of at most this many queries run on the slots' high-      */
                                /* priority streams over the whole GPU; 0 = one priority for all     */
-  uint32_t reserved;           /* must be 0                                                         */
+  uint32_t flags;              /* SLASH_SERVE_NO_PIN or 0                                           */
   double timeout_s;            /* a request still waiting for a batch this long after its arrival   */
                                /* is cancelled (SLASH_ETIMEOUT); <= 0: no deadline                  */
 } slash_serve_opts;
@@ -72,8 +76,8 @@ typedef struct {
  * h_ids_out and h_scores_out are page-locked when CUDA allows it, so that a
  * batch's features are copied to the device from where they lie and its
  * answers straight into place; where it does not, both pass through the
- * slots' pinned buffers.  The caller must not touch those arrays during the
- * call.  The thread polls the slots' events and the clock
+ * slots' pinned buffers (always, with SLASH_SERVE_NO_PIN).  The caller must
+ * not touch those arrays during the call.  The thread polls the slots' events and the clock
  * (a busy loop on one host core); it sleeps only through long idle gaps, up to
  * 2 ms before the next arrival.
  *

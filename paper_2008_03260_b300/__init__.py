@@ -49,6 +49,7 @@ class SlashError(RuntimeError):
         super().__init__(f"{where}: {slash_strerror(code)} ({code})")
 
 
+SLASH_SERVE_NO_PIN = 1  # slash_serve_opts.flags (include/slash_serve.h)
 SLASH_QUERY_FUSED = 0
 SLASH_QUERY_PLAIN = 1
 SLASH_QUERY_WARP_FUSED = 2
@@ -75,7 +76,7 @@ SLASH_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 class slash_serve_opts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_uint32), ("max_batch_queries", ctypes.c_uint32), ("topk", ctypes.c_uint32),
                 ("mode", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("reserve_sms", ctypes.c_uint32),
-                ("small_queries", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("timeout_s", ctypes.c_double)]
+                ("small_queries", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("timeout_s", ctypes.c_double)]
 
 
 class slash_params(ctypes.Structure):
@@ -295,7 +296,7 @@ def slash_autotune(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, topk: in
 
 def slash_serve(ix: int, arrival_s, req_q, offs, cols, topk: int, *, slots: int = 4,
                 max_batch_queries: int = 8192, mode="fused", threads: int = 0, timeout_s: float = 0.0,
-                reserve_sms: int = 0, small_queries: int = 0):
+                reserve_sms: int = 0, small_queries: int = 0, pin: bool = True):
     """The native serving loop (include/slash_serve.h) over host arrays:
     arrival_s float64 [n], req_q uint64 [n+1] (request i = queries
     [req_q[i], req_q[i+1])), the queries' CSR offs uint64 / cols uint32.
@@ -317,7 +318,7 @@ def slash_serve(ix: int, arrival_s, req_q, offs, cols, topk: int, *, slots: int 
     status = np.empty(n, dtype=np.int32)
     device = np.empty(n, dtype=np.float64)
     o = slash_serve_opts(slots, max_batch_queries, topk, _MODES.get(mode, mode), threads, reserve_sms,
-                         small_queries, 0, timeout_s)
+                         small_queries, 0 if pin else SLASH_SERVE_NO_PIN, timeout_s)
     ptr = lambda a: a.ctypes.data if a.size else None
     _check(_lib.slash_serve(ix, ctypes.byref(o), n, ptr(arr), rq.ctypes.data, of.ctypes.data, ptr(co), ptr(ids),
                             ptr(sc), ptr(launched), ptr(done), ptr(status), ptr(device)), "slash_serve")

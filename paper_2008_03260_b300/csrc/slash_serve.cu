@@ -88,7 +88,7 @@ extern "C" int slash_serve(slash_index* ix, const slash_serve_opts* o, uint32_t 
                            double* device_s) {
   if (!ix || !o) return SLASH_EINVAL;
   if (o->slots < 1u || o->slots > 16u || o->max_batch_queries < 1u || o->topk < 1u || o->topk > SLASH_MAX_TOPK ||
-      (o->mode != SLASH_QUERY_FUSED && o->mode != SLASH_QUERY_WARP_FUSED) || o->reserved != 0u ||
+      (o->mode != SLASH_QUERY_FUSED && o->mode != SLASH_QUERY_WARP_FUSED) || (o->flags & ~SLASH_SERVE_NO_PIN) != 0u ||
       (o->reserve_sms != 0u && o->small_queries == 0u))
     return SLASH_EINVAL;
   if (n == 0u) return SLASH_OK;
@@ -150,8 +150,9 @@ extern "C" int slash_serve(slash_index* ix, const slash_serve_opts* o, uint32_t 
   // answers straight into place (no host copies, no page faults on first touch
   // of the answer arrays while serving); otherwise both go through the slot's
   // page-locked buffers.
-  const bool direct_in = sl.pin(cols ? cols + offs[0] : nullptr, 4u * (offs[total_q] - offs[0]));
-  const bool direct_out = sl.pin(ids_out, 4u * total_q * k) && sl.pin(scores_out, 4u * total_q * k);
+  const bool pin = (o->flags & SLASH_SERVE_NO_PIN) == 0u;
+  const bool direct_in = pin && sl.pin(cols ? cols + offs[0] : nullptr, 4u * (offs[total_q] - offs[0]));
+  const bool direct_out = pin && sl.pin(ids_out, 4u * total_q * k) && sl.pin(scores_out, 4u * total_q * k);
   for (uint32_t i = 0; i < n; ++i) {
     launched_s[i] = done_s[i] = NAN;
     if (device_s) device_s[i] = NAN;

@@ -169,9 +169,9 @@ def test_native_serve_validates_before_touching_the_gpu():
                                   offsets.ctypes.data, cols.ctypes.data, *[a.ctypes.data for a in out], None)
 
     ok = dict(slots=2, max_batch_queries=8, topk=10, mode=s.SLASH_QUERY_FUSED, threads=0, reserve_sms=0,
-              small_queries=0, reserved=0, timeout_s=0.0)
+              small_queries=0, flags=0, timeout_s=0.0)
     for bad in (dict(slots=0), dict(slots=17), dict(max_batch_queries=0), dict(topk=0), dict(topk=257),
-                dict(mode=s.SLASH_QUERY_PLAIN), dict(mode=s.SLASH_QUERY_WARP_PLAIN), dict(reserved=1),
+                dict(mode=s.SLASH_QUERY_PLAIN), dict(mode=s.SLASH_QUERY_WARP_PLAIN), dict(flags=2),
                 dict(reserve_sms=8)):  # an SM reserve needs a small-batch size
         assert call(s.slash_serve_opts(**{**ok, **bad})) == s.SLASH_EINVAL, bad
     o = s.slash_serve_opts(**ok)
@@ -207,12 +207,14 @@ def test_native_serving_equals_oracle_refuses_and_cancels():
         ix.sync()
         reqs = poisson_requests(50_000.0, 400, qo, qc, seed=7, max_size=512)
         want = {q.rid: oix.query(q.offs, q.cols, 10) for q in reqs if q.nq <= 300}
-        # (schedule, SMs left to small batches, small-batch size): one priority for all, then
-        # high-priority small batches beside large ones held to 48 and to 8 SMs
-        for mode, reserve, small in (("fused", 0, 0), ("warp_fused", 0, 0), ("fused", 100, 32),
-                                     ("warp_fused", 140, 64)):
+        # (schedule, SMs left to small batches, small-batch size, caller arrays page-locked):
+        # one priority for all, then high-priority small batches beside large ones held to
+        # 48 and to 8 SMs; and every batch through the slots' buffers
+        for mode, reserve, small, pin in (("fused", 0, 0, True), ("warp_fused", 0, 0, True),
+                                          ("fused", 100, 32, True), ("warp_fused", 140, 64, True),
+                                          ("fused", 0, 0, False)):
             res, summ = serve_native(reqs, ix, topk=10, slots=4, max_batch_queries=300, mode=mode,
-                                     reserve_sms=reserve, small_queries=small)
+                                     reserve_sms=reserve, small_queries=small, pin=pin)
             by = {r.rid: r for r in res}
             big = [q for q in reqs if q.nq > 300]
             assert big and all(by[q.rid].status == SLASH_EBUSY for q in big)
