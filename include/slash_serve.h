@@ -48,6 +48,10 @@ typedef struct {
   uint32_t flags;              /* SLASH_SERVE_NO_PIN or 0                                           */
   double timeout_s;            /* a request still waiting for a batch this long after its arrival   */
                                /* is cancelled (SLASH_ETIMEOUT); <= 0: no deadline                  */
+  uint64_t mem_budget_bytes;   /* device bytes the in-flight batches may hold, counted per request  */
+                               /* as 8(q+1) + 4 nnz (its CSR) + 8 q topk (ids and scores) for q     */
+                               /* queries; a request above it alone is refused (SLASH_EBUSY), and a  */
+                               /* batch waits while it would exceed what is left; 0 = no budget      */
 } slash_serve_opts;
 
 /* Serve n_requests requests in real time.  Request i arrives h_arrival_s[i]
@@ -55,7 +59,9 @@ typedef struct {
  * [h_req_q[i], h_req_q[i+1]) of one query CSR: query j's feature ids are
  * h_cols[h_offs[j] .. h_offs[j+1]) (h_req_q[0] = 0; h_offs[0] need not be 0).
  * A batch is formed, whenever a slot is free, from the waiting requests in
- * arrival order while its queries stay within max_batch_queries.
+ * arrival order while its queries stay within max_batch_queries and the bytes
+ * of all batches in flight within mem_budget_bytes (the fused schedules need no
+ * per-batch workspace beyond the batch's own CSR and answers).
  *
  * Outputs (row-major [total queries][topk], as slash_query): h_ids_out int32,
  * h_scores_out uint32 of every query of an answered request; per request

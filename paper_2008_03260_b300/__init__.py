@@ -76,7 +76,8 @@ SLASH_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 class slash_serve_opts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_uint32), ("max_batch_queries", ctypes.c_uint32), ("topk", ctypes.c_uint32),
                 ("mode", ctypes.c_uint32), ("threads", ctypes.c_uint32), ("reserve_sms", ctypes.c_uint32),
-                ("small_queries", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("timeout_s", ctypes.c_double)]
+                ("small_queries", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("timeout_s", ctypes.c_double),
+                ("mem_budget_bytes", ctypes.c_uint64)]
 
 
 class slash_params(ctypes.Structure):
@@ -296,7 +297,7 @@ def slash_autotune(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, topk: in
 
 def slash_serve(ix: int, arrival_s, req_q, offs, cols, topk: int, *, slots: int = 4,
                 max_batch_queries: int = 8192, mode="fused", threads: int = 0, timeout_s: float = 0.0,
-                reserve_sms: int = 0, small_queries: int = 0, pin: bool = True):
+                reserve_sms: int = 0, small_queries: int = 0, pin: bool = True, mem_budget: int = 0):
     """The native serving loop (include/slash_serve.h) over host arrays:
     arrival_s float64 [n], req_q uint64 [n+1] (request i = queries
     [req_q[i], req_q[i+1])), the queries' CSR offs uint64 / cols uint32.
@@ -318,7 +319,7 @@ def slash_serve(ix: int, arrival_s, req_q, offs, cols, topk: int, *, slots: int 
     status = np.empty(n, dtype=np.int32)
     device = np.empty(n, dtype=np.float64)
     o = slash_serve_opts(slots, max_batch_queries, topk, _MODES.get(mode, mode), threads, reserve_sms,
-                         small_queries, 0 if pin else SLASH_SERVE_NO_PIN, timeout_s)
+                         small_queries, 0 if pin else SLASH_SERVE_NO_PIN, timeout_s, mem_budget)
     ptr = lambda a: a.ctypes.data if a.size else None
     _check(_lib.slash_serve(ix, ctypes.byref(o), n, ptr(arr), rq.ctypes.data, of.ctypes.data, ptr(co), ptr(ids),
                             ptr(sc), ptr(launched), ptr(done), ptr(status), ptr(device)), "slash_serve")

@@ -45,6 +45,7 @@ struct Slot {
   bool busy = false;
   uint32_t r0 = 0, r1 = 0;  // the batch's requests [r0, r1)
   uint64_t q0 = 0, nq = 0;  // and its queries [q0, q0 + nq)
+  uint64_t bytes = 0;       // and their device bytes (the budget's count)
 };
 
 struct Slots {
@@ -105,14 +106,21 @@ extern "C" int slash_serve(slash_index* ix, const slash_serve_opts* o, uint32_t 
   const uint64_t cap = o->max_batch_queries, k = o->topk;
   auto req_nq = [&](uint32_t i) { return req_q[i + 1] - req_q[i]; };
   auto nnz_of = [&](uint64_t q0, uint64_t q1) { return offs[q1] - offs[q0]; };
+  // device bytes of request i in flight: its CSR in, its ids and scores out
+  auto req_bytes = [&](uint32_t i) {
+    return 8u * (req_nq(i) + 1u) + 4u * nnz_of(req_q[i], req_q[i + 1]) + 8u * req_nq(i) * k;
+  };
+  const uint64_t budget = o->mem_budget_bytes ? o->mem_budget_bytes : ~0ull;
+  // a request never admitted: more queries than a batch, or more bytes than the budget
+  auto refused = [&](uint32_t i) { return req_nq(i) > cap || req_bytes(i) > budget; };
 
   // The largest batch the stream can form: a run of consecutive admitted
   // requests (a refused one ends a run) of at most `cap` queries.
   uint64_t most_q = 0, most_nnz = 0;
   for (uint32_t i = 0, j = 0; i < n; ++i) {
-    if (req_nq(i) > cap) { j = i + 1; continue; }
+    if (refused(i)) { j = i + 1; continue; }
     if (j < i + 1) j = i + 1;
-    while (j < n && req_nq(j) <= cap && req_q[j + 1] - req_q[i] <= cap) ++j;
+    while (j < n && !refused(j) && req_q[j + 1] - req_q[i] <= cap) ++j;
     most_q = std::max(most_q, req_q[j] - req_q[i]);
     most_nnz = std::max(most_nnz, nnz_of(req_q[i], req_q[j]));
   }
@@ -166,8 +174,9 @@ extern "C" int slash_serve(slash_index* ix, const slash_serve_opts* o, uint32_t 
   const Clock::time_point t0 = Clock::now();
   auto now_s = [&]() { return std::chrono::duration<double>(Clock::now() - t0).count(); };
 
-  uint32_t next = 0;  // requests [0, next) have arrived
-  uint32_t head = 0;  // requests [head, next) wait for a batch
+  uint32_t next = 0;     // requests [0, next) have arrived
+  uint32_t head = 0;     // requests [head, next) wait for a batch
+  uint64_t in_use = 0;   // device bytes of the batches in flight
   for (;;) {
     const double now = now_s();
     while (next < n && arrival[next] <= now) ++next;
@@ -197,11 +206,12 @@ extern "C" int slash_serve(slash_index* ix, const slash_serve_opts* o, uint32_t 
         done_s[r] = t_done;
         if (device_s) device_s[r] = 1e-3 * (double)ms;
       }
+      in_use -= x.bytes;
       x.busy = false;
     }
     // the head of the queue: refused (too large for any batch) or past its deadline
     while (head < next) {
-      if (req_nq(head) > cap) status[head] = SLASH_EBUSY;
+      if (refused(head)) status[head] = SLASH_EBUSY;
       else if (o->timeout_s > 0.0 && now - arrival[head] > o->timeout_s) status[head] = SLASH_ETIMEOUT;
       else break;
       ++head;
@@ -209,9 +219,13 @@ extern "C" int slash_serve(slash_index* ix, const slash_serve_opts* o, uint32_t 
     for (Slot& x : sl.s) {  // a batch for every free slot while requests wait
       if (x.busy || head >= next) continue;
       uint32_t r1 = head;
-      while (r1 < next && req_nq(r1) <= cap && req_q[r1 + 1] - req_q[head] <= cap &&
-             !(o->timeout_s > 0.0 && now - arrival[r1] > o->timeout_s))
+      uint64_t bytes = 0;
+      while (r1 < next && !refused(r1) && req_q[r1 + 1] - req_q[head] <= cap &&
+             in_use + bytes + req_bytes(r1) <= budget && !(o->timeout_s > 0.0 && now - arrival[r1] > o->timeout_s)) {
+        bytes += req_bytes(r1);
         ++r1;
+      }
+      if (r1 == head) break;  // the head waits for budget (or is refused or expired on the next pass)
       const uint64_t q0 = req_q[head], nq = req_q[r1] - q0;
       for (uint32_t r = head; r < r1; ++r) launched_s[r] = now;
       if (nq == 0u) {  // requests without queries are answered at once
@@ -255,6 +269,8 @@ extern "C" int slash_serve(slash_index* ix, const slash_serve_opts* o, uint32_t 
         return SLASH_ECUDA;
       }
       x.busy = true;
+      x.bytes = bytes;
+      in_use += bytes;
       x.r0 = head;
       x.r1 = r1;
       x.q0 = q0;

@@ -282,7 +282,8 @@ def summarize(requests: list[Request], res: dict, n_batches: int) -> dict:
 
 def serve_native(requests: list[Request], ix, *, topk: int, slots: int = 4, max_batch_queries: int = 8192,
                  mode: str = "fused", threads: int = 0, timeout_s: float = 0.0, reserve_sms: int = 0,
-                 small_queries: int = 0, pin: bool = True) -> tuple[list[Result], dict]:
+                 small_queries: int = 0, pin: bool = True, mem_budget: int = 16 << 30
+                 ) -> tuple[list[Result], dict]:
     """The same request stream through the library's native loop (slash_serve):
     admission, batching and the slots' streams run in C++; this function only
     lays the requests out as arrays and reads the answers back."""
@@ -294,7 +295,7 @@ def serve_native(requests: list[Request], ix, *, topk: int, slots: int = 4, max_
     ids, sc, launched, done, status, device = ix.serve(arrival, req_q, offs, cols, topk, slots=slots,
                                                max_batch_queries=max_batch_queries, mode=mode, threads=threads,
                                                timeout_s=timeout_s, reserve_sms=reserve_sms,
-                                               small_queries=small_queries, pin=pin)
+                                               small_queries=small_queries, pin=pin, mem_budget=mem_budget)
     res = {}
     for i, r in enumerate(reqs):
         q0, q1 = int(req_q[i]), int(req_q[i + 1])

@@ -227,6 +227,21 @@ def test_native_serving_equals_oracle_refuses_and_cancels():
                 want_ids, want_sc = want[q.rid]
                 assert np.array_equal(r.ids, want_ids), (mode, reserve, q.rid)
                 assert np.array_equal(r.scores, want_sc), (mode, reserve, q.rid)
+        # a device-memory budget of the median request's bytes: the larger requests are
+        # refused, the rest answered as alone (one or two batches in flight at a time)
+        from paper_2008_03260_b300.serve import request_bytes
+        rb = {q.rid: request_bytes(q, 10) for q in reqs}
+        budget = sorted(rb.values())[len(reqs) // 2]
+        res, summ = serve_native(reqs, ix, topk=10, slots=4, max_batch_queries=300, mem_budget=budget)
+        by = {r.rid: r for r in res}
+        for q in reqs:
+            r = by[q.rid]
+            if q.nq > 300 or rb[q.rid] > budget:
+                assert r.status == SLASH_EBUSY, q.rid
+                continue
+            assert r.status == 0 and np.array_equal(r.ids, want[q.rid][0]), q.rid
+            assert np.array_equal(r.scores, want[q.rid][1]), q.rid
+        assert summ["refused"] == sum(1 for q in reqs if q.nq > 300 or rb[q.rid] > budget)
         # a launch held to a few SMs answers as one over the whole GPU
         q1 = int(qo[2000])
         d_qo, d_qc = dev((qo[:2001] - qo[0]).astype(np.uint64)), dev(np.ascontiguousarray(qc[int(qo[0]):q1]))
