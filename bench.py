@@ -663,13 +663,42 @@ def bench_uneven(args, w: workloads.Workload) -> dict:
     ix.sync()
     ix.close()
     t_plain = w.n_queries / per["plain"]
+    cpu = None if args.no_cpu_baseline else uneven_cpu_baseline(w, offs, cols, qo, qc)
     return {"metric": "queries/s, 1M uneven-nnz queries per launch (tuned schedule from a CUDA graph vs plain)",
             "value": w.n_queries / t_graph, "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_graph, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": config_of(w, args),
             "plain_queries_per_s": per["plain"], "speedup_vs_plain": t_plain / t_graph,
             "queries_per_s_by_schedule": per, "schedule": repr(best), "all_schedules_equal": same,
-            "clocks": clk.summary()}
+            "cpu_baseline": cpu, "clocks": clk.summary()}
+
+
+def uneven_cpu_baseline(w: workloads.Workload, offs, cols, qo, qc, n_all: int = 100_000) -> dict:
+    """The oracle on the uneven mix: one thread answering a 20k-query sample
+    against the 100k-row index, and every host core at once answering its share
+    of n_all queries against its own copy-sized index (a 100k-row partition)."""
+    import oracle
+    cores, model = cpu_info()
+    ix = oracle.Index(K=w.K, L=w.L, log2_buckets=w.log2_buckets, reservoir=w.reservoir, cm_rows=w.cm_rows,
+                      cm_width=w.cm_width, shards=w.shards, seed=w.seed, capacity=w.n_rows)
+    ix.insert(offs, cols)
+    nq1 = min(len(qo) - 1, 20_000)
+    t = time.perf_counter()
+    ix.query(qo[:nq1 + 1], qc[:int(qo[nq1])], w.topk)
+    t1 = time.perf_counter() - t
+    del ix
+    per_core = -(-n_all // cores)
+    t = time.perf_counter()
+    (_, aq), = oracle_all_cores(w, w.n_rows, per_core, 1, cores)
+    wall = time.perf_counter() - t
+    return {"value": cores * per_core / aq, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "cpu_model": model,
+            "sample": f"all {cores} host cores at once, each answering {per_core} uneven-mix queries against its "
+                      f"own {w.n_rows}-row oracle index ({cores * per_core} queries in all); rate = all queries / "
+                      f"the slowest core ({wall:.1f}s wall)",
+            "single_thread": {"value": nq1 / t1, "unit": "queries/s", "cores": 1,
+                              "sample": f"the first {nq1} queries of the batch against the {w.n_rows}-row oracle "
+                                        f"index, {t1:.1f}s"}}
 
 
 def bench_serving(args, w: workloads.Workload) -> dict:
