@@ -9,14 +9,17 @@ order into the next batch, as long as the batch stays under
 inputs + outputs) stay under ``mem_budget``.  A request that could never fit
 is refused (``SLASH_EBUSY``).  A request may carry a deadline: if it is still
 queued when its deadline passes it is cancelled (``SLASH_ETIMEOUT``, no
-result) instead of launched.  Latency = completion on the device - arrival;
-each result also records when its batch was launched, so a latency splits
-into time spent queued on the host and time on the device.
+result) instead of launched.  Latency = answers in the caller's hands -
+arrival, on the host's clock; each result also records when its batch was
+launched and the batch's span on the device (CUDA timing events), so a
+latency splits into time queued, host time and device time.
 
 The batching logic (:class:`Batcher`) is host code with no device calls; the
 device work is behind :class:`GpuExecutor`, which issues the fused query
 kernel through the C ABI.  Results do not depend on how requests are grouped:
 every query is answered by one CTA from the same read-only index.
+:func:`serve_native` runs the same policy in the library's C++ loop
+(``slash_serve``), which is the one the bench reports.
 """
 from __future__ import annotations
 
