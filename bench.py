@@ -372,6 +372,8 @@ def main():
                     help="SMs the native loop's large batches leave to batches of few queries")
     ap.add_argument("--serve-small-queries", type=int, default=0,
                     help="largest batch the native loop runs on its high-priority streams")
+    ap.add_argument("--no-patterns", action="store_true",
+                    help="skip the short serving and uneven-batch runs appended to the default line")
     ap.add_argument("--no-serve-python", action="store_true",
                     help="serve through the native loop only (skip the Python loop's comparison run)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -593,12 +595,58 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, offs, cols, qo, qc)
     ix.close()
+    if world == 1 and w.name == "criteo" and not args.no_patterns:
+        out["patterns"] = patterns_summary(args)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
 
+
+
+def patterns_summary(args) -> dict:
+    """Short runs of the two serving-side patterns after the main measurement
+    (their own workloads run them at full length): the native serving loop over
+    the serving workload's 8-shard index at 1k and 10k req/s for 5 s each, and
+    the 1M-query uneven batch (tuned schedule from a CUDA graph against the plain
+    path).  A failure is recorded, not raised."""
+    import torch
+    import paper_2008_03260_b300 as slash
+    from paper_2008_03260_b300.serve import poisson_requests, serve_native
+    out = {}
+    try:
+        w = workloads.ALL["serving"]
+        g = datagen.Generator(dim_bits=w.dim_bits)
+        offs, cols = g.rows(w.seed, 0, w.n_rows)
+        qo, qc, _ = g.queries(w.seed, w.qseed, 200_000, w.n_rows, **w.query_kwargs())
+        dev = lambda a: torch.from_numpy(a.view(np.int64 if a.dtype == np.uint64 else np.int32)).cuda()
+        ix8 = slash.Index(slash.Params(**w.params()))
+        ix8.insert(dev(offs), dev(cols))
+        ix8.sync()
+        rates = {}
+        for rate in (1000, 10000):
+            reqs = poisson_requests(float(rate), 5 * rate, qo, qc, seed=rate)
+            with Clocks(0) as clk:
+                _, summ = serve_native(reqs, ix8, topk=w.topk, slots=8, max_batch_queries=4096, mode="fused")
+            rates[str(rate)] = {k: summ[k] for k in ("requests", "refused", "queries", "p50_ms", "p99_ms",
+                                                     "p99_small_ms", "queries_per_s", "p99_gpu_span_ms")}
+            rates[str(rate)]["clocks"] = clk.summary()
+        ix8.close()
+        out["serving"] = {"sample": "native loop, 8 slots, batches <= 4096 queries, the serving workload's "
+                                    "8-shard index (100k rows), Poisson arrivals for 5 s per rate, request "
+                                    "sizes log-uniform 1-4096 queries from a 200k-query pool",
+                          "rates": rates}
+    except Exception as e:  # pragma: no cover - reported in the line
+        out["serving"] = {"error": repr(e)}
+    try:
+        a = argparse.Namespace(**{**vars(args), "no_cpu_baseline": True})
+        u = bench_uneven(a, workloads.ALL["uneven"])
+        out["uneven"] = {k: u[k] for k in ("value", "unit", "plain_queries_per_s", "speedup_vs_plain",
+                                           "all_schedules_equal", "schedule", "clocks")}
+    except Exception as e:  # pragma: no cover - reported in the line
+        out["uneven"] = {"error": repr(e)}
+    return out
 
 
 # ----------------------------------------------------------------------------- other workloads
