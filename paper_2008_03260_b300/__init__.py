@@ -405,7 +405,7 @@ def slash_set_next_id(ix: int, next_id: int) -> None:
 
 def slash_query_candidates(ix: int, d_offs: torch.Tensor, d_cols: torch.Tensor, m: int, stream=None):
     """Each query's distinct local candidates: counts int32 [nq], ids int32 [nq, m] in the order of their
-    first occurrence in the query's buckets (entries past the count are not written)."""
+    first occurrence in the query's buckets, -1 past the count."""
     nq = d_offs.numel() - 1
     counts = torch.empty(nq, dtype=torch.int32, device=d_offs.device)
     ids = torch.empty((nq, m), dtype=torch.int32, device=d_offs.device)
