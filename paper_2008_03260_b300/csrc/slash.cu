@@ -1259,7 +1259,8 @@ struct StagedLayout {
   uint32_t pcap;     // pool entries, (2k+1)*S*L for k = kLocalTop
   uint32_t off_cm, off_ids, off_est, off_pool, off_bkey, off_boff, off_hist, off_ctrl, off_bar, bytes;
   uint32_t extra_tx;  // test support: bytes announced on the mbarrier beyond the copies (0 in service)
-  uint32_t tmem_cols, tmem_j;  // four-row sketches: TMEM columns per CTA, 4-id groups per thread
+  uint32_t tmem_cols, tmem_j;  // four-row sketches: TMEM columns per team, 4-id groups per thread
+  uint32_t tmem_alloc;         // TMEM columns the CTA allocates: a power of two >= teams * tmem_cols
   uint32_t async16;  // 1: every warp copies the ids in 16-byte cp.async pieces; 0: one bulk copy per bucket
 };
 
@@ -1889,7 +1890,10 @@ __device__ bool staged_answer(const Geo& g, const StagedLayout& lay, unsigned ch
 }
 
 // Staged engine: persistent CTAs of blockDim.x / kTeamT teams; every team pulls
-// queries from the launch's work counter.  kFused = false: bucket addresses from
+// queries from the launch's work counter.  With marked_only (fused only) a team
+// answers only the queries whose first output id is kRedoMark, the ones the
+// warp engine left: warp 0 takes the counter 128 queries at a time and reads
+// their marks in one round of loads.  kFused = false: bucket addresses from
 // the hash kernel (qbkt[t*ldq + q]), the next query's keys and fills prefetched;
 // kFused = true: the team hashes each query itself (DOPH binning by all its
 // threads, densification and table addresses by its warp 0, in the id buffer's
@@ -1901,7 +1905,7 @@ k_query_staged(const __grid_constant__ Geo g, const StagedLayout lay, const uint
                uint64_t ldq, const uint64_t* __restrict__ offs, const uint32_t* __restrict__ cols, uint32_t nq,
                uint32_t k, const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill,
                int32_t* __restrict__ ids_out, uint32_t* __restrict__ scores_out, uint32_t* __restrict__ work,
-               uint32_t* __restrict__ err) {
+               uint32_t* __restrict__ err, uint32_t marked_only) {
   extern __shared__ __align__(128) unsigned char ssm[];
   const Team tm{threadIdx.x / kTeamT, kTeamT, threadIdx.x % kTeamT, (threadIdx.x % kTeamT) >> 5, threadIdx.x & 31u};
   const uint32_t teams = blockDim.x / kTeamT;
@@ -1921,7 +1925,7 @@ k_query_staged(const __grid_constant__ Geo g, const StagedLayout lay, const uint
     mbar_fence_init();
   }
   const bool tmem = kD == 4 && lay.tmem_cols != 0u;
-  if (tmem && threadIdx.x < 32) tmem_alloc(tslot, lay.tmem_cols * teams);  // whole warp 0 of the CTA
+  if (tmem && threadIdx.x < 32) tmem_alloc(tslot, lay.tmem_alloc);  // whole warp 0 of the CTA
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
@@ -1937,8 +1941,45 @@ k_query_staged(const __grid_constant__ Geo g, const StagedLayout lay, const uint
     }
   }
   uint32_t parity = 0;
+  uint32_t mcur = 0, mend = 0;  // marked_only: warp 0's range of the counter not yet scanned
   for (;;) {
-    if (tid == 0) ctrl[S_Q] = kFused ? atomicAdd(work, 1u) : pf.q;
+    if (kFused && marked_only) {
+      if (warp == 0) {  // the next marked query at or after mcur (warp-uniform loop)
+        constexpr uint32_t kGrab = 128u;
+        uint32_t q = nq;
+        for (;;) {
+          if (mcur >= mend) {
+            uint32_t b = 0;
+            if (lane == 0) b = atomicAdd(work, kGrab);
+            b = __shfl_sync(0xFFFFFFFFu, b, 0);
+            mcur = b;
+            mend = b + kGrab;
+            if (b >= nq) break;
+          }
+          bool mk[kGrab / 32];
+#pragma unroll
+          for (uint32_t j = 0; j < kGrab / 32; ++j) {
+            const uint32_t i = mcur + 32u * j + lane;
+            mk[j] = i < mend && i < nq && ids_out[(uint64_t)i * k] == kRedoMark;
+          }
+          uint32_t found = 0xFFFFFFFFu;
+#pragma unroll
+          for (uint32_t j = 0; j < kGrab / 32; ++j) {
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, mk[j]);
+            if (found == 0xFFFFFFFFu && bal) found = mcur + 32u * j + (uint32_t)(__ffs(bal) - 1);
+          }
+          if (found != 0xFFFFFFFFu) {
+            q = found;
+            mcur = found + 1u;
+            break;
+          }
+          mcur = mend;
+        }
+        if (lane == 0) ctrl[S_Q] = q;
+      }
+    } else if (tid == 0) {
+      ctrl[S_Q] = kFused ? atomicAdd(work, 1u) : pf.q;
+    }
     if (tid < S_N && tid != S_Q) ctrl[tid] = 0u;
     uint4* cm4 = reinterpret_cast<uint4*>(cmw);
     for (uint32_t i = tid; i < cm4n; i += kTeamT) cm4[i] = make_uint4(0, 0, 0, 0);
@@ -1986,7 +2027,7 @@ k_query_staged(const __grid_constant__ Geo g, const StagedLayout lay, const uint
   __syncthreads();
   if (tmem && threadIdx.x < 32) {
     tmem_fence_after_sync();
-    tmem_dealloc(*tslot, lay.tmem_cols * teams);
+    tmem_dealloc(*tslot, lay.tmem_alloc);
   }
 }
 
@@ -2779,8 +2820,14 @@ bool warp_ok(const slash_index* ix, uint32_t topk) {
          (size_t)kWarpWarps * make_warp_layout(ix->p).per_warp * 4u <= ix->smem_optin;
 }
 
-// The warp engine on n queries (rows offs[0..n] of cols), then k_query_redo for
-// the queries it left to the general kernel.
+int launch_staged(slash_index* ix, bool fused, uint32_t thr, uint32_t ctas_cap, uint32_t sms, const uint64_t* offs,
+                  const uint32_t* cols, const uint32_t* qbkt, uint64_t ldq, uint32_t n, uint32_t topk, int32_t* ids,
+                  uint32_t* scores, cudaStream_t st, bool marked_only);
+
+// The warp engine on n queries (rows offs[0..n] of cols), then the queries it
+// left (more than kWarpMaxM candidates): the fused schedule hands them to the
+// staged engine where the index has one (each team answers only marked
+// queries), else, and for any the staged engine leaves, k_query_redo.
 int launch_warp(slash_index* ix, bool fused, uint32_t ctas_cap, uint32_t sms, const uint64_t* offs,
                 const uint32_t* cols, const uint32_t* qbkt, uint64_t ldq, uint32_t n, uint32_t topk, int32_t* ids,
                 uint32_t* scores, cudaStream_t st) {
@@ -2806,6 +2853,9 @@ int launch_warp(slash_index* ix, bool fused, uint32_t ctas_cap, uint32_t sms, co
                                                               ix->slots, ix->fill, ids, scores, work, ix->err);
   }
   SLASH_CK(cudaGetLastError());
+  if (fused && ix->staged && topk <= kLocalTop)
+    return launch_staged(ix, true, default_query_threads(ix->p), 0u, sms, offs, cols, nullptr, 0, n, topk, ids,
+                         scores, st, true);
   return launch_redo(ix, offs, cols, n, topk, ids, scores, sms, st);
 }
 
@@ -2822,7 +2872,7 @@ uint32_t staged_teams(const slash_index* ix, uint32_t thr, const StagedLayout& l
 // kernel), then k_query_redo for the queries it left marked.
 int launch_staged(slash_index* ix, bool fused, uint32_t thr, uint32_t ctas_cap, uint32_t sms, const uint64_t* offs,
                   const uint32_t* cols, const uint32_t* qbkt, uint64_t ldq, uint32_t n, uint32_t topk, int32_t* ids,
-                  uint32_t* scores, cudaStream_t st) {
+                  uint32_t* scores, cudaStream_t st, bool marked_only) {
   StagedLayout lay = make_staged_layout(ix->p);
   lay.extra_tx = ix->stall_copies ? 16u : 0u;
   // the team copies the ids itself in 16-byte pieces (one bulk copy per bucket
@@ -2841,8 +2891,13 @@ int launch_staged(slash_index* ix, bool fused, uint32_t thr, uint32_t ctas_cap, 
       const uint32_t need = (thr / 128u) * 8u * lay.tmem_j;
       uint32_t cols = 32u;
       while (cols < need) cols <<= 1;
-      if (cols * teams <= 512u) {
+      // tcgen05.alloc takes a power of two from 32 to 512 columns: three teams
+      // of 32 columns allocate 128
+      uint32_t alloc = 32u;
+      while (alloc < cols * teams) alloc <<= 1;
+      if (alloc <= 512u) {
         lay.tmem_cols = cols;
+        lay.tmem_alloc = alloc;
       } else {
         lay.tmem_j = 0u;
       }
@@ -2868,9 +2923,10 @@ int launch_staged(slash_index* ix, bool fused, uint32_t thr, uint32_t ctas_cap, 
     const uint32_t* slots = ix->slots;
     const uint32_t* fill = ix->fill;
     uint32_t* err = ix->err;
+    const uint32_t mo = marked_only ? 1u : 0u;
     void* args[] = {(void*)gp, (void*)&lay, (void*)&qbkt, (void*)&ldq, (void*)&offs, (void*)&cols, (void*)&n,
                     (void*)&topk, (void*)&slots, (void*)&fill, (void*)&ids, (void*)&scores, (void*)&work,
-                    (void*)&err};
+                    (void*)&err, (void*)&mo};
     SLASH_CK(cudaLaunchKernel(fn, dim3(grid), dim3(block), args, smem, st));
   }
   return launch_redo(ix, offs, cols, n, topk, ids, scores, sms, st);
@@ -3159,7 +3215,7 @@ int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
   if (ix->staged && topk <= kLocalTop) {
     if (o.mode == SLASH_QUERY_FUSED)
       return launch_staged(ix, true, thr, o.ctas_per_sm, sms, d_offs, d_cols, nullptr, 0, n_queries, topk, d_ids_out,
-                           d_scores_out, st);
+                           d_scores_out, st, false);
     const uint64_t chunk = std::min<uint64_t>(n_queries, 1ull << 22);
     int rc = grow_query_ws(ix, chunk);
     if (rc) return rc;
@@ -3168,7 +3224,7 @@ int slash_query_ex(slash_index* ix, const uint64_t* d_offs, const uint32_t* d_co
       rc = run_hash(ix, d_offs + q0, d_cols, n, 0, ix->qbkt, n, nullptr, false, st);
       if (rc) return rc;
       rc = launch_staged(ix, false, thr, o.ctas_per_sm, sms, d_offs + q0, d_cols, ix->qbkt, n, n, topk,
-                         d_ids_out + q0 * topk, d_scores_out + q0 * topk, st);
+                         d_ids_out + q0 * topk, d_scores_out + q0 * topk, st, false);
       if (rc) return rc;
     }
     return SLASH_OK;
@@ -3544,7 +3600,7 @@ extern "C" int slash_query_static(slash_index* ix, const uint64_t* d_offs, const
     rc = run_hash(ix, d_offs, d_cols, n_queries, 0, qbkt, n_queries, nullptr, false, st);
     if (rc) return rc;
     return launch_staged(ix, false, 512u, 0u, ix->num_sms, d_offs, d_cols, qbkt, n_queries, n_queries, topk, d_ids_out,
-                         d_scores_out, st);
+                         d_scores_out, st, false);
   }
   const QueryLayout lay = make_query_layout(ix->p, 512u);
   if (lay.bytes > ix->smem_optin) return SLASH_EINVAL;

@@ -173,8 +173,10 @@ def test_query_sharded_bit_exact(shards, R, B):
         _gpu_insert(ix, offs, cols, [0, 5000, 5001, n])
         ids, sc = ix.query(_dev(qo), _dev(qc), 10)
         ix.sync()
-        for mode in ("warp_fused", "warp_plain"):
-            wi, ws_ = ix.query(_dev(qo), _dev(qc), 10, mode=mode)
+        # 256-thread teams: at (3, 8, 6) a CTA holds three of them (its TMEM allocation
+        # is rounded up to a power of two); the warp engine hands its large queries to them
+        for mode, thr in (("warp_fused", 256), ("warp_plain", 256), ("fused", 256), ("plain", 256)):
+            wi, ws_ = ix.query(_dev(qo), _dev(qc), 10, mode=mode, threads=thr)
             ix.sync()
             assert np.array_equal(wi.cpu().numpy(), ids.cpu().numpy()), mode
             assert np.array_equal(_host_u32(ws_), _host_u32(sc)), mode
