@@ -370,8 +370,8 @@ def main():
     ap.add_argument("--serve-rates", default="1000,10000,30000,100000")
     ap.add_argument("--serve-reserve-sms", type=int, default=0,
                     help="SMs the native loop's large batches leave to batches of few queries")
-    ap.add_argument("--serve-small-queries", type=int, default=0,
-                    help="largest batch the native loop runs on its high-priority streams")
+    ap.add_argument("--serve-small-queries", type=int, default=256,
+                    help="largest batch the native loop runs with the team schedule on its high-priority streams")
     ap.add_argument("--no-patterns", action="store_true",
                     help="skip the short serving and uneven-batch runs appended to the default line")
     ap.add_argument("--no-serve-python", action="store_true",
@@ -624,16 +624,19 @@ def patterns_summary(args) -> dict:
         ix8 = slash.Index(slash.Params(**w.params()))
         ix8.insert(dev(offs), dev(cols))
         ix8.sync()
+        sched, _ = serving_schedule(torch, ix8, qo, qc, w.topk)
         rates = {}
         for rate in (1000, 10000):
             reqs = poisson_requests(float(rate), 5 * rate, qo, qc, seed=rate)
             with Clocks(0) as clk:
-                _, summ = serve_native(reqs, ix8, topk=w.topk, slots=8, max_batch_queries=4096, mode="fused")
+                _, summ = serve_native(reqs, ix8, topk=w.topk, slots=8, max_batch_queries=4096, mode=sched["mode"],
+                                       small_queries=256)
             rates[str(rate)] = {k: summ[k] for k in ("requests", "refused", "queries", "p50_ms", "p99_ms",
                                                      "p99_small_ms", "queries_per_s", "p99_gpu_span_ms")}
             rates[str(rate)]["clocks"] = clk.summary()
         ix8.close()
-        out["serving"] = {"sample": "native loop, 8 slots, batches <= 4096 queries, the serving workload's "
+        out["serving"] = {"schedule": sched["mode"], "small_batches": "<= 256 queries: team schedule, high priority",
+                          "sample": "native loop, 8 slots, batches <= 4096 queries, the serving workload's "
                                     "8-shard index (100k rows), Poisson arrivals for 5 s per rate, request "
                                     "sizes log-uniform 1-4096 queries from a 200k-query pool",
                           "rates": rates}
@@ -749,6 +752,30 @@ def uneven_cpu_baseline(w: workloads.Workload, offs, cols, qo, qc, n_all: int = 
                                         f"index, {t1:.1f}s"}}
 
 
+def serving_schedule(torch, ix, qo, qc, topk: int, sample: int = 4096) -> tuple[dict, dict]:
+    """The faster of the two schedules that may run on several streams at once
+    (fused team engine, fused warp engine), timed on a batch of the loop's
+    largest size from the query pool (a batch's time is what a request waits:
+    on large launches the warp engine's throughput wins, on a 4096-query batch
+    its slowest warps decide)."""
+    dev = lambda a: torch.from_numpy(a.view(np.int64 if a.dtype == np.uint64 else np.int32)).cuda()
+    d_qo = dev((qo[:sample + 1] - qo[0]).astype(np.uint64))
+    d_qc = dev(np.ascontiguousarray(qc[int(qo[0]):int(qo[sample])]))
+    ids = torch.empty((sample, topk), dtype=torch.int32, device="cuda")
+    sc = torch.empty_like(ids)
+    timings = {}
+    for mode in ("fused", "warp_fused"):
+        for i in range(8):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ix.query(d_qo, d_qc, topk, d_ids_out=ids, d_scores_out=sc, mode=mode)
+            b.record()
+            b.synchronize()
+            if i >= 2:
+                timings[mode] = min(timings.get(mode, math.inf), a.elapsed_time(b))
+    return {"mode": min(timings, key=timings.get), "threads": 0}, timings
+
+
 def bench_serving(args, w: workloads.Workload) -> dict:
     """Poisson request streams against an 8-shard resident index: p50/p99 latency."""
     torch, slash = _gpu_setup(w)
@@ -763,23 +790,8 @@ def bench_serving(args, w: workloads.Workload) -> dict:
     # the query schedule: slots run concurrently on their own streams, which the
     # fused schedules allow (no shared workspace); the faster one on a batch of
     # the request pool serves
-    sample = 1 << 16
-    d_qo = dev((qo[:sample + 1] - qo[0]).astype(np.uint64))
-    d_qc = dev(np.ascontiguousarray(qc[int(qo[0]):int(qo[sample])]))
-    ids = torch.empty((sample, w.topk), dtype=torch.int32, device="cuda")
-    sc = torch.empty_like(ids)
-    timings = {}
-    for mode in ("fused", "warp_fused"):
-        for i in range(4):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            ix.query(d_qo, d_qc, w.topk, d_ids_out=ids, d_scores_out=sc, mode=mode)
-            b.record()
-            b.synchronize()
-            if i >= 2:
-                timings[mode] = min(timings.get(mode, math.inf), a.elapsed_time(b))
-    sched = {"mode": min(timings, key=timings.get), "threads": 0}
-    log(f"[bench] serving: schedule {sched} (ms per {sample} queries: {timings})")
+    sched, timings = serving_schedule(torch, ix, qo, qc, w.topk)
+    log(f"[bench] serving: schedule {sched} (ms per 4096 queries: {timings})")
     per_rate = {}
     rates = [int(x) for x in args.serve_rates.split(",")]
     for rate in rates:
@@ -812,7 +824,7 @@ def bench_serving(args, w: workloads.Workload) -> dict:
             "warmup": 0, "ms_per_step": top["p50_ms"], "higher_is_better": True, "scaling": "weak",
             "p50_p99_ms": {r: [round(v["p50_ms"], 4), round(v["p99_ms"], 4)] for r, v in per_rate.items()},
             "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": config_of(w, args),
-            "schedule": sched, "schedule_ms_per_65536_queries": timings, "slots": args.serve_slots,
+            "schedule": sched, "schedule_ms_per_4096_queries": timings, "slots": args.serve_slots,
             "max_batch_queries": args.serve_max_batch, "reserve_sms": args.serve_reserve_sms,
             "small_queries": args.serve_small_queries, "rates": per_rate}
 

@@ -43,8 +43,10 @@ typedef struct {
   uint32_t reserve_sms;        /* SMs a batch of more than small_queries queries leaves free         */
                                /* (slash_query_opts.max_sms = SM count - reserve_sms); 0 = none;    */
                                /* needs small_queries >= 1 and < the SM count                        */
-  uint32_t small_queries;      /* batches of at most this many queries run on the slots' high-      */
-                               /* priority streams over the whole GPU; 0 = one priority for all     */
+  uint32_t small_queries;      /* batches of at most this many queries run the team schedule        */
+                               /* (SLASH_QUERY_FUSED: the shortest time per query) on the slots'    */
+                               /* high-priority streams over the whole GPU, the others `mode`;      */
+                               /* 0 = `mode` and one priority for all                               */
   uint32_t flags;              /* SLASH_SERVE_NO_PIN or 0                                           */
   double timeout_s;            /* a request still waiting for a batch this long after its arrival   */
                                /* is cancelled (SLASH_ETIMEOUT); <= 0: no deadline                  */

@@ -2059,7 +2059,8 @@ __global__ void __launch_bounds__(kWarpWarps * 32, 4)
 k_query_warp(const __grid_constant__ Geo g, const WarpLayout lay, const uint32_t* __restrict__ qbkt, uint64_t ldq,
              const uint64_t* __restrict__ offs, const uint32_t* __restrict__ cols, uint32_t nq, uint32_t k,
              const uint32_t* __restrict__ slots, const uint32_t* __restrict__ fill, int32_t* __restrict__ ids_out,
-             uint32_t* __restrict__ scores_out, uint32_t* __restrict__ work, uint32_t* __restrict__ err) {
+             uint32_t* __restrict__ scores_out, uint32_t* __restrict__ work, uint32_t* __restrict__ err,
+             uint32_t per) {
   extern __shared__ __align__(16) uint32_t wsm[];
   const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
   uint32_t* base = wsm + warp * lay.per_warp;
@@ -2075,14 +2076,14 @@ k_query_warp(const __grid_constant__ Geo g, const WarpLayout lay, const uint32_t
   __syncwarp();
   uint32_t blk = 0, left = 0;
   for (;;) {
-    if (left == 0) {  // the next 32 queries of the batch for this warp
+    if (left == 0) {  // the next `per` queries of the batch for this warp
       uint32_t b = 0;
       if (lane == 0) b = atomicAdd(work, 1u);
-      blk = __shfl_sync(0xFFFFFFFFu, b, 0) * 32u;
-      left = 32;
+      blk = __shfl_sync(0xFFFFFFFFu, b, 0) * per;
+      left = per;
       if (blk >= nq) break;
     }
-    const uint32_t q = blk + (32u - left);
+    const uint32_t q = blk + (per - left);
     --left;
     if (q >= nq) { left = 0; continue; }
     int32_t* io = ids_out + (uint64_t)q * k;
@@ -2839,7 +2840,11 @@ int launch_warp(slash_index* ix, bool fused, uint32_t ctas_cap, uint32_t sms, co
   if (rc) return rc;
   if (bps < 1) return SLASH_EINVAL;
   if (ctas_cap) bps = std::min<int>(bps, (int)ctas_cap);
-  const uint64_t blocks = ((uint64_t)n + 31u) / 32u;  // a warp takes 32 queries at a time
+  // a warp takes `per` queries per visit to the work counter: up to 32 for large
+  // batches (few atomics), fewer when that would leave resident warps idle
+  const uint64_t warps = (uint64_t)sms * bps * kWarpWarps;
+  const uint32_t per = (uint32_t)std::max<uint64_t>(1u, std::min<uint64_t>(32u, (uint64_t)n / (4u * warps)));
+  const uint64_t blocks = ((uint64_t)n + per - 1u) / per;
   const uint32_t grid = (uint32_t)std::min<uint64_t>((blocks + kWarpWarps - 1) / kWarpWarps, (uint64_t)sms * bps);
   uint32_t* work = ix->work + (ix->work_next.fetch_add(1u) % kWorkRing);
   SLASH_CK(cudaMemsetAsync(work, 0, sizeof(uint32_t), st));
@@ -2847,10 +2852,10 @@ int launch_warp(slash_index* ix, bool fused, uint32_t ctas_cap, uint32_t sms, co
     Launch lq(ix, fused ? "k_query_warp_fused" : "k_query_warp", st);
     if (fused)
       k_query_warp<true><<<grid, kWarpWarps * 32, smem, st>>>(ix->geo, lay, qbkt, ldq, offs, cols, n, topk, ix->slots,
-                                                             ix->fill, ids, scores, work, ix->err);
+                                                             ix->fill, ids, scores, work, ix->err, per);
     else
       k_query_warp<false><<<grid, kWarpWarps * 32, smem, st>>>(ix->geo, lay, qbkt, ldq, offs, cols, n, topk,
-                                                              ix->slots, ix->fill, ids, scores, work, ix->err);
+                                                              ix->slots, ix->fill, ids, scores, work, ix->err, per);
   }
   SLASH_CK(cudaGetLastError());
   if (fused && ix->staged && topk <= kLocalTop)

@@ -166,8 +166,10 @@ extern "C" int slash_serve(slash_index* ix, const slash_serve_opts* o, uint32_t 
     if (device_s) device_s[i] = NAN;
     status[i] = 0;
   }
-  // a batch of more than small_queries queries leaves reserve_sms SMs to the small ones
-  const slash_query_opts qo_small{o->mode, o->threads, 0u, 0u};
+  // a batch of more than small_queries queries leaves reserve_sms SMs to the small
+  // ones; the small ones run the team schedule (a query per CTA team: the shortest
+  // time per query), the others the given one
+  const slash_query_opts qo_small{SLASH_QUERY_FUSED, o->threads, 0u, 0u};
   const slash_query_opts qo_big{o->mode, o->threads, 0u, o->reserve_sms ? (uint32_t)num_sms - o->reserve_sms : 0u};
 
   // time zero; every time below is read from the host's clock
