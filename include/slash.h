@@ -141,6 +141,7 @@ int slash_query(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols,
 #define SLASH_QUERY_PLAIN 1u       /* one launch per stage: hash kernel, then gather/count/top-k kernel      */
 #define SLASH_QUERY_WARP_FUSED 2u  /* one warp per query (hash included); for queries with few candidates:
                                       up to 32 counted by warp matches, up to 512 in a per-warp table, more
+                                      by the team engine of SLASH_QUERY_FUSED where the index has one, else
                                       by the general kernel.  topk <= 10 and cm_width <= 32768 only          */
 #define SLASH_QUERY_WARP_PLAIN 3u  /* the same after the hash kernel                                          */
 
