@@ -143,7 +143,8 @@ int slash_query(slash_index *ix, const uint64_t *d_offs, const uint32_t *d_cols,
                                       up to 32 counted by warp matches, up to 512 in a per-warp table, more
                                       by the team engine of SLASH_QUERY_FUSED where the index has one, else
                                       by the general kernel.  topk <= 10 and cm_width <= 32768 only          */
-#define SLASH_QUERY_WARP_PLAIN 3u  /* the same after the hash kernel                                          */
+#define SLASH_QUERY_WARP_PLAIN 3u  /* the same after the hash kernel; queries above 512 candidates by the
+                                      general kernel                                                        */
 
 typedef struct {
   uint32_t mode;         /* SLASH_QUERY_FUSED, _PLAIN, _WARP_FUSED or _WARP_PLAIN                   */
